@@ -30,15 +30,16 @@ def lib():
         i64p = ctypes.POINTER(ctypes.c_int64)
         i32p = ctypes.POINTER(ctypes.c_int32)
         u32p = ctypes.POINTER(ctypes.c_uint32)
+        u16p = ctypes.POINTER(ctypes.c_uint16)
         L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
         L.orc_philox4x32_10.restype = None
         L.orc_lattice_chain.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
-                                        ctypes.c_int, ctypes.c_double, i32p, u8p, u8p,
+                                        ctypes.c_int, ctypes.c_double, i32p, u8p, u16p,
                                         f64p, i64p, i64p]
         L.orc_lattice_chain.restype = ctypes.c_int
         L.orc_lattice_run.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64,
                                       ctypes.c_int64, ctypes.c_int, ctypes.c_double,
-                                      ctypes.c_int, u8p, f64p, i64p, i64p, u8p, u8p, f64p]
+                                      ctypes.c_int, u16p, f64p, i64p, i64p, u8p, u8p, f64p]
         L.orc_lattice_run.restype = None
         L.orc_offlattice_run.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64,
                                          ctypes.c_int64, ctypes.c_int, ctypes.c_int,
@@ -80,13 +81,13 @@ def lattice_run(seed, N, C, beta_eps=0.0, ensemble=0, chain0=0, threads=None,
                 trace=False, coords=False):
     """Grow chains chain0 .. chain0+C-1 on the cubic lattice (Algorithm 1, Eq. 3).
 
-    Returns a dict of numpy arrays: counts [C,8] u8, logw [C] f64, r2 [C] i64,
+    Returns a dict of numpy arrays: counts [C,8] u16, logw [C] f64, r2 [C] i64,
     n2rg2 [C] i64, alive [C] u8, and optionally trace [C,N-1] u8 and
     coords [C,N,3] f64.
     """
     C = int(C)
     out = {
-        "counts": np.zeros((C, 8), np.uint8),
+        "counts": np.zeros((C, 8), np.uint16),
         "logw": np.zeros(C, np.float64),
         "r2": np.zeros(C, np.int64),
         "n2rg2": np.zeros(C, np.int64),
@@ -99,7 +100,7 @@ def lattice_run(seed, N, C, beta_eps=0.0, ensemble=0, chain0=0, threads=None,
     lib().orc_lattice_run(
         int(seed), int(ensemble), int(chain0), C, int(N), float(beta_eps),
         int(threads or default_threads()),
-        _ptr(out["counts"], ctypes.c_uint8), _ptr(out["logw"], ctypes.c_double),
+        _ptr(out["counts"], ctypes.c_uint16), _ptr(out["logw"], ctypes.c_double),
         _ptr(out["r2"], ctypes.c_int64), _ptr(out["n2rg2"], ctypes.c_int64),
         _ptr(out["alive"], ctypes.c_uint8), _ptr(out.get("trace"), ctypes.c_uint8),
         _ptr(out.get("coords"), ctypes.c_double))

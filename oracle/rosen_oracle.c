@@ -117,10 +117,10 @@ static int l1(const int32_t *a, const int32_t *b)
  */
 ORC_EXPORT int orc_lattice_chain(uint64_t seed, uint32_t ens, uint32_t chain,
                                  int N, double beta_eps, int32_t *pos,
-                                 uint8_t *trace, uint8_t counts[8],
+                                 uint8_t *trace, uint16_t counts[8],
                                  double *logw, int64_t *r2, int64_t *n2rg2)
 {
-    memset(counts, 0, 8);
+    memset(counts, 0, sizeof(uint16_t) * 8);
     memset(pos, 0, sizeof(int32_t) * 3 * (size_t)N);
     if (trace) memset(trace, 0xFF, (size_t)(N - 1));
     double lw = 0.0;
@@ -400,7 +400,7 @@ typedef struct {
     int N, k, potential;
     double sigma, cutoff, beta_eps;
     /* outputs, indexed by local chain c (0 .. C-1) */
-    uint8_t *counts;          /* [C][8]        lattice   */
+    uint16_t *counts;         /* [C][8]        lattice   */
     double *logw;             /* [C]                      */
     int64_t *r2_i;            /* [C]           lattice   */
     int64_t *n2rg2;           /* [C]           lattice   */
@@ -418,13 +418,13 @@ static void *run_range(void *arg)
     if (J->kind == 0) {
         int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)N);
         for (int64_t c = J->lo; c < J->hi; ++c) {
-            uint8_t cnt[8];
+            uint16_t cnt[8];
             double lw;
             int64_t r2, g2;
             int ok = orc_lattice_chain(
                 J->seed, J->ens, (uint32_t)(J->chain0 + c), N, J->beta_eps, pos,
                 J->trace ? J->trace + (size_t)c * (N - 1) : NULL, cnt, &lw, &r2, &g2);
-            if (J->counts) memcpy(J->counts + 8 * (size_t)c, cnt, 8);
+            if (J->counts) memcpy(J->counts + 8 * (size_t)c, cnt, sizeof cnt);
             if (J->logw) J->logw[c] = lw;
             if (J->r2_i) J->r2_i[c] = r2;
             if (J->n2rg2) J->n2rg2[c] = g2;
@@ -480,7 +480,7 @@ static void run_threads(run_job *base, int64_t C, int nthreads)
 
 ORC_EXPORT void orc_lattice_run(uint64_t seed, uint32_t ens, int64_t chain0,
                                 int64_t C, int N, double beta_eps, int nthreads,
-                                uint8_t *counts, double *logw, int64_t *r2,
+                                uint16_t *counts, double *logw, int64_t *r2,
                                 int64_t *n2rg2, uint8_t *alive, uint8_t *trace,
                                 double *coords)
 {
