@@ -1,0 +1,187 @@
+/*
+ * rosen.h -- C ABI of the GB300 Rosenbluth chain-growth library (librosen.so).
+ *
+ * The library grows very many independent polymer chains with the
+ * Rosenbluth method of Guo & Baulin, "GPU Implementation of the Rosenbluth
+ * Generation Method for Static Monte Carlo Simulations" (arxiv 1704.04381),
+ * on the simple cubic lattice (Section 3.3.2, Algorithm 1) and in real space
+ * (Section 3.3.3, Algorithm 2), and reduces W-weighted ensemble averages
+ * (Eq. 2, Eq. 9).  Every step runs in the library's own CUDA kernels for
+ * sm_103a; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: a ROSEN_* status.  ROSEN_OK on success.  On failure a
+ *    description is available from rosen_last_error() (thread-local).
+ *  - Array pointers are DEVICE pointers owned by the caller, unless a
+ *    comment says otherwise.  The library never frees them and keeps no
+ *    reference after the call returns (the serving API is the exception and
+ *    says so).  Output pointers that may be NULL are marked "optional".
+ *  - Work is enqueued asynchronously on `stream` (a cudaStream_t passed as
+ *    void*; NULL is the legacy default stream).  Parameters are checked on
+ *    the host first: a bad parameter returns ROSEN_EINVAL and enqueues
+ *    nothing.  ROSEN_ECUDA reports a CUDA launch error.
+ *  - Per-chain arrays are indexed by the local chain index c in [0, C); the
+ *    chain's random stream is keyed by its global index chain0 + c, so a
+ *    range of chains can be grown in pieces (or on several GPUs) with
+ *    identical results.
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = the 64-bit
+ *    seed (low word first), counter = (chain, ensemble, step, slot).
+ */
+#ifndef ROSEN_H
+#define ROSEN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ROSEN_API __attribute__((visibility("default")))
+#else
+#define ROSEN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define ROSEN_OK 0
+#define ROSEN_EINVAL 1    /* bad argument; nothing was enqueued            */
+#define ROSEN_ENOMEM 2    /* workspace too small / budget exceeded         */
+#define ROSEN_ECUDA 3     /* a CUDA call failed                            */
+#define ROSEN_ETIMEOUT 4  /* a bounded wait ran out                        */
+#define ROSEN_EBUSY 5     /* queue full, try again                         */
+#define ROSEN_EAGAIN 6    /* result not ready yet                          */
+#define ROSEN_ECLOSED 7   /* server shut down / request cancelled          */
+#define ROSEN_ENOTFOUND 8 /* unknown ticket                                */
+
+/* ---- limits and flags ------------------------------------------------ */
+#define ROSEN_LATTICE_NMAX 512    /* packed 10-bit lattice coordinates      */
+#define ROSEN_OFFLATTICE_NMAX 1024
+#define ROSEN_KMAX 128            /* real-space trials per step             */
+
+#define ROSEN_STORE_TRACE 1u      /* write the per-step trace bytes         */
+#define ROSEN_STORE_COORDS 2u     /* write the chain coordinates            */
+
+#define ROSEN_HARD_SPHERE 0
+#define ROSEN_LJ 1
+
+/* Human-readable name of a status code (static string). */
+ROSEN_API const char *rosen_status_string(int status);
+/* Last error message of the calling thread ("" if none). */
+ROSEN_API const char *rosen_last_error(void);
+/* Library version string, e.g. "rosen 0.1 sm_103a". */
+ROSEN_API const char *rosen_version(void);
+
+/* ---- Philox stream (exposed for verification) ------------------------ */
+/*
+ * out[4*q + w] = word w of Philox4x32-10(counter = (chain0 + q, ensemble,
+ * step, slot), key = seed), for q in [0, n).  out: device, 4*n uint32.
+ * This is the generator every growth kernel draws from (it replaces the
+ * paper's per-thread cuRAND state, Section 3.2).
+ */
+ROSEN_API int rosen_philox(uint64_t seed, uint32_t ensemble, uint32_t step, uint32_t slot,
+                 int64_t chain0, int64_t n, uint32_t *out, void *stream);
+
+/* ---- cubic lattice growth (Section 3.3.2, Algorithm 1, Eq. 3) --------- */
+typedef struct rosen_lattice_params {
+    uint64_t seed;
+    uint32_t ensemble;        /* ensemble id, part of the Philox counter    */
+    int32_t N;                /* monomers per chain, 2 <= N <= 512          */
+    int64_t C;                /* chains, C >= 0                             */
+    int64_t chain0;           /* global index of chain 0; chain0+C <= 2^32  */
+    double beta_eps;          /* >= 0, finite.  0: athermal SAW.  > 0: each
+                                 non-bonded nearest-neighbour contact has
+                                 energy -eps (interacting SAW)              */
+    uint32_t flags;           /* ROSEN_STORE_TRACE | ROSEN_STORE_COORDS     */
+    int32_t lanes_per_chain;  /* 0 = automatic; else 1 (one chain per lane) */
+} rosen_lattice_params;
+
+typedef struct rosen_lattice_out {
+    uint16_t *counts; /* [C][8] optional: counts[c][m] = steps with m free
+                         neighbours (m = 1..6); counts[c][0] = 1 marks a dead
+                         chain (trapped: W = 0).  For beta_eps = 0 the exact
+                         weight is W = prod_m m^counts[c][m].              */
+    float *logw;      /* [C] optional: log W, -inf for a dead chain.  FP32
+                         sum of FP32 logs (athermal: from the exact counts) */
+    int32_t *r2;      /* [C] optional: R_ee^2 (exact)                       */
+    int64_t *n2rg2;   /* [C] optional: N^2 R_g^2 = N sum|r_i|^2 - |sum r_i|^2
+                         (exact)                                            */
+    uint8_t *trace;   /* [N-1][C] optional (needs ROSEN_STORE_TRACE):
+                         byte (m << 3) | d for step i at [i-1][c], d the
+                         chosen neighbour in the order +x,-x,+y,-y,+z,-z;
+                         7 at the step that dead-ends, 0xFF after it        */
+    int32_t *coords;  /* [N][3][C] optional (needs ROSEN_STORE_COORDS):
+                         monomer i, axis a of chain c at [i][a][c]; zero
+                         after a dead end                                   */
+} rosen_lattice_out;
+
+/*
+ * Grow chains chain0 .. chain0+C-1 on the simple cubic lattice.  Monomer 0
+ * is at the origin; step i scores the six neighbours of monomer i-1 against
+ * monomers 0..i-2 (free / number of contacts), multiplies W by the number of
+ * free neighbours (athermal) or by the sum of their Boltzmann factors
+ * exp(beta_eps * contacts) (interacting), and picks one neighbour in
+ * proportion to its weight.  Results are identical, bit for bit, to a
+ * sequential implementation of the same rule in FP64 (the FP32 selection
+ * falls back to FP64 whenever rounding could change the choice).
+ * Errors: EINVAL for N outside [2, 512], C < 0, chain0 + C > 2^32,
+ * beta_eps < 0 or not finite, unknown flags or lanes_per_chain.
+ */
+ROSEN_API int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lattice_out *o,
+                       void *stream);
+
+/* ---- ensemble reduction (Eq. 2 with W as weight, Eq. 9) --------------- */
+#define ROSEN_REDUCE_LATTICE 0    /* inputs: counts or logw, r2 (int32), n2rg2 */
+#define ROSEN_REDUCE_OFFLATTICE 1 /* inputs: logw, r2 (float), rg2 (float)     */
+
+typedef struct rosen_reduce_in {
+    int32_t kind;            /* ROSEN_REDUCE_LATTICE / ROSEN_REDUCE_OFFLATTICE */
+    int32_t N;               /* monomers per chain                           */
+    int32_t k;               /* trials per step for logZ_norm (0: none)      */
+    int32_t use_counts;      /* lattice only: 1 = take log W from counts in
+                                FP64 (exact athermal weights), 0 = from logw */
+    int64_t C;               /* chains, >= 1                                 */
+    const float *logw;       /* [C] log W, -inf = dead (ignored if use_counts) */
+    const uint16_t *counts;  /* [C][8] (lattice, use_counts = 1)             */
+    const int32_t *r2_i;     /* [C] lattice R_ee^2                           */
+    const int64_t *n2rg2;    /* [C] lattice N^2 R_g^2                        */
+    const float *r2_f;       /* [C] real-space R_ee^2                        */
+    const float *rg2_f;      /* [C] real-space R_g^2                         */
+} rosen_reduce_in;
+
+/* Ensemble statistics, all FP64.  With w_c = exp(log W_c - log_max):     */
+typedef struct rosen_stats {
+    double n;          /* chains, dead ones included (Eq. 9)               */
+    double n_alive;
+    double log_max;    /* max log W over live chains                       */
+    double S0, S1, S2; /* sum w, sum w R_ee^2, sum w R_g^2                 */
+    double Q0;         /* sum w^2                                          */
+    double Q1_r2, Q2_r2;   /* sum w^2 R_ee^2, sum w^2 R_ee^4               */
+    double Q1_rg2, Q2_rg2; /* sum w^2 R_g^2,  sum w^2 R_g^4                */
+    double logZ;       /* log((1/n) sum W), Eq. 9                          */
+    double logZ_norm;  /* logZ - (N-1) log k (k > 0), else logZ            */
+    double mean_r2, se_r2;   /* S1/S0 (Eq. 2) and its ratio standard error */
+    double mean_rg2, se_rg2;
+    double ess;        /* S0^2 / Q0                                        */
+} rosen_stats;
+
+/* Bytes of device workspace rosen_reduce needs for C chains. */
+ROSEN_API size_t rosen_reduce_workspace_size(int64_t C);
+
+/*
+ * Reduce per-chain outputs to ensemble statistics in FP64 with a max-shifted
+ * (log-sum-exp) sum, in a fixed order that depends only on C: the result is
+ * deterministic.  out: DEVICE pointer to one rosen_stats.  workspace: device,
+ * at least rosen_reduce_workspace_size(C) bytes, contents need not be
+ * initialised.  All chains dead gives logZ = -inf, means = NaN, ess = 0.
+ * Errors: EINVAL (C < 1, missing input array, bad kind), ENOMEM (workspace
+ * too small).
+ */
+ROSEN_API int rosen_reduce(const rosen_reduce_in *in, rosen_stats *out, void *workspace,
+                 size_t workspace_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ROSEN_H */

@@ -1,0 +1,344 @@
+// lattice.cu -- Rosenbluth growth on the simple cubic lattice
+// (Guo & Baulin, Section 3.3.2, Algorithm 1; weight of Eq. 3).
+//
+// GB300 mapping: one chain per lane.  A warp grows 32 chains in lock-step
+// (every chain is at the same step i), so the overlap scan over the earlier
+// monomers has a warp-uniform trip count and no divergence.  The chain lives
+// in shared memory as one packed 32-bit key per monomer,
+//     key = (x + 512) | (y + 512) << 10 | (z + 512) << 20,
+// stored [monomer][lane] so that a warp's 32 loads of monomer j hit 32
+// different banks.  For every earlier monomer j the kernel forms
+//     t = key_j - key_end + (2, 2, 2)
+// with one integer add: t is the packed displacement (dx+2, dy+2, dz+2) and
+// it fits three 3-bit fields exactly when the monomer lies in the 5x5x5 box
+// around the end (|d| <= 511 on every axis keeps the fields from borrowing
+// into each other).  A 512-entry table indexed by those fields turns the
+// displacement into "occupies neighbour d" bits and "touches neighbour d"
+// contact increments, which are simply added (a site holds one monomer, so
+// the occupancy bits never carry).  Parity halves the athermal scan: only
+// monomers j with j = i (mod 2) can sit on a neighbour of the end.
+//
+// Selection: athermal steps take the idx-th free neighbour with
+// idx = floor(x * m / 2^32).  Interacting steps draw r = u24(x) * S in FP32
+// and take the smallest slot whose prefix sum exceeds r; when r lies within
+// 2^-18 S of one of the chosen slot's bounds the choice is recomputed in FP64
+// with exactly the sequential FP64 arithmetic, so the path never depends on
+// FP32 rounding.
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace rosen {
+namespace {
+
+constexpr uint32_t kFieldMask = 0x00701C07u;                  // 3-bit fields at 0, 10, 20
+constexpr uint32_t kNearBias = 2u | (2u << 10) | (2u << 20);  // +2 on every axis
+constexpr uint32_t kOriginKey = 512u | (512u << 10) | (512u << 20);
+constexpr int kLutWords = 512;
+constexpr int kSelBytes = 512;
+
+// Gather the three 3-bit fields of t into a 9-bit table index.
+__device__ __forceinline__ uint32_t lut_index(uint32_t t)
+{
+    return (t | (t >> 7) | (t >> 14)) & 0x1FFu;
+}
+
+// Table entry for an earlier monomer at displacement d from the chain end.
+// Bits 0..5: d is neighbour n of the end (neighbour n is occupied).
+// Bits 8+3n..10+3n: the monomer is at lattice distance 1 from neighbour n
+// (one non-bonded contact for a monomer placed there).
+__device__ uint32_t lut_entry(int idx)
+{
+    const int dx = (idx & 7) - 2, dy = ((idx >> 3) & 7) - 2, dz = ((idx >> 6) & 7) - 2;
+    if (dx > 2 || dy > 2 || dz > 2) return 0u;
+    if (dx == 0 && dy == 0 && dz == 0) return 0u;
+    uint32_t e = 0u;
+    for (int n = 0; n < 6; ++n) {
+        const int ex = (n == 0) - (n == 1), ey = (n == 2) - (n == 3), ez = (n == 4) - (n == 5);
+        const int l1 = abs(dx - ex) + abs(dy - ey) + abs(dz - ez);
+        if (l1 == 0) e |= 1u << n;
+        else if (l1 == 1) e += 1u << (8 + 3 * n);
+    }
+    return e;
+}
+
+// Position of the (idx+1)-th set bit of a 6-bit mask (selection table).
+__device__ uint8_t nth_set_bit(uint32_t mask, uint32_t idx)
+{
+    uint32_t seen = 0;
+    for (int n = 0; n < 6; ++n)
+        if ((mask >> n) & 1u) {
+            if (seen == idx) return (uint8_t)n;
+            ++seen;
+        }
+    return 0xFFu;
+}
+
+struct LatticeArgs {
+    uint32_t k0, k1, ens, chain0;
+    int32_t N;
+    int64_t C;
+    float wt32[8];    // exp(beta_eps * c), c = 0..5, rounded to FP32
+    double wt64[8];   // the same in FP64
+    float logm[8];    // log(m), m = 0..6 (athermal log W from counts)
+    uint4 *counts;    // [C] packed 8 x u16
+    float *logw;
+    int32_t *r2;
+    int64_t *n2rg2;
+    uint8_t *trace;   // [N-1][C]
+    int32_t *coords;  // [N][3][C]
+};
+
+// The FP64 selection, in exactly the order of the sequential definition:
+// S = sum of the weights in slot order, r = u24(x) * S, first slot whose
+// running prefix exceeds r, else the last slot with a positive weight.
+__device__ __noinline__ int select_fp64(uint32_t freem, uint32_t acc, uint32_t x,
+                                        const double *wt64)
+{
+    double w[6], S = 0.0;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        const uint32_t cd = (acc >> (8 + 3 * d)) & 7u;
+        w[d] = ((freem >> d) & 1u) ? wt64[cd] : 0.0;
+        S = __dadd_rn(S, w[d]);
+    }
+    const double r = __dmul_rn(u24d(x), S);
+    double P = 0.0;
+    int sel = -1;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        P = __dadd_rn(P, w[d]);
+        if (sel < 0 && P > r) sel = d;
+    }
+    if (sel < 0)
+#pragma unroll
+        for (int d = 0; d < 6; ++d)
+            if (w[d] > 0.0) sel = d;
+    return sel;
+}
+
+template <bool kIsaw>
+__global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *lut = smem;
+    uint8_t *seltab = reinterpret_cast<uint8_t *>(smem + kLutWords);
+    float *wt32 = reinterpret_cast<float *>(smem + kLutWords + kSelBytes / 4);
+    double *wt64 = reinterpret_cast<double *>(smem + kLutWords + kSelBytes / 4 + 8);
+    uint32_t *keys = smem + kLutWords + kSelBytes / 4 + 8 + 16;
+
+    for (int q = threadIdx.x; q < kLutWords; q += blockDim.x) {
+        lut[q] = lut_entry(q);
+        seltab[q] = nth_set_bit((uint32_t)q >> 3, (uint32_t)q & 7u);
+    }
+    if (threadIdx.x < 8) {
+        wt32[threadIdx.x] = a.wt32[threadIdx.x];
+        wt64[threadIdx.x] = a.wt64[threadIdx.x];
+    }
+    __syncthreads();
+
+    const int B = blockDim.x;
+    const int64_t c = (int64_t)blockIdx.x * B + threadIdx.x;
+    if (c >= a.C) return;
+    const uint32_t chain = a.chain0 + (uint32_t)c;
+    const int N = a.N;
+    const int64_t C = a.C;
+    uint32_t *my = keys + threadIdx.x;
+
+    uint32_t key = kOriginKey;
+    my[0] = key;
+    int sx = 0, sy = 0, sz = 0, sq = 0;
+    int ex = 0, ey = 0, ez = 0;
+    uint64_t cnt = 0;      // 9-bit field m holds the number of steps with m free sites
+    float lw = 0.f;
+    int dead_at = 0;
+    if (a.coords) {
+        a.coords[(0 * 3 + 0) * C + c] = 0;
+        a.coords[(0 * 3 + 1) * C + c] = 0;
+        a.coords[(0 * 3 + 2) * C + c] = 0;
+    }
+
+    for (int i = 1; i < N; ++i) {
+        uint32_t acc = 0u;
+        const uint32_t kb = kNearBias - key;
+        if (kIsaw) {
+#pragma unroll 4
+            for (int j = 0; j <= i - 2; ++j) {
+                const uint32_t t = my[j * B] + kb;
+                if ((t & ~kFieldMask) == 0u) acc += lut[lut_index(t)];
+            }
+        } else {
+#pragma unroll 4
+            for (int j = i & 1; j <= i - 2; j += 2) {
+                const uint32_t t = my[j * B] + kb;
+                if ((t & ~kFieldMask) == 0u) acc += lut[lut_index(t)];
+            }
+        }
+        const uint32_t freem = ~acc & 63u;
+        const int m = __popc(freem);
+        if (m == 0) {
+            dead_at = i;
+            break;
+        }
+        const uint32_t x = philox(make_uint4(chain, a.ens, (uint32_t)i, 0u), a.k0, a.k1).x;
+        int sel;
+        if (!kIsaw) {
+            sel = seltab[(freem << 3) | __umulhi(x, (uint32_t)m)];
+        } else {
+            float w[6], S = 0.f;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                const uint32_t cd = (acc >> (8 + 3 * d)) & 7u;
+                w[d] = ((freem >> d) & 1u) ? wt32[cd] : 0.f;
+                S += w[d];
+            }
+            const float r = u24f(x) * S;
+            float P = 0.f, lo = 0.f, hi = 0.f;
+            sel = -1;
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                const float Pn = P + w[d];
+                if (sel < 0 && Pn > r) {
+                    sel = d;
+                    lo = P;
+                    hi = Pn;
+                }
+                P = Pn;
+            }
+            const float tol = S * 0x1p-18f;
+            if (sel < 0 || !(r - lo > tol) || !(hi - r > tol)) sel = select_fp64(freem, acc, x, wt64);
+            lw += logf(S);
+        }
+        cnt += 1ull << (9 * m);
+        const uint32_t axis_step = 1u << (10 * (sel >> 1));
+        key = (sel & 1) ? key - axis_step : key + axis_step;
+        my[i * B] = key;
+        ex = (int)(key & 1023u) - 512;
+        ey = (int)((key >> 10) & 1023u) - 512;
+        ez = (int)(key >> 20) - 512;
+        sx += ex;
+        sy += ey;
+        sz += ez;
+        sq += ex * ex + ey * ey + ez * ez;
+        if (a.trace) a.trace[(int64_t)(i - 1) * C + c] = (uint8_t)((m << 3) | sel);
+        if (a.coords) {
+            a.coords[((int64_t)i * 3 + 0) * C + c] = ex;
+            a.coords[((int64_t)i * 3 + 1) * C + c] = ey;
+            a.coords[((int64_t)i * 3 + 2) * C + c] = ez;
+        }
+    }
+
+    if (dead_at) {
+        // Trapped (Section 3.3.2 restarts such chains; here W = 0 is kept).
+        if (a.counts) a.counts[c] = make_uint4(1u, 0u, 0u, 0u);
+        if (a.logw) a.logw[c] = -INFINITY;
+        if (a.r2) a.r2[c] = 0;
+        if (a.n2rg2) a.n2rg2[c] = 0;
+        if (a.trace) {
+            a.trace[(int64_t)(dead_at - 1) * C + c] = 7u;
+            for (int i = dead_at + 1; i < N; ++i) a.trace[(int64_t)(i - 1) * C + c] = 0xFFu;
+        }
+        if (a.coords)
+            for (int i = dead_at; i < N; ++i)
+                for (int q = 0; q < 3; ++q) a.coords[((int64_t)i * 3 + q) * C + c] = 0;
+        return;
+    }
+    uint32_t cm[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) cm[q] = (uint32_t)(cnt >> (9 * q)) & 511u;
+    if (!kIsaw) {
+        lw = 0.f;
+#pragma unroll
+        for (int q = 2; q <= 6; ++q) lw += (float)cm[q] * a.logm[q];
+    }
+    if (a.counts)
+        a.counts[c] = make_uint4(cm[0] | (cm[1] << 16), cm[2] | (cm[3] << 16),
+                                 cm[4] | (cm[5] << 16), cm[6]);
+    if (a.logw) a.logw[c] = lw;
+    if (a.r2) a.r2[c] = ex * ex + ey * ey + ez * ez;
+    if (a.n2rg2)
+        a.n2rg2[c] = (int64_t)N * sq -
+                     ((int64_t)sx * sx + (int64_t)sy * sy + (int64_t)sz * sz);
+}
+
+}  // namespace
+}  // namespace rosen
+
+using namespace rosen;
+
+static size_t lattice_smem_bytes(int N, int B)
+{
+    return (size_t)(kLutWords + kSelBytes / 4 + 8 + 16) * 4 + (size_t)N * B * 4;
+}
+
+// Block size: the largest multiple of 32 (at most 256) whose coordinate
+// tile fits in about half of an SM's shared memory, so that at least two
+// blocks are resident per SM.
+static int lattice_block(int N)
+{
+    const size_t budget = 110 * 1024;
+    int B = 256;
+    while (B > 32 && lattice_smem_bytes(N, B) > budget) B -= 32;
+    return B;
+}
+
+extern "C" int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lattice_out *o,
+                                  void *stream)
+{
+    if (!p || !o) return set_error(ROSEN_EINVAL, "rosen_lattice_grow: NULL params or outputs");
+    if (p->N < 2 || p->N > ROSEN_LATTICE_NMAX)
+        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: N = %d outside [2, %d]", p->N,
+                         ROSEN_LATTICE_NMAX);
+    if (p->C < 0 || p->chain0 < 0 || p->chain0 + p->C > (int64_t(1) << 32))
+        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: chains [%lld, %lld) outside [0, 2^32)",
+                         (long long)p->chain0, (long long)(p->chain0 + p->C));
+    if (!(p->beta_eps >= 0.0) || !isfinite(p->beta_eps))
+        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: beta_eps must be finite and >= 0");
+    if (p->flags & ~(ROSEN_STORE_TRACE | ROSEN_STORE_COORDS))
+        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: unknown flags 0x%x", p->flags);
+    if (p->lanes_per_chain != 0 && p->lanes_per_chain != 1)
+        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: lanes_per_chain must be 0 or 1");
+    if ((p->flags & ROSEN_STORE_TRACE) && !o->trace)
+        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: ROSEN_STORE_TRACE without trace");
+    if ((p->flags & ROSEN_STORE_COORDS) && !o->coords)
+        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: ROSEN_STORE_COORDS without coords");
+    if (o->counts && (reinterpret_cast<uintptr_t>(o->counts) & 15u))
+        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: counts must be 16-byte aligned");
+    if (p->C == 0) return ROSEN_OK;
+
+    LatticeArgs a;
+    memset(&a, 0, sizeof a);
+    a.k0 = (uint32_t)p->seed;
+    a.k1 = (uint32_t)(p->seed >> 32);
+    a.ens = p->ensemble;
+    a.chain0 = (uint32_t)p->chain0;
+    a.N = p->N;
+    a.C = p->C;
+    for (int q = 0; q < 8; ++q) {
+        a.wt64[q] = exp(p->beta_eps * (double)q);
+        a.wt32[q] = (float)a.wt64[q];
+        a.logm[q] = q >= 1 ? (float)log((double)q) : 0.f;
+    }
+    a.counts = reinterpret_cast<uint4 *>(o->counts);
+    a.logw = o->logw;
+    a.r2 = o->r2;
+    a.n2rg2 = o->n2rg2;
+    a.trace = (p->flags & ROSEN_STORE_TRACE) ? o->trace : nullptr;
+    a.coords = (p->flags & ROSEN_STORE_COORDS) ? o->coords : nullptr;
+
+    const int B = lattice_block(p->N);
+    const size_t smem = lattice_smem_bytes(p->N, B);
+    const int64_t blocks = (p->C + B - 1) / B;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->beta_eps == 0.0) {
+        cudaFuncSetAttribute(lattice_lane_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        lattice_lane_kernel<false><<<(unsigned)blocks, B, smem, s>>>(a);
+    } else {
+        cudaFuncSetAttribute(lattice_lane_kernel<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        lattice_lane_kernel<true><<<(unsigned)blocks, B, smem, s>>>(a);
+    }
+    return check_launch("rosen_lattice_grow");
+}

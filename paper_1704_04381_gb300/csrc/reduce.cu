@@ -1,0 +1,298 @@
+// reduce.cu -- FP64 ensemble reduction of Rosenbluth-weighted observables
+// (Guo & Baulin, Eq. 2 with W as the importance weight; Eq. 9 for Z_N).
+//
+// Rosenbluth weights span hundreds of orders of magnitude, so the sums are
+// formed in FP64 relative to a running maximum (log-sum-exp).  The chains
+// are cut into fixed tiles of kTile chains; one block reduces one tile to a
+// partial (its max M_t and the sums scaled by exp(-M_t)), and a single block
+// merges the partials.  Tiles, the in-tile order and the merge tree depend
+// only on C, so the result is bit-for-bit deterministic.
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace rosen {
+namespace {
+
+constexpr int kTile = 2048;
+constexpr int kThreads = 256;
+constexpr int kPerThread = kTile / kThreads;
+constexpr int kFinalThreads = 256;
+
+struct Partial {
+    double M;          // max log W in the tile (-inf: no live chain)
+    double s[8];       // S0 S1 S2 Q0 Q1a Q2a Q1b Q2b, scaled by exp(-M) / exp(-2M)
+    double alive;
+    double pad[2];
+};
+
+struct ReduceArgs {
+    int32_t kind, N, k, use_counts;
+    int64_t C;
+    const float *logw;
+    const uint4 *counts;
+    const int32_t *r2_i;
+    const int64_t *n2rg2;
+    const float *r2_f;
+    const float *rg2_f;
+    double logm[8];     // log(m) in FP64, m = 0..6
+    double inv_n2;      // 1 / N^2
+};
+
+__device__ __forceinline__ void load_chain(const ReduceArgs &a, int64_t c, double &lw,
+                                           double &A1, double &A2)
+{
+    if (a.kind == ROSEN_REDUCE_LATTICE) {
+        if (a.use_counts) {
+            const uint4 v = a.counts[c];
+            if (v.x & 0xFFFFu) {
+                lw = -INFINITY;
+            } else {
+                // log W = sum_m counts[m] log m, exact up to FP64 rounding.
+                const uint32_t cm[7] = {v.x & 0xFFFFu, v.x >> 16, v.y & 0xFFFFu, v.y >> 16,
+                                        v.z & 0xFFFFu, v.z >> 16, v.w & 0xFFFFu};
+                double s = 0.0;
+#pragma unroll
+                for (int q = 2; q <= 6; ++q) s = fma((double)cm[q], a.logm[q], s);
+                lw = s;
+            }
+        } else {
+            lw = (double)a.logw[c];
+        }
+        A1 = (double)a.r2_i[c];
+        A2 = (double)a.n2rg2[c] * a.inv_n2;
+    } else {
+        lw = (double)a.logw[c];
+        A1 = (double)a.r2_f[c];
+        A2 = (double)a.rg2_f[c];
+    }
+}
+
+// Merge partial b into a (same max-shift convention).
+__device__ __forceinline__ void merge(double &Ma, double *sa, double &na, double Mb,
+                                      const double *sb, double nb)
+{
+    const double M = fmax(Ma, Mb);
+    if (M == -INFINITY) {
+        na += nb;
+        return;
+    }
+    const double fa = (Ma == -INFINITY) ? 0.0 : exp(Ma - M);
+    const double fb = (Mb == -INFINITY) ? 0.0 : exp(Mb - M);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) sa[q] = sa[q] * fa + sb[q] * fb;
+#pragma unroll
+    for (int q = 3; q < 8; ++q) sa[q] = sa[q] * (fa * fa) + sb[q] * (fb * fb);
+    Ma = M;
+    na += nb;
+}
+
+__global__ void __launch_bounds__(kThreads) reduce_tiles_kernel(const ReduceArgs a, Partial *part)
+{
+    __shared__ double red[kThreads / 32][10];
+    __shared__ double tileM;
+    const int64_t c0 = (int64_t)blockIdx.x * kTile;
+    double lw[kPerThread], A1[kPerThread], A2[kPerThread];
+    double m = -INFINITY;
+#pragma unroll
+    for (int q = 0; q < kPerThread; ++q) {
+        const int64_t c = c0 + threadIdx.x + (int64_t)q * kThreads;
+        if (c < a.C) {
+            load_chain(a, c, lw[q], A1[q], A2[q]);
+        } else {
+            lw[q] = -INFINITY;
+            A1[q] = A2[q] = 0.0;
+        }
+        m = fmax(m, lw[q]);
+    }
+    // Block maximum.
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp][0] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mm = -INFINITY;
+        for (int w = 0; w < kThreads / 32; ++w) mm = fmax(mm, red[w][0]);
+        tileM = mm;
+    }
+    __syncthreads();
+    const double M = tileM;
+    double s[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) s[q] = 0.0;
+    if (M > -INFINITY) {
+#pragma unroll
+        for (int q = 0; q < kPerThread; ++q) {
+            if (lw[q] == -INFINITY) continue;
+            const double w = exp(lw[q] - M), w2 = w * w;
+            s[0] += w;
+            s[1] += w * A1[q];
+            s[2] += w * A2[q];
+            s[3] += w2;
+            s[4] += w2 * A1[q];
+            s[5] += w2 * A1[q] * A1[q];
+            s[6] += w2 * A2[q];
+            s[7] += w2 * A2[q] * A2[q];
+            s[8] += 1.0;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 9; ++q) red[warp][q] = s[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Partial P;
+        P.M = M;
+        for (int q = 0; q < 8; ++q) {
+            double t = 0.0;
+            for (int w = 0; w < kThreads / 32; ++w) t += red[w][q];
+            P.s[q] = t;
+        }
+        double al = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) al += red[w][8];
+        P.alive = al;
+        P.pad[0] = P.pad[1] = 0.0;
+        part[blockIdx.x] = P;
+    }
+}
+
+__global__ void __launch_bounds__(kFinalThreads) reduce_final_kernel(const Partial *part,
+                                                                     int64_t ntiles,
+                                                                     const ReduceArgs a,
+                                                                     rosen_stats *out)
+{
+    __shared__ double sM[kFinalThreads], sS[kFinalThreads][8], sN[kFinalThreads];
+    double M = -INFINITY, S[8] = {0, 0, 0, 0, 0, 0, 0, 0}, na = 0.0;
+    for (int64_t t = threadIdx.x; t < ntiles; t += kFinalThreads)
+        merge(M, S, na, part[t].M, part[t].s, part[t].alive);
+    sM[threadIdx.x] = M;
+    for (int q = 0; q < 8; ++q) sS[threadIdx.x][q] = S[q];
+    sN[threadIdx.x] = na;
+    __syncthreads();
+    for (int half = kFinalThreads / 2; half > 0; half >>= 1) {
+        if (threadIdx.x < half) {
+            double Mb = sM[threadIdx.x + half], Sb[8];
+            for (int q = 0; q < 8; ++q) Sb[q] = sS[threadIdx.x + half][q];
+            double Ma = sM[threadIdx.x], Sa[8], nA = sN[threadIdx.x];
+            for (int q = 0; q < 8; ++q) Sa[q] = sS[threadIdx.x][q];
+            merge(Ma, Sa, nA, Mb, Sb, sN[threadIdx.x + half]);
+            sM[threadIdx.x] = Ma;
+            for (int q = 0; q < 8; ++q) sS[threadIdx.x][q] = Sa[q];
+            sN[threadIdx.x] = nA;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    rosen_stats r;
+    r.n = (double)a.C;
+    r.n_alive = sN[0];
+    r.log_max = sM[0];
+    r.S0 = sS[0][0];
+    r.S1 = sS[0][1];
+    r.S2 = sS[0][2];
+    r.Q0 = sS[0][3];
+    r.Q1_r2 = sS[0][4];
+    r.Q2_r2 = sS[0][5];
+    r.Q1_rg2 = sS[0][6];
+    r.Q2_rg2 = sS[0][7];
+    if (sN[0] == 0.0) {
+        r.logZ = -INFINITY;
+        r.logZ_norm = -INFINITY;
+        r.mean_r2 = r.se_r2 = r.mean_rg2 = r.se_rg2 = NAN;
+        r.ess = 0.0;
+    } else {
+        r.logZ = r.log_max + log(r.S0 / (double)a.C);
+        r.logZ_norm = a.k > 0 ? r.logZ - (double)(a.N - 1) * log((double)a.k) : r.logZ;
+        const double m1 = r.S1 / r.S0, m2 = r.S2 / r.S0;
+        const double v1 = r.Q2_r2 - 2.0 * m1 * r.Q1_r2 + m1 * m1 * r.Q0;
+        const double v2 = r.Q2_rg2 - 2.0 * m2 * r.Q1_rg2 + m2 * m2 * r.Q0;
+        r.mean_r2 = m1;
+        r.se_r2 = sqrt(v1 > 0.0 ? v1 : 0.0) / r.S0;
+        r.mean_rg2 = m2;
+        r.se_rg2 = sqrt(v2 > 0.0 ? v2 : 0.0) / r.S0;
+        r.ess = r.S0 * r.S0 / r.Q0;
+    }
+    *out = r;
+}
+
+}  // namespace
+
+// Shared with the other translation units that reduce on the device.
+int64_t reduce_tiles(int64_t C) { return (C + kTile - 1) / kTile; }
+
+int reduce_launch(const rosen_reduce_in *in, rosen_stats *out, void *part_ws, cudaStream_t s)
+{
+    ReduceArgs a;
+    memset(&a, 0, sizeof a);
+    a.kind = in->kind;
+    a.N = in->N;
+    a.k = in->k;
+    a.use_counts = in->use_counts;
+    a.C = in->C;
+    a.logw = in->logw;
+    a.counts = reinterpret_cast<const uint4 *>(in->counts);
+    a.r2_i = in->r2_i;
+    a.n2rg2 = in->n2rg2;
+    a.r2_f = in->r2_f;
+    a.rg2_f = in->rg2_f;
+    for (int q = 0; q < 8; ++q) a.logm[q] = q >= 1 ? log((double)q) : 0.0;
+    a.inv_n2 = 1.0 / ((double)in->N * (double)in->N);
+    const int64_t tiles = reduce_tiles(in->C);
+    Partial *part = reinterpret_cast<Partial *>(part_ws);
+    reduce_tiles_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(a, part);
+    reduce_final_kernel<<<1, kFinalThreads, 0, s>>>(part, tiles, a, out);
+    return check_launch("rosen_reduce");
+}
+
+int reduce_validate(const rosen_reduce_in *in, const rosen_stats *out)
+{
+    if (!in || !out) return set_error(ROSEN_EINVAL, "rosen_reduce: NULL input or output");
+    if (in->C < 1) return set_error(ROSEN_EINVAL, "rosen_reduce: C must be >= 1");
+    if (in->N < 1) return set_error(ROSEN_EINVAL, "rosen_reduce: N must be >= 1");
+    if (in->k < 0) return set_error(ROSEN_EINVAL, "rosen_reduce: k must be >= 0");
+    if (in->kind == ROSEN_REDUCE_LATTICE) {
+        if (in->use_counts ? !in->counts : !in->logw)
+            return set_error(ROSEN_EINVAL, "rosen_reduce: missing counts/logw");
+        if (in->use_counts && (reinterpret_cast<uintptr_t>(in->counts) & 15u))
+            return set_error(ROSEN_EINVAL, "rosen_reduce: counts must be 16-byte aligned");
+        if (!in->r2_i || !in->n2rg2)
+            return set_error(ROSEN_EINVAL, "rosen_reduce: lattice needs r2_i and n2rg2");
+    } else if (in->kind == ROSEN_REDUCE_OFFLATTICE) {
+        if (!in->logw || !in->r2_f || !in->rg2_f)
+            return set_error(ROSEN_EINVAL, "rosen_reduce: real space needs logw, r2_f, rg2_f");
+    } else {
+        return set_error(ROSEN_EINVAL, "rosen_reduce: unknown kind %d", in->kind);
+    }
+    return ROSEN_OK;
+}
+
+size_t reduce_workspace_bytes(int64_t C)
+{
+    return (size_t)reduce_tiles(C < 1 ? 1 : C) * sizeof(Partial);
+}
+
+}  // namespace rosen
+
+using namespace rosen;
+
+extern "C" size_t rosen_reduce_workspace_size(int64_t C) { return reduce_workspace_bytes(C); }
+
+extern "C" int rosen_reduce(const rosen_reduce_in *in, rosen_stats *out, void *workspace,
+                            size_t workspace_bytes, void *stream)
+{
+    int st = reduce_validate(in, out);
+    if (st != ROSEN_OK) return st;
+    if (!workspace || workspace_bytes < reduce_workspace_bytes(in->C))
+        return set_error(ROSEN_ENOMEM, "rosen_reduce: workspace of %zu bytes < %zu needed",
+                         workspace_bytes, reduce_workspace_bytes(in->C));
+    if (reinterpret_cast<uintptr_t>(workspace) & 15u)
+        return set_error(ROSEN_EINVAL, "rosen_reduce: workspace must be 16-byte aligned");
+    return reduce_launch(in, out, workspace, (cudaStream_t)stream);
+}

@@ -1,0 +1,199 @@
+"""Thin ctypes binding of librosen.so (include/rosen.h).
+
+Every function here only marshals arguments: PyTorch tensors are passed as
+raw device pointers, PyTorch streams as their cudaStream_t handle, and the
+work runs in the library's CUDA kernels.  There is no fallback: if the
+library is missing or was built without a GPU to run on, calls raise.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+# ---- constants mirrored from rosen.h -------------------------------------
+ROSEN_OK, ROSEN_EINVAL, ROSEN_ENOMEM, ROSEN_ECUDA = 0, 1, 2, 3
+ROSEN_ETIMEOUT, ROSEN_EBUSY, ROSEN_EAGAIN, ROSEN_ECLOSED, ROSEN_ENOTFOUND = 4, 5, 6, 7, 8
+ROSEN_LATTICE_NMAX = 512
+ROSEN_OFFLATTICE_NMAX = 1024
+ROSEN_KMAX = 128
+ROSEN_STORE_TRACE = 1
+ROSEN_STORE_COORDS = 2
+ROSEN_HARD_SPHERE = 0
+ROSEN_LJ = 1
+ROSEN_REDUCE_LATTICE = 0
+ROSEN_REDUCE_OFFLATTICE = 1
+
+STAT_KEYS = ["n", "n_alive", "log_max", "S0", "S1", "S2", "Q0", "Q1_r2", "Q2_r2",
+             "Q1_rg2", "Q2_rg2", "logZ", "logZ_norm", "mean_r2", "se_r2", "mean_rg2",
+             "se_rg2", "ess"]
+
+
+class RosenError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (status_string(status), message))
+        self.status = status
+
+
+_vp = ctypes.c_void_p
+
+
+class rosen_lattice_params(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("ensemble", ctypes.c_uint32),
+                ("N", ctypes.c_int32), ("C", ctypes.c_int64), ("chain0", ctypes.c_int64),
+                ("beta_eps", ctypes.c_double), ("flags", ctypes.c_uint32),
+                ("lanes_per_chain", ctypes.c_int32)]
+
+
+class rosen_lattice_out(ctypes.Structure):
+    _fields_ = [("counts", _vp), ("logw", _vp), ("r2", _vp), ("n2rg2", _vp),
+                ("trace", _vp), ("coords", _vp)]
+
+
+class rosen_reduce_in(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("N", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("use_counts", ctypes.c_int32), ("C", ctypes.c_int64), ("logw", _vp),
+                ("counts", _vp), ("r2_i", _vp), ("n2rg2", _vp), ("r2_f", _vp),
+                ("rg2_f", _vp)]
+
+
+_LIB = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load():
+    """Load librosen.so; raise if it has not been built."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError("librosen.so is not built (%s); run paper_1704_04381_gb300.build.build()"
+                           % path)
+    L = ctypes.CDLL(path)
+    L.rosen_status_string.argtypes = [ctypes.c_int]
+    L.rosen_status_string.restype = ctypes.c_char_p
+    L.rosen_last_error.argtypes = []
+    L.rosen_last_error.restype = ctypes.c_char_p
+    L.rosen_version.argtypes = []
+    L.rosen_version.restype = ctypes.c_char_p
+    L.rosen_philox.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                               ctypes.c_int64, ctypes.c_int64, _vp, _vp]
+    L.rosen_philox.restype = ctypes.c_int
+    L.rosen_lattice_grow.argtypes = [ctypes.POINTER(rosen_lattice_params),
+                                     ctypes.POINTER(rosen_lattice_out), _vp]
+    L.rosen_lattice_grow.restype = ctypes.c_int
+    L.rosen_reduce_workspace_size.argtypes = [ctypes.c_int64]
+    L.rosen_reduce_workspace_size.restype = ctypes.c_size_t
+    L.rosen_reduce.argtypes = [ctypes.POINTER(rosen_reduce_in), _vp, _vp, ctypes.c_size_t, _vp]
+    L.rosen_reduce.restype = ctypes.c_int
+    _LIB = L
+    return L
+
+
+def status_string(status):
+    return load().rosen_status_string(int(status)).decode()
+
+
+def last_error():
+    return load().rosen_last_error().decode()
+
+
+def version():
+    return load().rosen_version().decode()
+
+
+def _check(status):
+    if status != ROSEN_OK:
+        raise RosenError(status, last_error())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError("librosen takes device tensors")
+    if not t.is_contiguous():
+        raise ValueError("librosen takes contiguous tensors")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ---- entry points ----------------------------------------------------------
+def rosen_philox(seed, ensemble, step, slot, chain0, n, out, stream=None):
+    """out [n, 4] uint32 (int32 tensor) <- Philox4x32-10 of counters (chain0+q, ensemble, step, slot)."""
+    _check(load().rosen_philox(int(seed), int(ensemble), int(step), int(slot), int(chain0),
+                               int(n), _ptr(out), _stream(stream)))
+
+
+def rosen_lattice_grow(params, out, stream=None):
+    """Grow lattice chains.  params: rosen_lattice_params; out: dict of tensors."""
+    o = rosen_lattice_out(counts=_ptr(out.get("counts")), logw=_ptr(out.get("logw")),
+                          r2=_ptr(out.get("r2")), n2rg2=_ptr(out.get("n2rg2")),
+                          trace=_ptr(out.get("trace")), coords=_ptr(out.get("coords")))
+    _check(load().rosen_lattice_grow(ctypes.byref(params), ctypes.byref(o), _stream(stream)))
+
+
+def rosen_reduce_workspace_size(C):
+    return int(load().rosen_reduce_workspace_size(int(C)))
+
+
+def rosen_reduce(inp, stats, workspace, stream=None):
+    """Reduce per-chain outputs (rosen_reduce_in built from tensors) into stats [18] float64."""
+    _check(load().rosen_reduce(ctypes.byref(inp), _ptr(stats), _ptr(workspace),
+                               workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+# ---- conveniences (allocation only) ---------------------------------------
+def lattice_params(seed, N, C, beta_eps=0.0, ensemble=0, chain0=0, flags=0, lanes_per_chain=0):
+    return rosen_lattice_params(seed=int(seed), ensemble=int(ensemble), N=int(N), C=int(C),
+                                chain0=int(chain0), beta_eps=float(beta_eps), flags=int(flags),
+                                lanes_per_chain=int(lanes_per_chain))
+
+
+def lattice_outputs(N, C, device="cuda", trace=False, coords=False):
+    """Allocate the per-chain output tensors of rosen_lattice_grow."""
+    out = {
+        "counts": torch.empty((C, 8), dtype=torch.int16, device=device),
+        "logw": torch.empty(C, dtype=torch.float32, device=device),
+        "r2": torch.empty(C, dtype=torch.int32, device=device),
+        "n2rg2": torch.empty(C, dtype=torch.int64, device=device),
+    }
+    if trace:
+        out["trace"] = torch.empty((N - 1, C), dtype=torch.uint8, device=device)
+    if coords:
+        out["coords"] = torch.empty((N, 3, C), dtype=torch.int32, device=device)
+    return out
+
+
+def lattice_reduce_in(out, N, use_counts):
+    C = out["logw"].numel()
+    return rosen_reduce_in(kind=ROSEN_REDUCE_LATTICE, N=int(N), k=0, use_counts=int(use_counts),
+                           C=C, logw=_ptr(out["logw"]), counts=_ptr(out["counts"]),
+                           r2_i=_ptr(out["r2"]), n2rg2=_ptr(out["n2rg2"]), r2_f=None, rg2_f=None)
+
+
+def stats_tensor(device="cuda"):
+    return torch.empty(len(STAT_KEYS), dtype=torch.float64, device=device)
+
+
+def stats_dict(t):
+    return dict(zip(STAT_KEYS, t.detach().cpu().tolist()))
+
+
+def reduce_workspace(C, device="cuda"):
+    nbytes = rosen_reduce_workspace_size(C)
+    return torch.empty((nbytes + 15) // 16 * 2, dtype=torch.float64, device=device)

@@ -1,0 +1,132 @@
+"""Host-side checks of the C ABI (no GPU needed).
+
+- librosen.so builds for sm_103a and exports every function include/rosen.h
+  declares;
+- the ctypes structures of the binding have the C layout;
+- argument validation returns ROSEN_EINVAL / ROSEN_ENOMEM before any CUDA
+  call is made, so it is exercised here without a device.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1704_04381_gb300 import build as pkg_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def rosen():
+    pkg_build.build()
+    from paper_1704_04381_gb300 import rosen as r
+    r.load()
+    return r
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*[A-Za-z_][\w\s\*]*?\b(rosen_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(rosen):
+    names = declared_functions()
+    assert "rosen_lattice_grow" in names and "rosen_reduce" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", rosen.library_path()],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (rosen_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    # Nothing but the ABI leaks out of the library.
+    extra = [n for n in exported if n not in names]
+    assert not extra, extra
+
+
+def test_struct_layout_matches_c(rosen, tmp_path):
+    structs = {
+        "rosen_lattice_params": rosen.rosen_lattice_params,
+        "rosen_lattice_out": rosen.rosen_lattice_out,
+        "rosen_reduce_in": rosen.rosen_reduce_in,
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rosen.h"', "int main(void){"]
+    for name, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for fname, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, fname, name, fname))
+    lines.append('printf("rosen_stats %zu\\n", sizeof(rosen_stats));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                 check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(got["%s.%s" % (name, fname)]) == getattr(cls, fname).offset, (name, fname)
+    assert int(got["rosen_stats"]) == 8 * len(rosen.STAT_KEYS)
+
+
+def _grow(rosen, **kw):
+    p = rosen.lattice_params(**{**dict(seed=1, N=16, C=10), **kw})
+    o = rosen.rosen_lattice_out()
+    return rosen.load().rosen_lattice_grow(ctypes.byref(p), ctypes.byref(o), None)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(N=1), dict(N=513), dict(C=-1), dict(chain0=-5), dict(chain0=2 ** 32 - 5, C=10),
+    dict(beta_eps=-0.1), dict(beta_eps=float("nan")), dict(beta_eps=float("inf")),
+    dict(flags=8), dict(flags=1), dict(flags=2), dict(lanes_per_chain=3),
+])
+def test_lattice_rejects_bad_parameters(rosen, kw):
+    assert _grow(rosen, **kw) == rosen.ROSEN_EINVAL
+    assert rosen.last_error() != ""
+
+
+def test_lattice_empty_launch_is_a_no_op(rosen):
+    assert _grow(rosen, C=0) == rosen.ROSEN_OK
+
+
+def test_misaligned_counts_rejected(rosen):
+    p = rosen.lattice_params(seed=1, N=8, C=4)
+    o = rosen.rosen_lattice_out(counts=8)
+    assert rosen.load().rosen_lattice_grow(ctypes.byref(p), ctypes.byref(o), None) == \
+        rosen.ROSEN_EINVAL
+
+
+def test_reduce_validation(rosen):
+    L = rosen.load()
+    inp = rosen.rosen_reduce_in(kind=rosen.ROSEN_REDUCE_LATTICE, N=8, k=0, use_counts=0, C=0)
+    assert L.rosen_reduce(ctypes.byref(inp), 1024, 2048, 1 << 20, None) == rosen.ROSEN_EINVAL
+    inp.C = 100
+    assert L.rosen_reduce(ctypes.byref(inp), 1024, 2048, 1 << 20, None) == rosen.ROSEN_EINVAL
+    inp.logw, inp.r2_i, inp.n2rg2 = 4096, 8192, 16384
+    need = rosen.rosen_reduce_workspace_size(100)
+    assert need > 0
+    assert L.rosen_reduce(ctypes.byref(inp), 1024, 2048, need - 1, None) == rosen.ROSEN_ENOMEM
+    inp.kind = 7
+    assert L.rosen_reduce(ctypes.byref(inp), 1024, 2048, need, None) == rosen.ROSEN_EINVAL
+    assert rosen.rosen_reduce_workspace_size(10 ** 7) >= (10 ** 7 // 2048) * 96
+
+
+def test_philox_validation(rosen):
+    L = rosen.load()
+    assert L.rosen_philox(1, 0, 0, 0, 2 ** 32 - 1, 2, 4096, None) == rosen.ROSEN_EINVAL
+    assert L.rosen_philox(1, 0, 0, 0, 0, 4, 4100, None) == rosen.ROSEN_EINVAL
+    assert L.rosen_philox(1, 0, 0, 0, 0, 0, None, None) == rosen.ROSEN_OK
+
+
+def test_status_strings(rosen):
+    assert rosen.status_string(rosen.ROSEN_OK) == "ROSEN_OK"
+    assert rosen.status_string(rosen.ROSEN_ETIMEOUT) == "ROSEN_ETIMEOUT"
+    assert "sm_103a" in rosen.version()
