@@ -99,7 +99,8 @@ typedef struct rosen_lattice_params {
 typedef struct rosen_lattice_out {
     uint16_t *counts; /* [C][8] optional: counts[c][m] = steps with m free
                          neighbours (m = 1..6); counts[c][0] = 1 marks a dead
-                         chain (trapped: W = 0).  For beta_eps = 0 the exact
+                         chain (trapped: W = 0; the other entries keep the
+                         steps before the dead end).  For beta_eps = 0 the exact
                          weight is W = prod_m m^counts[c][m].              */
     float *logw;      /* [C] optional: log W, -inf for a dead chain.  FP32
                          sum of FP32 logs (athermal: from the exact counts) */

@@ -229,9 +229,16 @@ __global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a)
         }
     }
 
+    if (dead_at) cnt += 1ull;   // counts[0] = 1 marks the dead end
+    uint32_t cm[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) cm[q] = (uint32_t)(cnt >> (9 * q)) & 511u;
+    if (a.counts)
+        a.counts[c] = make_uint4(cm[0] | (cm[1] << 16), cm[2] | (cm[3] << 16),
+                                 cm[4] | (cm[5] << 16), cm[6]);
     if (dead_at) {
-        // Trapped (Section 3.3.2 restarts such chains; here W = 0 is kept).
-        if (a.counts) a.counts[c] = make_uint4(1u, 0u, 0u, 0u);
+        // Trapped (Section 3.3.2 restarts such chains; here W = 0 is kept and
+        // the counts of the steps before the dead end stay recorded).
         if (a.logw) a.logw[c] = -INFINITY;
         if (a.r2) a.r2[c] = 0;
         if (a.n2rg2) a.n2rg2[c] = 0;
@@ -244,17 +251,11 @@ __global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a)
                 for (int q = 0; q < 3; ++q) a.coords[((int64_t)i * 3 + q) * C + c] = 0;
         return;
     }
-    uint32_t cm[7];
-#pragma unroll
-    for (int q = 0; q < 7; ++q) cm[q] = (uint32_t)(cnt >> (9 * q)) & 511u;
     if (!kIsaw) {
         lw = 0.f;
 #pragma unroll
         for (int q = 2; q <= 6; ++q) lw += (float)cm[q] * a.logm[q];
     }
-    if (a.counts)
-        a.counts[c] = make_uint4(cm[0] | (cm[1] << 16), cm[2] | (cm[3] << 16),
-                                 cm[4] | (cm[5] << 16), cm[6]);
     if (a.logw) a.logw[c] = lw;
     if (a.r2) a.r2[c] = ex * ex + ey * ey + ez * ez;
     if (a.n2rg2)

@@ -1,8 +1,12 @@
 """GPU parity of rosen_reduce with the oracle's FP64 reduction (Eq. 2, Eq. 9).
 
 Both sides reduce the same per-chain inputs; they differ only in the order
-of FP64 additions, so the statistics agree to 1e-12 relative.  The GPU
-result is also deterministic: a second launch is bitwise identical.
+of FP64 additions.  A sum of n non-negative terms carries a relative error of
+at most (n-1) eps (eps = 2^-53) in any order, so sums, their ratios and logZ
+agree within 4 n eps (relative; absolute for logZ).  The standard errors come
+from sum w^2 (A - mean)^2 = Q2 - 2 mean Q1 + mean^2 Q0, whose cancellation
+multiplies that bound by kappa = (Q2 + 2 |mean| Q1 + mean^2 Q0) / variance.
+The GPU result is also deterministic: a second launch is bitwise identical.
 """
 import math
 
@@ -25,14 +29,36 @@ def rosen():
     return r
 
 
-def close(g, o, keys=KEYS, rel=1e-12):
+EPS = 2.0 ** -53
+
+
+def tolerance(o, key):
+    """Relative (absolute for logZ) bound on the order-of-summation difference."""
+    n = max(o["n_alive"], 1.0)
+    base = 4.0 * n * EPS + 1e-15
+    if key in ("se_r2", "se_rg2"):
+        q1, q2 = ("Q1_r2", "Q2_r2") if key == "se_r2" else ("Q1_rg2", "Q2_rg2")
+        m = o["mean_r2"] if key == "se_r2" else o["mean_rg2"]
+        var = (o[key] * o["S0"]) ** 2
+        kappa = (o[q2] + 2 * abs(m) * o[q1] + m * m * o["Q0"]) / var if var > 0 else 1.0
+        return base * max(kappa, 1.0)
+    return base
+
+
+def close(g, o, keys=KEYS):
     for k in keys:
         if isinstance(o[k], float) and math.isnan(o[k]):
             assert math.isnan(g[k]), k
-        elif math.isinf(o[k]):
+        elif math.isinf(o[k]) or k in ("n", "n_alive"):
             assert g[k] == o[k], k
+        elif k == "log_max":
+            # Equal inputs give the same maximum; log W recomputed from counts
+            # may differ by a few ulp between the FMA chain and numpy's sum.
+            assert abs(g[k] - o[k]) <= 8 * EPS * abs(o[k]), (k, g[k], o[k])
+        elif k in ("logZ", "logZ_norm"):
+            assert abs(g[k] - o[k]) <= tolerance(o, k), (k, g[k], o[k])
         else:
-            assert g[k] == pytest.approx(o[k], rel=rel, abs=1e-300), (k, g[k], o[k])
+            assert abs(g[k] - o[k]) <= tolerance(o, k) * abs(o[k]), (k, g[k], o[k])
 
 
 def lattice_case(rosen, seed, N, C, beta_eps):
