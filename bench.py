@@ -1,22 +1,24 @@
 """Benchmark: monomer insertions/s of Rosenbluth chain growth on one GB300.
 
-A step is one pass of the whole hot path over one batch:
+A step is one pass of the whole hot path over one batch of synthetic chains:
   lattice interacting SAW, N = 64, 10^7 chains, beta*eps = 0, 0.2, 0.4
-  (seeds 2, 3, 4): growth of every chain (rosen_lattice_grow) and the FP64
-  ensemble reduction of each ensemble (rosen_reduce).
-value = monomer insertions ((N-1) per chain) per second over the whole job.
+  (seeds 2, 3, 4), and real-space hard spheres, N = 64, k = 32 trial
+  directions, bond = diameter = 1, 10^7 chains (seed 5): growth of every
+  chain (rosen_lattice_grow / rosen_offlattice_grow) and the FP64 ensemble
+  reduction of each ensemble (rosen_reduce).
+value = monomer insertions ((N-1) per chain) per second over the whole step;
+"parts" gives each ensemble's own rate.
 
 Timing: W untimed warm-up steps, then K steps bracketed by a barrier and a
 device synchronize, timed with CUDA events on the launching stream.  The
-per-chain outputs (320 MB per ensemble) exceed the 129 MB L2, and the
-kernels read no inputs, so no L2 flush is needed between steps.
-The dominant kernel is also timed launch by launch (CUDA events on the same
-stream) for the roofline figure.  --impl reference times the FP64 CPU oracle
-instead, on a bounded sample of the same workload.
+kernels read no inputs and the per-chain outputs (160-320 MB per ensemble)
+exceed the 129 MB L2, so no L2 flush is needed between steps.  Every growth
+launch is also timed with its own pair of CUDA events on the same stream for
+the roofline figure.  --impl reference times the FP64 CPU oracle instead, on a
+bounded sample of the same workload.
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -29,17 +31,24 @@ sys.path.insert(0, ROOT)
 
 N = 64
 C = 10_000_000
-BETAS = [(0.0, 2), (0.2, 3), (0.4, 4)]
-WORKLOAD = "lattice ISAW N=64, 1e7 chains x beta*eps {0, 0.2, 0.4}"
+K_TRIALS = 32
+LATTICE = [(0.0, 2), (0.2, 3), (0.4, 4)]
+HS_SEED = 5
+WORKLOAD = ("N=64, 1e7 chains per ensemble: lattice ISAW beta*eps {0, 0.2, 0.4} + "
+            "real-space hard spheres k=32")
 METRIC = "monomer insertions/s at N=64 (lattice & real space) vs roofline; served p50/p99 latency"
 UNIT = "insertions/s"
 
-# Algorithmic integer work of one lattice chain (lane operations): every
-# pair test (an earlier monomer against the chain end) costs 6 operations
-# (add, range test, two shift-or for the table index, table load,
-# accumulate) and every step 100 (Philox4x32-10 at 70, selection and log
-# at 30).  Athermal steps test only monomers of the right parity.
-PAIR_OPS, STEP_OPS = 6, 100
+# Algorithmic work in 32-bit lane operations (the model is stated with the
+# roofline in the design doc):
+#  lattice: 6 per pair test (add, range test, gather multiply, shift, table
+#    load, accumulate), 100 per step (Philox 70, selection and log 30);
+#    athermal steps test only monomers of the matching parity;
+#  real space: 10 per bead scanned for the near list, 4 per pair test
+#    (3 FMA + min) of a listed bead against a trial, 60 per trial per step
+#    (half a Philox call, the direction), 40 per step (selection, commit).
+LAT_PAIR_OPS, LAT_STEP_OPS = 6, 100
+OFF_SCAN_OPS, OFF_PAIR_OPS, OFF_TRIAL_OPS, OFF_STEP_OPS = 10, 4, 60, 40
 
 
 def lattice_pairs(N, athermal):
@@ -49,16 +58,21 @@ def lattice_pairs(N, athermal):
 
 
 def lattice_ops_per_chain(N, athermal):
-    return PAIR_OPS * lattice_pairs(N, athermal) + STEP_OPS * (N - 1)
+    return LAT_PAIR_OPS * lattice_pairs(N, athermal) + LAT_STEP_OPS * (N - 1)
 
 
-def peaks():
+def offlattice_ops(N, k, chains, listed):
+    scanned = chains * (N - 1) * (N - 2) // 2
+    return (OFF_SCAN_OPS * scanned + OFF_PAIR_OPS * k * listed +
+            (OFF_TRIAL_OPS * k + OFF_STEP_OPS) * (N - 1) * chains)
+
+
+def sm_max_mhz():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    sms, mhz = 152, 2070.0
     if os.path.exists(path):
         with open(path) as f:
-            mhz = float(json.load(f).get("sm_max_mhz", mhz))
-    return sms, mhz
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    return 2070.0
 
 
 class ClockSampler:
@@ -77,7 +91,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.reader = threading.Thread(target=self._read, daemon=True)
             self.reader.start()
@@ -126,6 +140,41 @@ def dist_env():
     return rank, world, local
 
 
+class Ensembles:
+    """The step's ensembles: parameters, output tensors, reduction inputs."""
+
+    def __init__(self, rosen, torch, dev, chain0, with_hs=True):
+        self.rosen = rosen
+        self.items = []
+        for b, seed in LATTICE:
+            out = rosen.lattice_outputs(N, C, device=dev)
+            self.items.append({
+                "name": "lattice_beps%.1f" % b, "kind": "lattice", "athermal": b == 0.0,
+                "params": rosen.lattice_params(seed, N, C, beta_eps=b, chain0=chain0),
+                "out": out, "rin": rosen.lattice_reduce_in(out, N, use_counts=int(b == 0.0)),
+                "stats": rosen.stats_tensor(dev)})
+        if with_hs:
+            out = rosen.offlattice_outputs(N, C, device=dev, counters=True)
+            self.items.append({
+                "name": "hard_sphere_k32", "kind": "offlattice",
+                "params": rosen.offlattice_params(HS_SEED, N, C, K_TRIALS, chain0=chain0),
+                "out": out, "rin": rosen.offlattice_reduce_in(out, N, K_TRIALS),
+                "stats": rosen.stats_tensor(dev)})
+        self.ws = rosen.reduce_workspace(C, dev)
+
+    def grow(self, it, stream):
+        if it["kind"] == "lattice":
+            self.rosen.rosen_lattice_grow(it["params"], it["out"], stream)
+        else:
+            self.rosen.rosen_offlattice_grow(it["params"], it["out"], stream)
+
+    def reduce(self, it, stream):
+        self.rosen.rosen_reduce(it["rin"], it["stats"], self.ws, stream)
+
+    def launches_per_step(self):
+        return 3 * len(self.items)     # growth + two reduction kernels each
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -139,35 +188,31 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
-
     stream = torch.cuda.current_stream()
-    # Weak scaling: every rank grows its own C chains (global chain indices
-    # rank*C .. rank*C + C - 1 of each ensemble); no data-path collective.
+    # Weak scaling: every rank grows its own C chains of each ensemble (global
+    # chain indices rank*C .. rank*C + C - 1); no data-path collective.
     chain0 = rank * C
-    outs = [rosen.lattice_outputs(N, C, device=dev) for _ in BETAS]
-    params = [rosen.lattice_params(seed, N, C, beta_eps=b, chain0=chain0) for b, seed in BETAS]
-    stats = [rosen.stats_tensor(dev) for _ in BETAS]
-    ws = rosen.reduce_workspace(C, dev)
-    rins = [rosen.lattice_reduce_in(o, N, use_counts=int(b == 0.0)) for o, (b, _) in zip(outs, BETAS)]
-    launches_per_step = len(BETAS) * 3          # growth + two reduction kernels each
-
+    ens = Ensembles(rosen, torch, dev, chain0, with_hs=not args.lattice_only)
     kernel_ev = []
 
     def step(record=False):
-        for q in range(len(BETAS)):
+        for q, it in enumerate(ens.items):
             if record:
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-            rosen.rosen_lattice_grow(params[q], outs[q], stream)
+            ens.grow(it, stream)
             if record:
                 e1.record(stream)
                 kernel_ev.append((q, e0, e1))
-            rosen.rosen_reduce(rins[q], stats[q], ws, stream)
+            ens.reduce(it, stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    for it in ens.items:
+        if "counters" in it["out"]:
+            it["out"]["counters"].zero_()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -187,27 +232,41 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     ms_per_step = ms / args.steps
-    ins_per_step = len(BETAS) * C * (N - 1) * world
+    ins_per_step = len(ens.items) * C * (N - 1) * world
     value = ins_per_step / (ms_per_step / 1e3)
 
-    # Roofline of the dominant kernel (interacting growth, beta*eps > 0).
-    per_q = {q: [] for q in range(len(BETAS))}
+    per_q = {q: [] for q in range(len(ens.items))}
     for q, e0, e1 in kernel_ev:
         per_q[q].append(e0.elapsed_time(e1))
-    sms, mhz = peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_lane_ops = sms * 128 * mhz * 1e6
-    isaw_ms = statistics.mean(per_q[1] + per_q[2])
-    ath_ms = statistics.mean(per_q[0])
-    achieved = lattice_ops_per_chain(N, False) * C / (isaw_ms / 1e3)
-    parts = {
-        "lattice_athermal_ms": ath_ms,
-        "lattice_isaw_ms": isaw_ms,
-        "lattice_athermal_ins_per_s": C * (N - 1) / (ath_ms / 1e3),
-        "lattice_isaw_ins_per_s": C * (N - 1) / (isaw_ms / 1e3),
-    }
+    mhz = sm_max_mhz()
+    peak = sms * 128 * mhz * 1e6
+    parts = {}
+    rooflines = []
+    for q, it in enumerate(ens.items):
+        kms = statistics.mean(per_q[q])
+        st = rosen.stats_dict(it["stats"])
+        part = {"kernel_ms": kms, "insertions_per_s": C * (N - 1) / (kms / 1e3),
+                "mean_r2": st["mean_r2"], "se_r2": st["se_r2"], "logZ": st["logZ"],
+                "n_alive": st["n_alive"]}
+        if it["kind"] == "lattice":
+            ops = lattice_ops_per_chain(N, it["athermal"]) * C
+            kname = "lattice_lane_kernel<%s>" % ("athermal" if it["athermal"] else "isaw")
+        else:
+            cnt = it["out"]["counters"].cpu().tolist()
+            reps = max(1, args.steps)
+            listed = cnt[2] / reps
+            ops = offlattice_ops(N, K_TRIALS, C, listed)
+            part.update({"fp64_redecided_steps": cnt[0] / reps,
+                         "listed_beads_per_step": listed / (C * (N - 1))})
+            kname = "offlattice_warp_kernel<1>"
+        part["ops_per_chain"] = ops / C
+        parts[it["name"]] = part
+        rooflines.append((kms, ops, kname))
+    kms, ops, kname = max(rooflines)
+    achieved = ops / (kms / 1e3)
 
-    e2e = measure_e2e(args, rosen, torch, dev, stream, chain0, world)
+    e2e = None if args.no_e2e else measure_e2e(args, rosen, torch, dev, stream, chain0, ens)
     if world > 1:
         dist.destroy_process_group()
     if rank != 0:
@@ -215,81 +274,101 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32+fp32",
         "data": "synthetic (Philox-seeded growth; no input data)",
         "config": {"workload": WORKLOAD, "N": N, "chains_per_ensemble": C * world,
-                   "beta_eps": [b for b, _ in BETAS], "seeds": [s for _, s in BETAS],
-                   "l2": "no inputs; outputs 320 MB per ensemble > 129 MB L2, no flush",
+                   "lattice_beta_eps": [b for b, _ in LATTICE], "hs_k": K_TRIALS,
+                   "l2": "no inputs; outputs 160-320 MB per ensemble > 129 MB L2, no flush",
                    "parallelism": "dp%d (chain ranges per GPU)" % world},
         "parts": parts,
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_lane_ops / 1e12,
-                     "unit": "Tops/s (32-bit lane ops)", "frac": achieved / peak_lane_ops,
-                     "traffic": None, "kernel": "lattice_lane_kernel<isaw>",
-                     "ops_per_chain": lattice_ops_per_chain(N, False),
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+                     "unit": "Tops/s (32-bit lane ops)", "frac": achieved / peak,
+                     "traffic": None, "kernel": kname, "ops_per_chain": ops / C,
                      "peak_basis": "%d SMs x 128 lanes x %.0f MHz (max SM clock)" % (sms, mhz)},
         "clocks": clocks.summary(),
         "e2e": e2e,
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": ens.launches_per_step() * args.steps,
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args)
+        line["cpu_baseline"] = cpu_baseline(not args.lattice_only)
     print(json.dumps(line), flush=True)
 
 
-def measure_e2e(args, rosen, torch, dev, stream, chain0, world):
-    """Same metric through the C ABI with host buffers: per step the per-chain
-    outputs (log W, R^2, N^2 R_g^2) and the statistics are copied back to
-    pinned host memory; the only host-to-device input is the parameter block."""
-    outs = [rosen.lattice_outputs(N, C, device=dev) for _ in BETAS]
-    host = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
-             for k, v in o.items() if k != "counts"} for o in outs]
-    stats = [rosen.stats_tensor(dev) for _ in BETAS]
-    hstats = [torch.empty(len(rosen.STAT_KEYS), dtype=torch.float64, pin_memory=True)
-              for _ in BETAS]
-    ws = rosen.reduce_workspace(C, dev)
-    d2h = sum(v.numel() * v.element_size() for h in host for v in h.values()) + \
-        sum(h.numel() * 8 for h in hstats)
-    h2d = len(BETAS) * 48
+def measure_e2e(args, rosen, torch, dev, stream, chain0, ens):
+    """The same metric through the C ABI with host buffers: per step the
+    per-chain results (log W, R^2, R_g^2) and the statistics of every ensemble
+    are copied back to pinned host memory; the only host-to-device input is
+    the parameter block of each call."""
+    host = []
+    d2h = 0
+    for it in ens.items:
+        h = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True)
+             for k, v in it["out"].items() if k in ("logw", "r2", "n2rg2", "rg2")}
+        hs = torch.empty(len(rosen.STAT_KEYS), dtype=torch.float64, pin_memory=True)
+        host.append((h, hs))
+        d2h += sum(v.numel() * v.element_size() for v in h.values()) + hs.numel() * 8
+    h2d = sum(48 if it["kind"] == "lattice" else 72 for it in ens.items)
 
     def step():
-        for q, (b, seed) in enumerate(BETAS):
-            p = rosen.lattice_params(seed, N, C, beta_eps=b, chain0=chain0)
-            rosen.rosen_lattice_grow(p, outs[q], stream)
-            rosen.rosen_reduce(rosen.lattice_reduce_in(outs[q], N, int(b == 0.0)), stats[q], ws,
-                               stream)
-            for k in host[q]:
-                host[q][k].copy_(outs[q][k], non_blocking=True)
-            hstats[q].copy_(stats[q], non_blocking=True)
+        for it, (h, hs) in zip(ens.items, host):
+            ens.grow(it, stream)
+            ens.reduce(it, stream)
+            for k in h:
+                h[k].copy_(it["out"][k], non_blocking=True)
+            hs.copy_(it["stats"], non_blocking=True)
         torch.cuda.synchronize()
 
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, min(args.warmup, 2))):
         step()
     steps = max(1, min(args.steps, 5))
     t0 = time.perf_counter()
     for _ in range(steps):
         step()
     dt = (time.perf_counter() - t0) / steps
-    return {"value": len(BETAS) * C * (N - 1) / dt, "unit": UNIT,
+    return {"value": len(ens.items) * C * (N - 1) / dt, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
-def oracle_sample(threads):
-    """The oracle on a bounded sample: the first S chains of each ensemble."""
+def oracle_rates(with_hs, threads, budget_s):
+    """Oracle insertion rates per ensemble kind on bounded samples."""
     import oracle
-    S = int(os.environ.get("ROSEN_CPU_SAMPLE", "600000"))
-    t0 = time.perf_counter()
-    for b, seed in BETAS:
+    n_lat = int(os.environ.get("ROSEN_CPU_LATTICE_SAMPLE", "0")) or None
+    n_hs = int(os.environ.get("ROSEN_CPU_HS_SAMPLE", "0")) or None
+    rates, notes = {}, []
+    # Calibrate on a small batch, then size the sample to the time budget.
+    for b, seed in LATTICE:
+        t = time.perf_counter()
+        oracle.lattice_run(seed, N, 2000, beta_eps=b, threads=threads)
+        cal = (time.perf_counter() - t) / 2000
+        S = n_lat or max(2000, int(budget_s / (len(LATTICE) + 2) / max(cal, 1e-9)))
+        t = time.perf_counter()
         oracle.lattice_run(seed, N, S, beta_eps=b, threads=threads)
-    dt = time.perf_counter() - t0
-    return len(BETAS) * S * (N - 1) / dt, dt, S
+        dt = time.perf_counter() - t
+        rates["lattice_beps%.1f" % b] = S * (N - 1) / dt
+        notes.append("lattice beta_eps=%.1f: first %d chains (%.1f s)" % (b, S, dt))
+    if with_hs:
+        t = time.perf_counter()
+        oracle.offlattice_run(HS_SEED, N, 200, K_TRIALS, threads=threads)
+        cal = (time.perf_counter() - t) / 200
+        S = n_hs or max(200, int(2 * budget_s / (len(LATTICE) + 2) / max(cal, 1e-9)))
+        t = time.perf_counter()
+        oracle.offlattice_run(HS_SEED, N, S, K_TRIALS, threads=threads)
+        dt = time.perf_counter() - t
+        rates["hard_sphere_k32"] = S * (N - 1) / dt
+        notes.append("hard spheres k=32: first %d chains (%.1f s)" % (S, dt))
+    # The whole step at these rates: total insertions / total time.
+    total_time = sum(C * (N - 1) / r for r in rates.values())
+    value = len(rates) * C * (N - 1) / total_time
+    return value, rates, "; ".join(notes)
 
 
-def cpu_baseline(args):
+def cpu_baseline(with_hs):
     import oracle
     threads = oracle.default_threads()
-    v, dt, S = oracle_sample(threads)
-    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "first %d chains of each of the 3 ensembles (%.1f s)" % (S, dt)}
+    value, rates, note = oracle_rates(with_hs, threads, budget_s=15.0)
+    return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": note + "; value = the full step's insertions over the summed time "
+                             "at these rates", "parts": rates}
 
 
 def run_reference(args):
@@ -299,20 +378,23 @@ def run_reference(args):
     import oracle
     threads = oracle.default_threads()
     for _ in range(args.warmup):
-        pass
-    times = []
-    v = None
+        oracle.lattice_run(2, N, 1000, beta_eps=0.2, threads=threads)
+    vals, times, note = [], [], ""
     for _ in range(max(1, args.steps)):
-        v, dt, S = oracle_sample(threads)
-        times.append(dt)
-    v = len(BETAS) * S * (N - 1) / statistics.mean(times)
+        t = time.perf_counter()
+        v, rates, note = oracle_rates(True, threads, budget_s=max(2.0, 60.0 / max(1, args.steps)))
+        times.append(time.perf_counter() - t)
+        vals.append(v)
+    v = statistics.mean(vals)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * len(LATTICE + [0]) * C * (N - 1) / v,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "N": N},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "N": N,
+                                        "chains_per_ensemble": C, "hs_k": K_TRIALS},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": "first %d chains of each of the 3 ensembles per step" % S},
+                         "sample": "per step: " + note},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -325,9 +407,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--lattice-only", action="store_true")
+    ap.add_argument("--chains", type=int, default=None,
+                    help="chains per ensemble (default 10^7); smaller values are for profiling")
     args = ap.parse_args()
+    if args.chains:
+        global C
+        C = args.chains
     if args.impl == "reference":
-        os.environ.setdefault("ROSEN_CPU_SAMPLE", "200000")
         run_reference(args)
     else:
         run_ours(args)

@@ -131,6 +131,58 @@ typedef struct rosen_lattice_out {
 ROSEN_API int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lattice_out *o,
                        void *stream);
 
+/* ---- real-space growth (Section 3.3.3, Algorithm 2) ------------------- */
+typedef struct rosen_offlattice_params {
+    uint64_t seed;
+    uint32_t ensemble;        /* ensemble id, part of the Philox counter    */
+    int32_t N;                /* beads per chain, 2 <= N <= 1024            */
+    int64_t C;                /* chains, C >= 0                             */
+    int64_t chain0;           /* global index of chain 0; chain0+C <= 2^32  */
+    int32_t k;                /* trial directions per step, 1 <= k <= 128   */
+    int32_t potential;        /* ROSEN_HARD_SPHERE or ROSEN_LJ              */
+    double sigma;             /* bead diameter (HS) / LJ sigma, bond = 1;
+                                 0 <= sigma <= 4 (LJ: sigma > 0)            */
+    double cutoff;            /* LJ truncation radius, 0 < cutoff <= 8      */
+    double beta_eps;          /* LJ well depth over kT, >= 0, finite        */
+    uint32_t flags;           /* ROSEN_STORE_TRACE | ROSEN_STORE_COORDS     */
+    int32_t lanes_per_chain;  /* 0 = automatic; else 32 (one warp/chain)    */
+} rosen_offlattice_params;
+
+typedef struct rosen_offlattice_out {
+    float *logw;       /* [C] optional: log W (sum of log S_i), -inf if dead;
+                          log W - (N-1) log k estimates log of the mean
+                          Boltzmann factor of an ideal chain               */
+    float *r2;         /* [C] optional: R_ee^2                              */
+    float *rg2;        /* [C] optional: R_g^2 about the centre of mass      */
+    uint8_t *alive;    /* [C] optional: 1 = grown to N beads, 0 = dead end  */
+    uint8_t *trace;    /* [N-1][C] optional (needs ROSEN_STORE_TRACE): the
+                          chosen trial of step i at [i-1][c]; 0xFE at the
+                          dead step, 0xFF after it                          */
+    float *coords;     /* [N][3][C] optional (needs ROSEN_STORE_COORDS)     */
+    uint64_t *counters;/* [3] optional, accumulated with atomics (the
+                          caller zeroes them): steps re-decided in FP64,
+                          chains grown, beads listed near the chain end
+                          (each listed bead is tested against all k trials) */
+} rosen_offlattice_out;
+
+/*
+ * Grow chains chain0 .. chain0+C-1 in real space.  Bead 0 is at the origin;
+ * step i draws k unit vectors u_t uniformly on the sphere and scores the
+ * trial positions r_{i-1} + u_t against beads 0..i-2: hard spheres are free
+ * when no bead lies closer than sigma (W *= number of free trials, one free
+ * trial taken uniformly); Lennard-Jones trials get w_t = exp(-beta U_t) with
+ * U_t the sum of 4 eps [(sigma/d)^12 - (sigma/d)^6] over beads with
+ * d < cutoff (W *= sum_t w_t, trial t taken with probability w_t / sum).
+ * Coordinates are FP32 (float-float sums); decisions that FP32 rounding
+ * could flip are re-taken in FP64, so the path equals that of an FP64
+ * implementation of the same rule.
+ * Errors: EINVAL for N outside [2, 1024], k outside [1, 128], bad chain
+ * range, unknown potential, sigma/cutoff/beta_eps out of range, unknown
+ * flags or lanes_per_chain.
+ */
+ROSEN_API int rosen_offlattice_grow(const rosen_offlattice_params *p,
+                                    const rosen_offlattice_out *o, void *stream);
+
 /* ---- ensemble reduction (Eq. 2 with W as weight, Eq. 9) --------------- */
 #define ROSEN_REDUCE_LATTICE 0    /* inputs: counts or logw, r2 (int32), n2rg2 */
 #define ROSEN_REDUCE_OFFLATTICE 1 /* inputs: logw, r2 (float), rg2 (float)     */

@@ -12,11 +12,15 @@
 // with one integer add: t is the packed displacement (dx+2, dy+2, dz+2) and
 // it fits three 3-bit fields exactly when the monomer lies in the 5x5x5 box
 // around the end (|d| <= 511 on every axis keeps the fields from borrowing
-// into each other).  A 512-entry table indexed by those fields turns the
-// displacement into "occupies neighbour d" bits and "touches neighbour d"
-// contact increments, which are simply added (a site holds one monomer, so
-// the occupancy bits never carry).  Parity halves the athermal scan: only
-// monomers j with j = i (mod 2) can sit on a neighbour of the end.
+// into each other).  One multiply by 1 + 2^7 + 2^14 gathers the three fields
+// into bits 14..22 without carries (the partial products below bit 14 sum to
+// less than 2^13), giving a 9-bit index into a 512-entry table that turns
+// the displacement into "occupies neighbour d" bits and "touches neighbour
+// d" contact increments.  Monomers outside the box read the all-zero entry
+// 511, so the scan has no branch; the entries are simply added (a site holds
+// one monomer, so the occupancy bits never carry).  Parity halves the
+// athermal scan: only monomers j with j = i (mod 2) can sit on a neighbour
+// of the end.
 //
 // Selection: athermal steps take the idx-th free neighbour with
 // idx = floor(x * m / 2^32).  Interacting steps draw r = u24(x) * S in FP32
@@ -38,10 +42,15 @@ constexpr uint32_t kOriginKey = 512u | (512u << 10) | (512u << 20);
 constexpr int kLutWords = 512;
 constexpr int kSelBytes = 512;
 
-// Gather the three 3-bit fields of t into a 9-bit table index.
-__device__ __forceinline__ uint32_t lut_index(uint32_t t)
+constexpr uint32_t kGather = (1u << 14) | (1u << 7) | 1u;
+constexpr uint32_t kZeroSlot = 511u;   // fields (7,7,7): outside the box, entry 0
+
+// Table slot of displacement t: its three 3-bit fields as a 9-bit index if
+// the monomer lies in the 5x5x5 box around the end, else the zero entry.
+__device__ __forceinline__ uint32_t lut_slot(uint32_t t)
 {
-    return (t | (t >> 7) | (t >> 14)) & 0x1FFu;
+    const uint32_t idx = ((t * kGather) >> 14) & 0x1FFu;
+    return ((t & ~kFieldMask) == 0u) ? idx : kZeroSlot;
 }
 
 // Table entry for an earlier monomer at displacement d from the chain end.
@@ -76,7 +85,8 @@ __device__ uint8_t nth_set_bit(uint32_t mask, uint32_t idx)
 }
 
 struct LatticeArgs {
-    uint32_t k0, k1, ens, chain0;
+    PhiloxKeys key;
+    uint32_t ens, chain0;
     int32_t N;
     int64_t C;
     float wt32[8];    // exp(beta_eps * c), c = 0..5, rounded to FP32
@@ -165,14 +175,12 @@ __global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a)
         if (kIsaw) {
 #pragma unroll 4
             for (int j = 0; j <= i - 2; ++j) {
-                const uint32_t t = my[j * B] + kb;
-                if ((t & ~kFieldMask) == 0u) acc += lut[lut_index(t)];
+                acc += lut[lut_slot(my[j * B] + kb)];
             }
         } else {
 #pragma unroll 4
             for (int j = i & 1; j <= i - 2; j += 2) {
-                const uint32_t t = my[j * B] + kb;
-                if ((t & ~kFieldMask) == 0u) acc += lut[lut_index(t)];
+                acc += lut[lut_slot(my[j * B] + kb)];
             }
         }
         const uint32_t freem = ~acc & 63u;
@@ -181,7 +189,7 @@ __global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a)
             dead_at = i;
             break;
         }
-        const uint32_t x = philox(make_uint4(chain, a.ens, (uint32_t)i, 0u), a.k0, a.k1).x;
+        const uint32_t x = philox(make_uint4(chain, a.ens, (uint32_t)i, 0u), a.key).x;
         int sel;
         if (!kIsaw) {
             sel = seltab[(freem << 3) | __umulhi(x, (uint32_t)m)];
@@ -310,8 +318,7 @@ extern "C" int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lat
 
     LatticeArgs a;
     memset(&a, 0, sizeof a);
-    a.k0 = (uint32_t)p->seed;
-    a.k1 = (uint32_t)(p->seed >> 32);
+    a.key = philox_keys(p->seed);
     a.ens = p->ensemble;
     a.chain0 = (uint32_t)p->chain0;
     a.N = p->N;

@@ -51,6 +51,19 @@ class rosen_lattice_out(ctypes.Structure):
                 ("trace", _vp), ("coords", _vp)]
 
 
+class rosen_offlattice_params(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("ensemble", ctypes.c_uint32),
+                ("N", ctypes.c_int32), ("C", ctypes.c_int64), ("chain0", ctypes.c_int64),
+                ("k", ctypes.c_int32), ("potential", ctypes.c_int32), ("sigma", ctypes.c_double),
+                ("cutoff", ctypes.c_double), ("beta_eps", ctypes.c_double),
+                ("flags", ctypes.c_uint32), ("lanes_per_chain", ctypes.c_int32)]
+
+
+class rosen_offlattice_out(ctypes.Structure):
+    _fields_ = [("logw", _vp), ("r2", _vp), ("rg2", _vp), ("alive", _vp), ("trace", _vp),
+                ("coords", _vp), ("counters", _vp)]
+
+
 class rosen_reduce_in(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("N", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("use_counts", ctypes.c_int32), ("C", ctypes.c_int64), ("logw", _vp),
@@ -87,6 +100,9 @@ def load():
     L.rosen_lattice_grow.argtypes = [ctypes.POINTER(rosen_lattice_params),
                                      ctypes.POINTER(rosen_lattice_out), _vp]
     L.rosen_lattice_grow.restype = ctypes.c_int
+    L.rosen_offlattice_grow.argtypes = [ctypes.POINTER(rosen_offlattice_params),
+                                        ctypes.POINTER(rosen_offlattice_out), _vp]
+    L.rosen_offlattice_grow.restype = ctypes.c_int
     L.rosen_reduce_workspace_size.argtypes = [ctypes.c_int64]
     L.rosen_reduce_workspace_size.restype = ctypes.c_size_t
     L.rosen_reduce.argtypes = [ctypes.POINTER(rosen_reduce_in), _vp, _vp, ctypes.c_size_t, _vp]
@@ -147,6 +163,15 @@ def rosen_lattice_grow(params, out, stream=None):
     _check(load().rosen_lattice_grow(ctypes.byref(params), ctypes.byref(o), _stream(stream)))
 
 
+def rosen_offlattice_grow(params, out, stream=None):
+    """Grow real-space chains.  params: rosen_offlattice_params; out: dict of tensors."""
+    o = rosen_offlattice_out(logw=_ptr(out.get("logw")), r2=_ptr(out.get("r2")),
+                             rg2=_ptr(out.get("rg2")), alive=_ptr(out.get("alive")),
+                             trace=_ptr(out.get("trace")), coords=_ptr(out.get("coords")),
+                             counters=_ptr(out.get("counters")))
+    _check(load().rosen_offlattice_grow(ctypes.byref(params), ctypes.byref(o), _stream(stream)))
+
+
 def rosen_reduce_workspace_size(C):
     return int(load().rosen_reduce_workspace_size(int(C)))
 
@@ -177,6 +202,39 @@ def lattice_outputs(N, C, device="cuda", trace=False, coords=False):
     if coords:
         out["coords"] = torch.empty((N, 3, C), dtype=torch.int32, device=device)
     return out
+
+
+def offlattice_params(seed, N, C, k, potential=ROSEN_HARD_SPHERE, beta_eps=0.0, sigma=1.0,
+                      cutoff=2.5, ensemble=0, chain0=0, flags=0, lanes_per_chain=0):
+    return rosen_offlattice_params(seed=int(seed), ensemble=int(ensemble), N=int(N), C=int(C),
+                                   chain0=int(chain0), k=int(k), potential=int(potential),
+                                   sigma=float(sigma), cutoff=float(cutoff),
+                                   beta_eps=float(beta_eps), flags=int(flags),
+                                   lanes_per_chain=int(lanes_per_chain))
+
+
+def offlattice_outputs(N, C, device="cuda", trace=False, coords=False, counters=False):
+    """Allocate the per-chain output tensors of rosen_offlattice_grow."""
+    out = {
+        "logw": torch.empty(C, dtype=torch.float32, device=device),
+        "r2": torch.empty(C, dtype=torch.float32, device=device),
+        "rg2": torch.empty(C, dtype=torch.float32, device=device),
+        "alive": torch.empty(C, dtype=torch.uint8, device=device),
+    }
+    if trace:
+        out["trace"] = torch.empty((N - 1, C), dtype=torch.uint8, device=device)
+    if coords:
+        out["coords"] = torch.empty((N, 3, C), dtype=torch.float32, device=device)
+    if counters:
+        out["counters"] = torch.zeros(3, dtype=torch.int64, device=device)
+    return out
+
+
+def offlattice_reduce_in(out, N, k):
+    C = out["logw"].numel()
+    return rosen_reduce_in(kind=ROSEN_REDUCE_OFFLATTICE, N=int(N), k=int(k), use_counts=0, C=C,
+                           logw=_ptr(out["logw"]), counts=None, r2_i=None, n2rg2=None,
+                           r2_f=_ptr(out["r2"]), rg2_f=_ptr(out["rg2"]))
 
 
 def lattice_reduce_in(out, N, use_counts):

@@ -56,6 +56,8 @@ def test_struct_layout_matches_c(rosen, tmp_path):
         "rosen_lattice_params": rosen.rosen_lattice_params,
         "rosen_lattice_out": rosen.rosen_lattice_out,
         "rosen_reduce_in": rosen.rosen_reduce_in,
+        "rosen_offlattice_params": rosen.rosen_offlattice_params,
+        "rosen_offlattice_out": rosen.rosen_offlattice_out,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rosen.h"', "int main(void){"]
     for name, cls in structs.items():
@@ -130,3 +132,25 @@ def test_status_strings(rosen):
     assert rosen.status_string(rosen.ROSEN_OK) == "ROSEN_OK"
     assert rosen.status_string(rosen.ROSEN_ETIMEOUT) == "ROSEN_ETIMEOUT"
     assert "sm_103a" in rosen.version()
+
+
+def _grow_off(rosen, **kw):
+    p = rosen.offlattice_params(**{**dict(seed=1, N=16, C=10, k=32), **kw})
+    o = rosen.rosen_offlattice_out()
+    return rosen.load().rosen_offlattice_grow(ctypes.byref(p), ctypes.byref(o), None)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(N=1), dict(N=1025), dict(k=0), dict(k=129), dict(C=-1), dict(chain0=2 ** 32),
+    dict(potential=2), dict(sigma=-1.0), dict(sigma=float("nan")), dict(sigma=5.0),
+    dict(potential=1, cutoff=0.0), dict(potential=1, cutoff=9.0), dict(potential=1, sigma=0.0),
+    dict(beta_eps=-1.0), dict(beta_eps=float("inf")), dict(flags=4), dict(flags=1),
+    dict(lanes_per_chain=7),
+])
+def test_offlattice_rejects_bad_parameters(rosen, kw):
+    assert _grow_off(rosen, **kw) == rosen.ROSEN_EINVAL
+    assert rosen.last_error() != ""
+
+
+def test_offlattice_empty_launch_is_a_no_op(rosen):
+    assert _grow_off(rosen, C=0) == rosen.ROSEN_OK

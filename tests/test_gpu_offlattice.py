@@ -1,0 +1,151 @@
+"""GPU parity of rosen_offlattice_grow with the FP64 oracle (Algorithm 2).
+
+The GPU keeps coordinates in FP32 (float-float sums of FP32 directions) and
+re-decides in FP64 any step whose FP32 decision lies within its rounding
+bound, so at least 99.9% of chains must take exactly the oracle's path
+(trace equality); in practice all do.  For chains on the same path:
+- log W within (N-1) (2e-6 + 2e-7 |log W|) + the LJ energy rounding term
+  (N-1) * 1e-5 * beta_eps: every step adds one FP32 log (<= 1 ulp), the
+  running-sum rounding (<= 2^-24 |log W|), and for LJ the FP32 rounding of
+  the minimum trial energy (a sum of pair terms each within a few ulp);
+- R_ee^2 and R_g^2 within 2 R (N-1) 4e-7 + 2e-6 R^2: every position carries
+  at most (N-1) times the 4e-7 direction error (the float-float sums add
+  nothing), and the final FP32 sums a few ulp;
+and the ensemble means over all chains agree within 1e-3 relative and
+3 standard errors.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1704_04381_gb300 import build as pkg_build
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rosen():
+    pkg_build.build()
+    from paper_1704_04381_gb300 import rosen as r
+    r.load()
+    return r
+
+
+def grow(rosen, seed, N, C, k, potential=0, beta_eps=0.0, sigma=1.0, cutoff=2.5, chain0=0,
+         ensemble=0, coords=False):
+    flags = rosen.ROSEN_STORE_TRACE | (rosen.ROSEN_STORE_COORDS if coords else 0)
+    out = rosen.offlattice_outputs(N, C, trace=True, coords=coords, counters=True)
+    rosen.rosen_offlattice_grow(
+        rosen.offlattice_params(seed, N, C, k, potential=potential, beta_eps=beta_eps,
+                                sigma=sigma, cutoff=cutoff, chain0=chain0, ensemble=ensemble,
+                                flags=flags), out)
+    torch.cuda.synchronize()
+    return {k_: v.cpu().numpy() for k_, v in out.items()}
+
+
+def compare(g, o, N, beta_eps=0.0, min_same=0.999):
+    same = (g["trace"].T == o["trace"]).all(1)
+    frac = same.mean()
+    assert frac >= min_same, (frac, np.where(~same)[0][:10])
+    s = same
+    assert np.array_equal(g["alive"][s], o["alive"][s])
+    al = s & (o["alive"] == 1)
+    lw = o["logw"][al]
+    tol = (N - 1) * (2e-6 + 2e-7 * np.abs(lw) + 1e-5 * beta_eps)
+    err = np.abs(g["logw"][al].astype(np.float64) - lw)
+    assert (err <= tol).all(), (err.max(), tol[np.argmax(err - tol)])
+    assert np.isneginf(g["logw"][s & (o["alive"] == 0)]).all()
+    for key in ("r2", "rg2"):
+        ref = o[key][al]
+        tol = 2 * np.sqrt(ref) * (N - 1) * 4e-7 + 2e-6 * ref + 1e-7
+        err = np.abs(g[key][al].astype(np.float64) - ref)
+        assert (err <= tol).all(), (key, err.max())
+    return frac
+
+
+def ensemble_close(g, o, N):
+    # W-weighted means over all chains: within 1e-3 relative and 3 SE.
+    res = []
+    for src in (g, o):
+        lw = src["logw"].astype(np.float64)
+        st = oracle.reduce(lw, src["r2"].astype(np.float64), src["rg2"].astype(np.float64), N)
+        res.append(st)
+    for key, se in (("mean_r2", "se_r2"), ("mean_rg2", "se_rg2")):
+        d = abs(res[0][key] - res[1][key])
+        assert d <= 1e-3 * abs(res[1][key]) and d <= 3 * res[1][se] + 1e-12, (key, res)
+
+
+@pytest.mark.parametrize("N,k", [(64, 32), (16, 32), (40, 16), (33, 64), (20, 1), (24, 7),
+                                 (24, 33), (12, 128)])
+def test_hard_sphere_paths(rosen, N, k):
+    C = 3000 if N * k <= 2048 else 1200
+    g = grow(rosen, 5, N, C, k, coords=True)
+    o = oracle.offlattice_run(5, N, C, k, trace=True, coords=True)
+    compare(g, o, N)
+    ensemble_close(g, o, N)
+    # Coordinates of identical paths agree to the FP32 error bound.
+    same = (g["trace"].T == o["trace"]).all(1) & (o["alive"] == 1)
+    xyz = np.transpose(g["coords"], (2, 0, 1))[same].astype(np.float64)
+    assert np.abs(xyz - o["coords"][same]).max() <= (N - 1) * 4e-7 + 1e-6
+
+
+@pytest.mark.parametrize("N,k,beta_eps", [(64, 32, 1.0), (48, 16, 0.5), (30, 64, 0.7),
+                                          (20, 32, 0.0), (16, 8, 1.0)])
+def test_lennard_jones_paths(rosen, N, k, beta_eps):
+    C = 2000
+    g = grow(rosen, 12, N, C, k, potential=1, beta_eps=beta_eps)
+    o = oracle.offlattice_run(12, N, C, k, potential=oracle.LJ, beta_eps=beta_eps, trace=True)
+    compare(g, o, N, beta_eps)
+    ensemble_close(g, o, N)
+
+
+def test_edges_and_offsets(rosen):
+    for N in (2, 3):
+        g = grow(rosen, 8, N, 500, 32, chain0=77_777, ensemble=3)
+        o = oracle.offlattice_run(8, N, 500, 32, chain0=77_777, ensemble=3, trace=True)
+        compare(g, o, N, min_same=1.0)
+    # sigma = 0 is the ideal chain; a wide bead diameter kills chains quickly.
+    g = grow(rosen, 8, 20, 300, 16, sigma=0.0)
+    assert np.allclose(g["logw"], 19 * np.log(16), rtol=1e-6)
+    g = grow(rosen, 8, 20, 300, 16, sigma=1.6)
+    o = oracle.offlattice_run(8, 20, 300, 16, sigma=1.6, trace=True)
+    assert (o["alive"] == 0).any()
+    compare(g, o, 20)
+
+
+def test_longest_chains(rosen):
+    N, C = 1024, 24
+    g = grow(rosen, 3, N, C, 32)
+    o = oracle.offlattice_run(3, N, C, 32, trace=True)
+    compare(g, o, N, min_same=1.0)
+
+
+def test_sharding_is_invisible(rosen):
+    N, C = 32, 2000
+    whole = grow(rosen, 9, N, C, 32, potential=1, beta_eps=0.8)
+    a = grow(rosen, 9, N, 700, 32, potential=1, beta_eps=0.8)
+    b = grow(rosen, 9, N, C - 700, 32, potential=1, beta_eps=0.8, chain0=700)
+    for key in ("logw", "r2", "rg2", "alive"):
+        assert np.array_equal(whole[key], np.concatenate([a[key], b[key]]))
+
+
+def test_full_size_hard_sphere_sampled(rosen):
+    # Real-space hard spheres, N = 64, k = 32, 10^7 chains (one launch).
+    N, C, k = 64, 10_000_000, 32
+    out = rosen.offlattice_outputs(N, C, counters=True)
+    rosen.rosen_offlattice_grow(rosen.offlattice_params(5, N, C, k), out)
+    torch.cuda.synchronize()
+    for lo in (0, C // 3 + 5, C - 1000):
+        hi = min(C, lo + 1000)
+        o = oracle.offlattice_run(5, N, hi - lo, k, chain0=lo)
+        g = {key: v[lo:hi].cpu().numpy() for key, v in out.items() if key != "counters"}
+        assert (g["alive"] == o["alive"]).mean() >= 0.999
+        al = (o["alive"] == 1) & (g["alive"] == 1)
+        lw = o["logw"][al]
+        ok = np.abs(g["logw"][al] - lw) <= (N - 1) * (2e-6 + 2e-7 * np.abs(lw))
+        assert ok.mean() >= 0.999
+    cnt = out["counters"].cpu().numpy()
+    assert cnt[1] == C
+    alive = out["alive"].cpu().numpy()
+    assert 0.99 < alive.mean() < 1.0
