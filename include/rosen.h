@@ -233,6 +233,30 @@ ROSEN_API size_t rosen_reduce_workspace_size(int64_t C);
 ROSEN_API int rosen_reduce(const rosen_reduce_in *in, rosen_stats *out, void *workspace,
                  size_t workspace_bytes, void *stream);
 
+/* ---- reduction without device allocation ---------------------------- */
+/*
+ * No counterpart in the paper: this entry point exists for callers that
+ * cannot allocate device memory themselves -- code running while a CUDA
+ * stream is being captured into a graph (cudaMalloc is not allowed there),
+ * real-time or serving threads that must not take the allocator's implicit
+ * synchronisation, and hosts whose device memory is fully pre-reserved by
+ * another owner.  It is rosen_reduce with its scratch (the per-tile partials)
+ * taken from a fixed array inside librosen instead of a caller workspace:
+ *  - limit: C <= ROSEN_REDUCE_NOALLOC_MAX_CHAINS (2^24 chains, 768 KiB of
+ *    scratch, held by every GPU that loads the library until exit); larger C
+ *    returns ROSEN_ENOMEM and enqueues nothing;
+ *  - the first call on a device looks the scratch address up
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture;
+ *  - every call shares the one array, which keeps the last call's contents;
+ *    nothing in it needs clearing (each call rewrites what it reads), but
+ *    calls whose kernels overlap on the GPU (e.g. on two streams) race;
+ *  - it calls no cudaMalloc, cudaFree or allocating library routine.
+ * Arguments, results and errors are otherwise those of rosen_reduce.
+ */
+#define ROSEN_REDUCE_NOALLOC_MAX_CHAINS (1 << 24)
+ROSEN_API int rosen_reduce_noalloc(const rosen_reduce_in *in, rosen_stats *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,6 +10,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace rosen {
@@ -279,6 +281,65 @@ size_t reduce_workspace_bytes(int64_t C)
 }
 
 }  // namespace rosen
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant.  Its scratch (the per-tile partials) lives in a
+// fixed array in this file; every GPU that loads the library holds it until
+// the process exits.  In host code the array's name is only a stand-in, so
+// the device address is looked up with cudaGetSymbolAddress, once per device
+// (with that device current), on the first call made on it.
+// ---------------------------------------------------------------------------
+namespace rosen {
+namespace {
+
+constexpr int64_t kNoallocTiles = ((int64_t)ROSEN_REDUCE_NOALLOC_MAX_CHAINS + kTile - 1) / kTile;
+static __device__ __align__(256) Partial g_noalloc_partials[kNoallocTiles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+int noalloc_scratch(void **out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return set_error(ROSEN_ECUDA, "rosen_reduce_noalloc: cudaGetDevice: %s",
+                         cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices)
+        return set_error(ROSEN_EINVAL, "rosen_reduce_noalloc: device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+        if (e != cudaSuccess || !p)
+            return set_error(ROSEN_ECUDA, "rosen_reduce_noalloc: cudaGetSymbolAddress: %s",
+                             cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return ROSEN_OK;
+}
+
+}  // namespace
+}  // namespace rosen
+
+extern "C" int rosen_reduce_noalloc(const rosen_reduce_in *in, rosen_stats *out, void *stream)
+{
+    int st = rosen::reduce_validate(in, out);
+    if (st != ROSEN_OK) return st;
+    if (in->C > (int64_t)ROSEN_REDUCE_NOALLOC_MAX_CHAINS)
+        return rosen::set_error(ROSEN_ENOMEM,
+                                "rosen_reduce_noalloc: C = %lld exceeds the built-in scratch "
+                                "limit of %d chains; use rosen_reduce with a workspace",
+                                (long long)in->C, (int)ROSEN_REDUCE_NOALLOC_MAX_CHAINS);
+    void *ws = nullptr;
+    st = rosen::noalloc_scratch(&ws);
+    if (st != ROSEN_OK) return st;
+    // Every partial the final merge reads is rewritten by this call's tile
+    // kernel, so nothing in the shared scratch has to be cleared first.
+    return rosen::reduce_launch(in, out, ws, (cudaStream_t)stream);
+}
 
 using namespace rosen;
 

@@ -107,6 +107,8 @@ def load():
     L.rosen_reduce_workspace_size.restype = ctypes.c_size_t
     L.rosen_reduce.argtypes = [ctypes.POINTER(rosen_reduce_in), _vp, _vp, ctypes.c_size_t, _vp]
     L.rosen_reduce.restype = ctypes.c_int
+    L.rosen_reduce_noalloc.argtypes = [ctypes.POINTER(rosen_reduce_in), _vp, _vp]
+    L.rosen_reduce_noalloc.restype = ctypes.c_int
     _LIB = L
     return L
 
@@ -180,6 +182,15 @@ def rosen_reduce(inp, stats, workspace, stream=None):
     """Reduce per-chain outputs (rosen_reduce_in built from tensors) into stats [18] float64."""
     _check(load().rosen_reduce(ctypes.byref(inp), _ptr(stats), _ptr(workspace),
                                workspace.numel() * workspace.element_size(), _stream(stream)))
+
+
+ROSEN_REDUCE_NOALLOC_MAX_CHAINS = 1 << 24
+
+
+def rosen_reduce_noalloc(inp, stats, stream=None):
+    """rosen_reduce with the library's built-in scratch: for callers that cannot
+    allocate device memory (C <= 2^24; calls that overlap on the GPU race)."""
+    _check(load().rosen_reduce_noalloc(ctypes.byref(inp), _ptr(stats), _stream(stream)))
 
 
 # ---- conveniences (allocation only) ---------------------------------------
