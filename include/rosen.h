@@ -145,7 +145,8 @@ typedef struct rosen_offlattice_params {
     double cutoff;            /* LJ truncation radius, 0 < cutoff <= 8      */
     double beta_eps;          /* LJ well depth over kT, >= 0, finite        */
     uint32_t flags;           /* ROSEN_STORE_TRACE | ROSEN_STORE_COORDS     */
-    int32_t lanes_per_chain;  /* 0 = automatic; else 32 (one warp/chain)    */
+    int32_t lanes_per_chain;  /* 0 = automatic; else 8, 16 or 32 lanes grow
+                                 one chain (k <= 4 * lanes_per_chain)       */
 } rosen_offlattice_params;
 
 typedef struct rosen_offlattice_out {
@@ -182,6 +183,16 @@ typedef struct rosen_offlattice_out {
  */
 ROSEN_API int rosen_offlattice_grow(const rosen_offlattice_params *p,
                                     const rosen_offlattice_out *o, void *stream);
+
+/*
+ * The FP32 unit vectors the real-space kernels use as trial directions
+ * (Algorithm 2's "rngonsphere"): for each pair of words (a, b) = words[2q],
+ * words[2q+1], z = 1 - 2 u24(a), phi = 2 pi u24(b), s = sqrt((1-z)(1+z)),
+ * out[3q..3q+2] = (s cos phi, s sin phi, z).  words: device, 8-byte aligned,
+ * 2n uint32; out: device, 3n floats.  Exposed so the direction error bound
+ * the kernels rely on can be checked exhaustively.
+ */
+ROSEN_API int rosen_sphere_points(const uint32_t *words, int64_t n, float *out, void *stream);
 
 /* ---- ensemble reduction (Eq. 2 with W as weight, Eq. 9) --------------- */
 #define ROSEN_REDUCE_LATTICE 0    /* inputs: counts or logw, r2 (int32), n2rg2 */

@@ -4,24 +4,25 @@
 // a truncated Lennard-Jones energy; W is multiplied by the sum of the trial
 // weights and one trial is drawn in proportion to its weight.
 //
-// GB300 mapping: one warp per chain, lanes = trials (T = k/32 trials per
-// lane beyond 32).  Each step:
-//  1. lanes scan the earlier beads 32 at a time and keep, in ballot order
-//     (ascending bead index), those within 1 + R of the end (R = sigma or
-//     the cutoff); only those can reach a trial.  The kept displacement
+// GB300 mapping: a group of G lanes (G = 8, 16 or 32) grows one chain, so a
+// warp holds 32/G chains; each lane owns T = ceil(k/G) trials.  Each step:
+//  1. the group scans the earlier beads G at a time and keeps, in ballot
+//     order (ascending bead index), those within 1 + R of the end (R = sigma
+//     or the cutoff); only those can reach a trial.  The kept displacement
 //     g = end - r_j and c = 1 + |g|^2 go to a shared list;
-//  2. every lane draws its trial direction u (Philox, 24-bit uniforms) and
-//     evaluates d^2 = |g + u|^2 = c + 2 g.u against the list (three FMAs per
-//     pair, list entries broadcast from shared memory);
-//  3. free flags / weights are combined with ballots and a warp scan, and the
+//  2. every lane draws its trial directions u (Philox, 24-bit uniforms; one
+//     call gives two trials) and evaluates d^2 = |g + u|^2 = c + 2 g.u against
+//     the list (three FMAs per pair, entries broadcast from shared memory);
+//  3. free flags / weights are combined with group ballots and scans, and the
 //     selection draw picks the trial.
 // Positions are float-float (hi + lo) sums of the FP32 directions, so they
 // carry only the directions' own rounding.  Every FP32 decision comes with a
-// bound on its distance from the FP64 result (d^2 within G_i of sigma^2 or
-// of the cutoff, or the selection draw within E of a prefix-sum boundary);
-// when the bound is not met the warp replays the chain's exact positions in
-// FP64 and re-decides the step with the sequential FP64 arithmetic, so the
-// grown path is the one an FP64 implementation of the same rule takes.
+// bound on its distance from the FP64 result (d^2 within G_i of sigma^2 or of
+// the cutoff, or the selection draw within E of a prefix-sum boundary); when
+// the bound is not met the group replays the chain's positions in FP64 from
+// its chosen trials, stores them back (so later steps start from exact
+// positions), and re-decides the step with the sequential FP64 arithmetic of
+// the definition.  The grown path is the one an FP64 implementation takes.
 #include <math.h>
 #include <string.h>
 
@@ -30,78 +31,109 @@
 namespace rosen {
 namespace {
 
-constexpr int kWarp = 32;
+constexpr double kPi = 3.14159265358979323846;
 
 struct OffArgs {
     PhiloxKeys key;
     uint32_t ens, chain0;
-    int32_t N, k, lj;
+    int32_t N, k;
     int64_t C;
-    float sig2, rc2, rf2;      // sigma^2, cutoff^2, list radius^2 (with margin)
+    float sig2, rc2, rf2, rf;  // sigma^2, cutoff^2, list radius^2 (with margin), list radius
     float beta4;               // 4 beta eps (LJ)
-    float band0, band1;        // decision band G_i = band0 + band1 * i on d^2
+    float dband;               // HS: sigma (the distance at which decisions flip); LJ: cutoff
     float ucut2;               // 2 |s^6 (s^6 - 1)| at the cutoff: energy jump (doubled)
     double sig2d, rc2d, beta_eps;
     float *logw, *r2, *rg2;
     uint8_t *alive, *trace;
     float *coords;
-    unsigned long long *counters;   // optional [3]: steps re-decided, chains, list entries
+    unsigned long long *counters;   // optional [3]: steps re-decided, chains, listed beads
 };
 
-// Per-warp shared memory layout (N = chain length).
-struct WarpSmem {
-    float *hx, *hy, *hz, *lx, *ly, *lz;   // float-float positions [N]
-    float4 *nl;                           // near list: g.x, g.y, g.z, 1 + |g|^2
-    int *nj;                              // near list: bead index
-    uint8_t *tr;                          // chosen trial per step
-    double *R;                            // FP64 replay scratch [N][3]
-};
-
-__host__ __device__ inline size_t warp_smem_bytes(int N)
+// Per-chain shared memory: float-float positions, the near list, the trace.
+// Rounded up to 16 bytes so that every chain's float4 arrays stay aligned.
+// (The per-bead band array exists only for Lennard-Jones chains.)
+__host__ __device__ inline size_t chain_smem_bytes(int N, bool lj)
 {
     const size_t n = (size_t)N;
-    size_t b = 0;
-    b += 6 * n * sizeof(float);
-    b = (b + 15) & ~size_t(15);
-    b += n * sizeof(float4) + n * sizeof(int);
-    b += (n + 15) & ~size_t(15);
-    b = (b + 15) & ~size_t(15);
-    b += 3 * n * sizeof(double);
+    const size_t b = 3 * n * sizeof(float4) + n * sizeof(int) + (lj ? n * sizeof(float) : 0) + n;
     return (b + 15) & ~size_t(15);
 }
 
-__device__ inline WarpSmem carve(unsigned char *base, int N)
+struct ChainSmem {
+    float4 *hi, *lo;   // positions (x, y, z, -)
+    float4 *nl;        // near list: g.x, g.y, g.z, 1 + |g|^2
+    int *nj;           // near list: bead index
+    float *nb;         // near list: bound on |d^2 (FP32) - d^2 (FP64)| for this bead
+    uint8_t *tr;       // chosen trial of each step
+};
+
+__device__ inline ChainSmem carve(unsigned char *base, int N, bool lj)
 {
-    WarpSmem w;
-    float *f = reinterpret_cast<float *>(base);
-    w.hx = f;
-    w.hy = f + N;
-    w.hz = f + 2 * N;
-    w.lx = f + 3 * N;
-    w.ly = f + 4 * N;
-    w.lz = f + 5 * N;
-    size_t off = (6 * (size_t)N * sizeof(float) + 15) & ~size_t(15);
-    w.nl = reinterpret_cast<float4 *>(base + off);
-    off += (size_t)N * sizeof(float4);
-    w.nj = reinterpret_cast<int *>(base + off);
-    off += (size_t)N * sizeof(int);
-    w.tr = base + off;
-    off += ((size_t)N + 15) & ~size_t(15);
-    off = (off + 15) & ~size_t(15);
-    w.R = reinterpret_cast<double *>(base + off);
+    ChainSmem w;
+    w.hi = reinterpret_cast<float4 *>(base);
+    w.lo = w.hi + N;
+    w.nl = w.lo + N;
+    w.nj = reinterpret_cast<int *>(w.nl + N);
+    w.nb = reinterpret_cast<float *>(w.nj + N);
+    w.tr = reinterpret_cast<uint8_t *>(lj ? w.nb + N : w.nb);
     return w;
 }
 
+// Bound on |d^2 (FP32) - d^2 (FP64)| for a trial against a listed bead with
+// displacement g (|g| = gn, 1 + |g|^2 = c) whose position drifted for D steps
+// since it was last exact.  d^2 = c + 2 u.g differs from the exact value by
+// 2 (g + u).dg + 2 g.du + rounding, with |du| <= 4e-7 per direction (the
+// exhaustively measured component error is 2.7e-7; z is exact), |dg| <=
+// D 4e-7 + 2.1e-7 |g| (drift plus the rounding of g), |g + u| <= dmax (sigma
+// at the hard-sphere decision, min(1 + |g|, cutoff) for LJ), and three FMA
+// roundings of values up to 2c.  Doubled for safety.
+__device__ __forceinline__ float pair_band(float gn, float c, int D, float dmax)
+{
+    const float dg = (float)D * 4e-7f + 2.1e-7f * gn;
+    return 2.f * (2.f * dmax * dg + 2.f * gn * 4e-7f + 3.6e-7f * c);
+}
+
+// sin and cos of 2 pi V / 2^24 for a 24-bit integer V.  The quarter-turn
+// reduction is exact integer arithmetic: V = q 2^22 + r with r in
+// [-2^21, 2^21), so the angle is q (pi/2) + pi y with y = r / 2^23 exact in
+// FP32 and |y| <= 1/4.  sin(pi y) and cos(pi y) are their Taylor series
+// truncated after y^9 and y^10 (remainders below 2e-9), evaluated by Horner's
+// rule in FP32; the quadrant q only swaps and negates.
+__device__ __forceinline__ void sincos_turn24(uint32_t V, float &sn, float &cs)
+{
+    constexpr float S1 = (float)kPi;
+    constexpr float S3 = (float)(-kPi * kPi * kPi / 6.0);
+    constexpr float S5 = (float)(kPi * kPi * kPi * kPi * kPi / 120.0);
+    constexpr float S7 = (float)(-kPi * kPi * kPi * kPi * kPi * kPi * kPi / 5040.0);
+    constexpr float S9 = (float)(kPi * kPi * kPi * kPi * kPi * kPi * kPi * kPi * kPi / 362880.0);
+    constexpr float C2 = (float)(-kPi * kPi / 2.0);
+    constexpr float C4 = (float)(kPi * kPi * kPi * kPi / 24.0);
+    constexpr float C6 = (float)(-kPi * kPi * kPi * kPi * kPi * kPi / 720.0);
+    constexpr float C8 = (float)(kPi * kPi * kPi * kPi * kPi * kPi * kPi * kPi / 40320.0);
+    constexpr float C10 =
+        (float)(-kPi * kPi * kPi * kPi * kPi * kPi * kPi * kPi * kPi * kPi / 3628800.0);
+    const uint32_t qn = (V + (1u << 21)) >> 22;
+    const int32_t r = (int32_t)V - (int32_t)(qn << 22);
+    const float y = (float)r * 0x1p-23f;
+    const float y2 = y * y;
+    const float ps = fmaf(fmaf(fmaf(fmaf(S9, y2, S7), y2, S5), y2, S3), y2, S1) * y;
+    const float pc = fmaf(fmaf(fmaf(fmaf(fmaf(C10, y2, C8), y2, C6), y2, C4), y2, C2), y2, 1.f);
+    const uint32_t q = qn & 3u;
+    const float a = (q & 1u) ? pc : ps;
+    const float b = (q & 1u) ? ps : pc;
+    sn = (q & 2u) ? -a : a;
+    cs = ((q + 1u) & 2u) ? -b : b;
+}
+
 // Trial direction from two words (the reading of "rngonsphere"):
-// z = 1 - 2 u24(a) and phi = 2 pi u24(b); (1-z), (1+z) and 2 u24(b) are exact
-// in FP32, sincospif is within 1 ulp and sqrtf is correctly rounded, so each
-// component is within 2.7e-7 of the exact direction.
+// z = 1 - 2 u24(a), phi = 2 pi u24(b), s = sqrt((1-z)(1+z)).  (1-z), (1+z) are
+// exact in FP32; sqrtf is correctly rounded.
 __device__ __forceinline__ float3 dir32(uint32_t a, uint32_t b)
 {
     const float z = 1.f - 2.f * u24f(a);
     const float s = sqrtf((1.f - z) * (1.f + z));
     float sn, cs;
-    sincospif(2.f * u24f(b), &sn, &cs);
+    sincos_turn24(b >> 8, sn, cs);
     return make_float3(s * cs, s * sn, z);
 }
 
@@ -133,153 +165,306 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float v)
     lo = t - (hi - s);
 }
 
-__device__ __forceinline__ float warp_min(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
+template <int G>
+struct Group {
+    unsigned mask;   // the group's lanes in the warp
+    int gl;          // lane within the group
+    int base;        // first lane of the group in the warp
 
-__device__ __forceinline__ float warp_sum(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ double warp_min_d(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// FP64 replay of the chain's positions r_0 .. r_{i-1} from the chosen trials:
-// every lane recomputes the FP64 directions of its steps, then a warp scan
-// accumulates them.  Writes R[3*j + axis].
-__device__ __noinline__ void replay_positions(const OffArgs &a, const WarpSmem &w,
-                                              uint32_t chain, int i, int lane)
-{
-    if (lane == 0) {
-        w.R[0] = 0.0;
-        w.R[1] = 0.0;
-        w.R[2] = 0.0;
+    __device__ Group()
+    {
+        const int lane = threadIdx.x & 31;
+        gl = lane & (G - 1);
+        base = lane - gl;
+        mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << base);
     }
+    __device__ unsigned ballot(bool p) const
+    {
+        const unsigned b = __ballot_sync(mask, p);
+        return (G == 32) ? b : (b >> base) & ((1u << G) - 1u);
+    }
+    template <class V>
+    __device__ V bcast(V v, int src) const
+    {
+        return __shfl_sync(mask, v, src, G);
+    }
+    __device__ float min(float v) const
+    {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(mask, v, o, G));
+        return v;
+    }
+    __device__ double min(double v) const
+    {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(mask, v, o, G));
+        return v;
+    }
+    __device__ float max(float v) const
+    {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o, G));
+        return v;
+    }
+    __device__ float sum(float v) const
+    {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
+        return v;
+    }
+    template <class V>
+    __device__ V scan(V v) const   // inclusive prefix sum over the group
+    {
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) {
+            const V u = __shfl_up_sync(mask, v, o, G);
+            if (gl >= o) v += u;
+        }
+        return v;
+    }
+};
+
+// FP64 replay of r_1 .. r_{i-1} from the chosen trials; the exact positions
+// are stored back into the float-float arrays and the end returned.
+template <int G>
+__device__ __noinline__ void replay_positions(const OffArgs &a, const ChainSmem &w,
+                                              const Group<G> &g, uint32_t chain, int i,
+                                              double &ex, double &ey, double &ez)
+{
     double cx = 0.0, cy = 0.0, cz = 0.0;
-    for (int base = 1; base <= i - 1; base += kWarp) {
-        const int s = base + lane;
+    for (int b0 = 1; b0 <= i - 1; b0 += G) {
+        const int s = b0 + g.gl;
         double x = 0.0, y = 0.0, z = 0.0;
         if (s <= i - 1) {
             const int t = w.tr[s];
-            const uint4 q = philox(make_uint4(chain, a.ens, (uint32_t)s, 1u + (uint32_t)(t >> 1)), a.key);
+            const uint4 q =
+                philox(make_uint4(chain, a.ens, (uint32_t)s, 1u + (uint32_t)(t >> 1)), a.key);
             uint32_t wa, wb;
             trial_words(q, t, wa, wb);
             dir64(wa, wb, x, y, z);
         }
-#pragma unroll
-        for (int o = 1; o < kWarp; o <<= 1) {
-            const double px = __shfl_up_sync(0xffffffffu, x, o);
-            const double py = __shfl_up_sync(0xffffffffu, y, o);
-            const double pz = __shfl_up_sync(0xffffffffu, z, o);
-            if (lane >= o) {
-                x += px;
-                y += py;
-                z += pz;
-            }
-        }
-        x += cx;
-        y += cy;
-        z += cz;
+        x = g.scan(x) + cx;
+        y = g.scan(y) + cy;
+        z = g.scan(z) + cz;
         if (s <= i - 1) {
-            w.R[3 * s + 0] = x;
-            w.R[3 * s + 1] = y;
-            w.R[3 * s + 2] = z;
+            const float hx = (float)x, hy = (float)y, hz = (float)z;
+            w.hi[s] = make_float4(hx, hy, hz, 0.f);
+            w.lo[s] = make_float4((float)(x - hx), (float)(y - hy), (float)(z - hz), 0.f);
         }
-        cx = __shfl_sync(0xffffffffu, x, kWarp - 1);
-        cy = __shfl_sync(0xffffffffu, y, kWarp - 1);
-        cz = __shfl_sync(0xffffffffu, z, kWarp - 1);
+        cx = g.bcast(x, G - 1);
+        cy = g.bcast(y, G - 1);
+        cz = g.bcast(z, G - 1);
     }
-    __syncwarp();
+    __syncwarp(g.mask);
+    ex = cx;
+    ey = cy;
+    ez = cz;
 }
 
-template <int T>
-__global__ void __launch_bounds__(256) offlattice_warp_kernel(const OffArgs a, int warps)
+// FP64 re-decision of step i: replay the exact positions, recompute every
+// trial's free flag or energy in FP64 from the listed beads, and select with
+// the sequential FP64 arithmetic of the definition.
+template <int G, int T, bool LJ>
+__device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, const Group<G> &g,
+                                      uint32_t chain, int i, int nn, uint32_t selw,
+                                      const float *logm, float &ehx, float &ehy, float &ehz,
+                                      float &elx, float &ely, float &elz, int &sel, float &logS,
+                                      int &dead_at)
+{
+    const int k = a.k;
+    double ex, ey, ez;
+    replay_positions<G>(a, w, g, chain, i, ex, ey, ez);
+    // The exact end, back into the float-float registers.
+    ehx = (float)ex;
+    elx = (float)(ex - ehx);
+    ehy = (float)ey;
+    ely = (float)(ey - ehy);
+    ehz = (float)ez;
+    elz = (float)(ez - ehz);
+    double val[T];
+#pragma unroll
+    for (int s = 0; s < T; ++s) {
+        const int t = T * g.gl + s;
+        const uint4 xx =
+            philox(make_uint4(chain, a.ens, (uint32_t)i, 1u + (uint32_t)(t >> 1)), a.key);
+        uint32_t wa, wb;
+        trial_words(xx, t, wa, wb);
+        double dx, dy, dz;
+        dir64(wa, wb, dx, dy, dz);
+        const double tx = ex + dx, ty = ey + dy, tz = ez + dz;
+        double acc = 0.0;
+        bool fr = true;
+        for (int q = 0; q < nn; ++q) {
+            const int j = w.nj[q];
+            const float4 h = w.hi[j], l = w.lo[j];
+            const double rx = tx - ((double)h.x + (double)l.x);
+            const double ry = ty - ((double)h.y + (double)l.y);
+            const double rz = tz - ((double)h.z + (double)l.z);
+            const double d2 = rx * rx + ry * ry + rz * rz;
+            if (!LJ) {
+                if (d2 < a.sig2d) fr = false;
+            } else if (d2 < a.rc2d) {
+                const double sr = a.sig2d / d2;
+                const double s3 = sr * sr * sr;
+                acc += 4.0 * s3 * (s3 - 1.0);
+            }
+        }
+        const bool valid = t < k;
+        if (!valid) val[s] = LJ ? INFINITY : 0.0;
+        else if (!LJ) val[s] = fr ? 1.0 : 0.0;
+        else val[s] = (a.beta_eps == 0.0) ? 0.0 : a.beta_eps * acc;
+    }
+    if (!LJ) {
+        int cnt = 0;
+#pragma unroll
+        for (int s = 0; s < T; ++s) cnt += val[s] > 0.0;
+        const int incl = g.scan(cnt);
+        const int m = g.bcast(incl, G - 1);
+        if (m == 0) {
+            dead_at = i;
+        } else {
+            const int idx = (int)__umulhi(selw, (uint32_t)m);
+            int mine = -1, seen = incl - cnt;
+#pragma unroll
+            for (int s = 0; s < T; ++s)
+                if (val[s] > 0.0) {
+                    if (seen == idx) mine = T * g.gl + s;
+                    ++seen;
+                }
+            const unsigned who = g.ballot(mine >= 0);
+            sel = g.bcast(mine, __ffs(who) - 1);
+            logS = logm[m];
+        }
+    } else {
+        double bmin = INFINITY;
+#pragma unroll
+        for (int s = 0; s < T; ++s) bmin = fmin(bmin, val[s]);
+        bmin = g.min(bmin);
+        if (bmin == INFINITY) {
+            dead_at = i;
+        } else {
+            double wv[T];
+#pragma unroll
+            for (int s = 0; s < T; ++s) wv[s] = exp(-(val[s] - bmin));
+            // Sequential FP64 sum and prefix in trial order, as the
+            // definition states them; every lane walks the trials.
+            double S = 0.0, r = 0.0, P = 0.0;
+            int pick = -1, lastpos = -1;
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int t = 0; t < k; ++t) {
+                    double v = 0.0;
+#pragma unroll
+                    for (int s = 0; s < T; ++s)
+                        if (s == t % T) v = wv[s];
+                    v = g.bcast(v, t / T);
+                    if (pass == 0) {
+                        S += v;
+                        if (v > 0.0) lastpos = t;
+                    } else if (pick < 0) {
+                        P += v;
+                        if (P > r) pick = t;
+                    }
+                }
+                if (pass == 0) r = u24d(selw) * S;
+            }
+            sel = pick >= 0 ? pick : lastpos;
+            logS = (float)(log(S) - bmin);
+        }
+    }
+}
+
+template <int G, int T, bool LJ>
+__global__ void __launch_bounds__(256, 4) offlattice_group_kernel(const OffArgs a, int chains_per_block)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    const int64_t c = (int64_t)blockIdx.x * warps + wib;
-    if (c >= a.C) return;     // whole warps leave together
+    float *logm = reinterpret_cast<float *>(smem_raw);          // log m, m = 0..128
+    constexpr int kTable = 132;   // 528 bytes: keeps the per-chain areas 16-byte aligned
+    for (int q = threadIdx.x; q < kTable; q += blockDim.x) logm[q] = q ? logf((float)q) : 0.f;
+    __syncthreads();
+
+    const Group<G> g;
+    const int cib = threadIdx.x / G;
+    const int64_t c = (int64_t)blockIdx.x * chains_per_block + cib;
+    if (c >= a.C) return;     // whole groups leave together
     const int N = a.N, k = a.k;
-    const WarpSmem w = carve(smem_raw + (size_t)wib * warp_smem_bytes(N), N);
+    const ChainSmem w =
+        carve(smem_raw + kTable * sizeof(float) + (size_t)cib * chain_smem_bytes(N, LJ), N, LJ);
     const uint32_t chain = a.chain0 + (uint32_t)c;
 
-    if (lane == 0) {
-        w.hx[0] = w.hy[0] = w.hz[0] = 0.f;
-        w.lx[0] = w.ly[0] = w.lz[0] = 0.f;
+    if (g.gl == 0) {
+        w.hi[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        w.lo[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     float ehx = 0.f, ehy = 0.f, ehz = 0.f, elx = 0.f, ely = 0.f, elz = 0.f;
     float lw = 0.f;
     int dead_at = 0;
+    int exact_upto = 0;   // beads 0..exact_upto are exact (r_0; after a replay at step i: all < i)
     unsigned rechecks = 0;
     unsigned long long listed = 0;
 
     for (int i = 1; i < N; ++i) {
         // ---- 1. near list (ascending bead index) --------------------------
         int nn = 0;
-        for (int base = 0; base <= i - 2; base += kWarp) {
-            const int j = base + lane;
-            float gx = 0.f, gy = 0.f, gz = 0.f, g2 = 0.f;
+        float band = 0.f;    // largest bead band of the step (hard spheres)
+        for (int b0 = 0; b0 <= i - 2; b0 += G) {
+            const int j = b0 + g.gl;
+            float4 L = make_float4(0.f, 0.f, 0.f, 0.f);
             bool near = false;
             if (j <= i - 2) {
-                gx = (ehx - w.hx[j]) + (elx - w.lx[j]);
-                gy = (ehy - w.hy[j]) + (ely - w.ly[j]);
-                gz = (ehz - w.hz[j]) + (elz - w.lz[j]);
-                g2 = gx * gx + gy * gy + gz * gz;
+                const float4 h = w.hi[j], l = w.lo[j];
+                const float gx = (ehx - h.x) + (elx - l.x);
+                const float gy = (ehy - h.y) + (ely - l.y);
+                const float gz = (ehz - h.z) + (elz - l.z);
+                const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+                L = make_float4(gx, gy, gz, 1.f + g2);
                 near = g2 < a.rf2;
             }
-            const unsigned m = __ballot_sync(0xffffffffu, near);
+            const unsigned m = g.ballot(near);
             if (near) {
-                const int slot = nn + __popc(m & ((1u << lane) - 1u));
-                w.nl[slot] = make_float4(gx, gy, gz, 1.f + g2);
+                const int slot = nn + __popc(m & ((1u << g.gl) - 1u));
+                w.nl[slot] = L;
                 w.nj[slot] = j;
+                if (LJ) {
+                    const float gn = sqrtf(L.w - 1.f) * 1.001f + 1e-6f;
+                    w.nb[slot] =
+                        pair_band(gn, L.w, i - 1 - max(j, exact_upto), fminf(1.f + gn, a.dband));
+                }
             }
             nn += __popc(m);
         }
         listed += (unsigned)nn;
-        __syncwarp();
+        __syncwarp(g.mask);
+        if (!LJ && nn > 0) {
+            // One band for the step: the oldest listed bead drifted longest, and
+            // |g| <= sqrt(rf2), c <= 1 + rf2 for every listed bead.
+            const int D = i - 1 - max(w.nj[0], exact_upto);
+            band = pair_band(a.rf, 1.f + a.rf2, D, a.dband);
+        }
 
         // ---- 2. trials ----------------------------------------------------
         float ux[T], uy[T], uz[T];
         bool valid[T];
-        uint32_t selw;
-        {
-            uint4 x;
-            int last_call = -1;
+        uint32_t selw = 0;
+        uint4 x = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-            for (int s = 0; s < T; ++s) {
-                const int t = (T == 1) ? lane : T * lane + s;
-                valid[s] = t < k;
-                const int call = t >> 1;
-                if (call != last_call) {
-                    x = philox(make_uint4(chain, a.ens, (uint32_t)i, 1u + (uint32_t)call), a.key);
-                    last_call = call;
-                }
-                if (s == 0 && lane == 0)
-                    selw = (x.x & 0xFFu) | ((x.y & 0xFFu) << 8) | ((x.z & 0xFFu) << 16) |
-                           ((x.w & 0xFFu) << 24);
-                uint32_t wa, wb;
-                trial_words(x, t, wa, wb);
-                const float3 u = dir32(wa, wb);
-                ux[s] = 2.f * u.x;   // 2u: d^2 = c + (2u).g
-                uy[s] = 2.f * u.y;
-                uz[s] = 2.f * u.z;
-            }
-            selw = __shfl_sync(0xffffffffu, selw, 0);
+        for (int s = 0; s < T; ++s) {
+            const int t = T * g.gl + s;
+            valid[s] = t < k;
+            if (T == 1 || (s & 1) == 0)
+                x = philox(make_uint4(chain, a.ens, (uint32_t)i, 1u + (uint32_t)(t >> 1)), a.key);
+            if (s == 0)
+                selw = (x.x & 0xFFu) | ((x.y & 0xFFu) << 8) | ((x.z & 0xFFu) << 16) |
+                       ((x.w & 0xFFu) << 24);
+            uint32_t wa, wb;
+            trial_words(x, t, wa, wb);
+            const float3 u = dir32(wa, wb);
+            ux[s] = 2.f * u.x;   // 2u: d^2 = c + (2u).g
+            uy[s] = 2.f * u.y;
+            uz[s] = 2.f * u.z;
         }
+        selw = g.bcast(selw, 0);
 
         // ---- 3. pair loop -----------------------------------------------
-        const float G = a.band0 + a.band1 * (float)i;
         float mind[T], U[T], Ub[T], Ua[T];
         int ncut[T];
 #pragma unroll
@@ -290,30 +475,25 @@ __global__ void __launch_bounds__(256) offlattice_warp_kernel(const OffArgs a, i
             Ua[s] = 0.f;
             ncut[s] = 0;
         }
-        if (!a.lj) {
-            for (int q = 0; q < nn; ++q) {
-                const float4 L = w.nl[q];
+#pragma unroll 2
+        for (int q = 0; q < nn; ++q) {
+            const float4 L = w.nl[q];
+            const float bq = LJ ? w.nb[q] : 0.f;
 #pragma unroll
-                for (int s = 0; s < T; ++s) {
-                    const float d2 = fmaf(ux[s], L.x, fmaf(uy[s], L.y, fmaf(uz[s], L.z, L.w)));
+            for (int s = 0; s < T; ++s) {
+                const float d2 = fmaf(ux[s], L.x, fmaf(uy[s], L.y, fmaf(uz[s], L.z, L.w)));
+                if (!LJ) {
                     mind[s] = fminf(mind[s], d2);
-                }
-            }
-        } else {
-            for (int q = 0; q < nn; ++q) {
-                const float4 L = w.nl[q];
-#pragma unroll
-                for (int s = 0; s < T; ++s) {
-                    const float d2 = fmaf(ux[s], L.x, fmaf(uy[s], L.y, fmaf(uz[s], L.z, L.w)));
+                } else {
                     if (d2 < a.rc2) {
-                        const float sr = a.sig2 / d2;
+                        const float sr = __fdividef(a.sig2, d2);
                         const float s3 = sr * sr * sr;
                         const float e = s3 * (s3 - 1.f);
                         U[s] += e;
                         Ua[s] += fabsf(e);
-                        Ub[s] += sr * s3 * fabsf(2.f * s3 - 1.f);
+                        Ub[s] = fmaf(sr * s3, fabsf(2.f * s3 - 1.f) * bq, Ub[s]);
                     }
-                    ncut[s] += fabsf(d2 - a.rc2) < G;
+                    ncut[s] += fabsf(d2 - a.rc2) < bq;
                 }
             }
         }
@@ -322,52 +502,44 @@ __global__ void __launch_bounds__(256) offlattice_warp_kernel(const OffArgs a, i
         int sel = -1;
         float logS = 0.f;
         bool ok = true;
-        if (!a.lj) {
+        if (!LJ) {
             bool fr[T], flag = false;
             int cnt = 0;
 #pragma unroll
             for (int s = 0; s < T; ++s) {
                 fr[s] = valid[s] && mind[s] >= a.sig2;
-                flag |= valid[s] && fabsf(mind[s] - a.sig2) < G;
+                flag |= valid[s] && fabsf(mind[s] - a.sig2) < band;
                 cnt += fr[s];
             }
-            if (__any_sync(0xffffffffu, flag)) {
+            if (g.ballot(flag)) {
                 ok = false;
             } else {
-                // Free trials in trial order: lane-major with T per lane.
-                int pre = cnt;
-#pragma unroll
-                for (int o = 1; o < kWarp; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, pre, o);
-                    if (lane >= o) pre += v;
-                }
-                const int m = __shfl_sync(0xffffffffu, pre, kWarp - 1);
-                pre -= cnt;
+                const int incl = g.scan(cnt);
+                const int m = g.bcast(incl, G - 1);
                 if (m == 0) {
                     dead_at = i;
                 } else {
                     const int idx = (int)__umulhi(selw, (uint32_t)m);
-                    int mine = -1, seen = pre;
+                    int mine = -1, seen = incl - cnt;
 #pragma unroll
                     for (int s = 0; s < T; ++s)
                         if (fr[s]) {
-                            if (seen == idx) mine = (T == 1) ? lane : T * lane + s;
+                            if (seen == idx) mine = T * g.gl + s;
                             ++seen;
                         }
-                    const unsigned who = __ballot_sync(0xffffffffu, mine >= 0);
-                    sel = __shfl_sync(0xffffffffu, mine, __ffs(who) - 1);
-                    logS = logf((float)m);
+                    const unsigned who = g.ballot(mine >= 0);
+                    sel = g.bcast(mine, __ffs(who) - 1);
+                    logS = logm[m];
                 }
             }
         } else {
             float bu[T], bmin = INFINITY;
 #pragma unroll
             for (int s = 0; s < T; ++s) {
-                bu[s] = valid[s] ? a.beta4 * U[s] : INFINITY;
-                if (a.beta4 == 0.f && valid[s]) bu[s] = 0.f;
+                bu[s] = valid[s] ? (a.beta4 == 0.f ? 0.f : a.beta4 * U[s]) : INFINITY;
                 bmin = fminf(bmin, bu[s]);
             }
-            bmin = warp_min(bmin);
+            bmin = g.min(bmin);
             if (bmin == INFINITY) {
                 dead_at = i;
             } else {
@@ -376,46 +548,42 @@ __global__ void __launch_bounds__(256) offlattice_warp_kernel(const OffArgs a, i
                 for (int s = 0; s < T; ++s) {
                     wt[s] = exp2f(-(bu[s] - bmin) * 1.4426950408889634f);
                     own += wt[s];
-                    // |d(bu)/d(d^2)| = 4 beta eps (3 / sigma^2) s^4 |2 s^6 - 1| per pair,
-                    // plus FP32 rounding of the pair terms and the jump of
-                    // pairs that sit within the band of the cutoff; doubled.
-                    const float dbu = a.beta4 * (6.f / a.sig2 * G * Ub[s] + 1e-6f * Ua[s] +
+                    // |d(bu)/d(d^2)| = 4 beta eps (3 / sigma^2) s^4 |2 s^6 - 1| per
+                    // pair, the FP32 rounding of the pair terms, and the jump of
+                    // pairs within the band of the cutoff; doubled.
+                    // (Ub already carries each bead's own band.)  Trials of
+                    // zero weight contribute no error (and would give 0 * inf).
+                    const float dbu = a.beta4 * (6.f / a.sig2 * Ub[s] + 1e-6f * Ua[s] +
                                                  a.ucut2 * (float)ncut[s]);
-                    err += wt[s] * (dbu + 1.2e-7f * (bu[s] - bmin) + 3e-7f);
+                    if (wt[s] > 0.f) err += wt[s] * (dbu + 1.2e-7f * (bu[s] - bmin) + 3e-7f);
                 }
-                float pre = own;
-#pragma unroll
-                for (int o = 1; o < kWarp; o <<= 1) {
-                    const float v = __shfl_up_sync(0xffffffffu, pre, o);
-                    if (lane >= o) pre += v;
-                }
-                const float S = __shfl_sync(0xffffffffu, pre, kWarp - 1);
-                const float E = warp_sum(err) + S * 6e-8f * (float)(k + 2);
+                const float incl = g.scan(own);
+                const float S = g.bcast(incl, G - 1);
+                const float E = g.sum(err) + S * 6e-8f * (float)(k + 2);
                 const float r = u24f(selw) * S;
-                // Inclusive prefix of each of this lane's trials.
-                float P = pre - own;
+                float P = incl - own;
                 int mine = -1;
                 float lo = 0.f, hi = 0.f;
 #pragma unroll
                 for (int s = 0; s < T; ++s) {
                     const float Pn = P + wt[s];
                     if (mine < 0 && Pn > r && wt[s] > 0.f) {
-                        mine = (T == 1) ? lane : T * lane + s;
+                        mine = T * g.gl + s;
                         lo = P;
                         hi = Pn;
                     }
                     P = Pn;
                 }
-                const unsigned who = __ballot_sync(0xffffffffu, mine >= 0);
+                const unsigned who = g.ballot(mine >= 0);
                 if (who == 0u) {
                     ok = false;
                 } else {
                     const int src = __ffs(who) - 1;
-                    sel = __shfl_sync(0xffffffffu, mine, src);
-                    lo = __shfl_sync(0xffffffffu, lo, src);
-                    hi = __shfl_sync(0xffffffffu, hi, src);
+                    sel = g.bcast(mine, src);
+                    lo = g.bcast(lo, src);
+                    hi = g.bcast(hi, src);
                     if (!(r - lo > E) || !(hi - r > E)) ok = false;
-                    logS = logf(S) - bmin;
+                    logS = __logf(S) - bmin;
                 }
             }
         }
@@ -423,115 +591,15 @@ __global__ void __launch_bounds__(256) offlattice_warp_kernel(const OffArgs a, i
         // ---- 5. FP64 re-decision of an ambiguous step -------------------
         if (!ok) {
             ++rechecks;
-            replay_positions(a, w, chain, i, lane);
-            const double ex = w.R[3 * (i - 1)], ey = w.R[3 * (i - 1) + 1], ez = w.R[3 * (i - 1) + 2];
-            double val[T];
-            uint4 x;
-            int last_call = -1;
-#pragma unroll
-            for (int s = 0; s < T; ++s) {
-                const int t = (T == 1) ? lane : T * lane + s;
-                const int call = t >> 1;
-                if (call != last_call) {
-                    x = philox(make_uint4(chain, a.ens, (uint32_t)i, 1u + (uint32_t)call), a.key);
-                    last_call = call;
-                }
-                uint32_t wa, wb;
-                trial_words(x, t, wa, wb);
-                double dx, dy, dz;
-                dir64(wa, wb, dx, dy, dz);
-                const double tx = ex + dx, ty = ey + dy, tz = ez + dz;
-                double acc = 0.0;
-                bool fr = true;
-                for (int q = 0; q < nn; ++q) {
-                    const int j = w.nj[q];
-                    const double rx = tx - w.R[3 * j], ry = ty - w.R[3 * j + 1],
-                                 rz = tz - w.R[3 * j + 2];
-                    const double d2 = rx * rx + ry * ry + rz * rz;
-                    if (!a.lj) {
-                        if (d2 < a.sig2d) fr = false;
-                    } else if (d2 < a.rc2d) {
-                        const double sr = a.sig2d / d2;
-                        const double s3 = sr * sr * sr;
-                        acc += 4.0 * s3 * (s3 - 1.0);
-                    }
-                }
-                if (!valid[s]) val[s] = a.lj ? INFINITY : 0.0;
-                else if (!a.lj) val[s] = fr ? 1.0 : 0.0;
-                else val[s] = (a.beta_eps == 0.0) ? 0.0 : a.beta_eps * acc;
-            }
-            if (!a.lj) {
-                int cnt = 0;
-#pragma unroll
-                for (int s = 0; s < T; ++s) cnt += val[s] > 0.0;
-                int pre = cnt;
-#pragma unroll
-                for (int o = 1; o < kWarp; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, pre, o);
-                    if (lane >= o) pre += v;
-                }
-                const int m = __shfl_sync(0xffffffffu, pre, kWarp - 1);
-                pre -= cnt;
-                if (m == 0) {
-                    dead_at = i;
-                } else {
-                    const int idx = (int)__umulhi(selw, (uint32_t)m);
-                    int mine = -1, seen = pre;
-#pragma unroll
-                    for (int s = 0; s < T; ++s)
-                        if (val[s] > 0.0) {
-                            if (seen == idx) mine = (T == 1) ? lane : T * lane + s;
-                            ++seen;
-                        }
-                    const unsigned who = __ballot_sync(0xffffffffu, mine >= 0);
-                    sel = __shfl_sync(0xffffffffu, mine, __ffs(who) - 1);
-                    logS = logf((float)m);
-                }
-            } else {
-                double bmin = INFINITY;
-#pragma unroll
-                for (int s = 0; s < T; ++s) bmin = fmin(bmin, val[s]);
-                bmin = warp_min_d(bmin);
-                if (bmin == INFINITY) {
-                    dead_at = i;
-                } else {
-                    double wv64[T];
-#pragma unroll
-                    for (int s = 0; s < T; ++s) wv64[s] = exp(-(val[s] - bmin));
-                    // Sequential FP64 sum and prefix in trial order, as the
-                    // definition states them; every lane walks the trials.
-                    double S = 0.0, r = 0.0, P = 0.0;
-                    int pick = -1, lastpos = -1;
-                    for (int pass = 0; pass < 2; ++pass) {
-                        for (int t = 0; t < k; ++t) {
-                            const int src = (T == 1) ? t : t / T;
-                            const int ss = (T == 1) ? 0 : t % T;
-                            double v = 0.0;
-#pragma unroll
-                            for (int s = 0; s < T; ++s)
-                                if (s == ss) v = wv64[s];
-                            const double wv = __shfl_sync(0xffffffffu, v, src);
-                            if (pass == 0) {
-                                S += wv;
-                                if (wv > 0.0) lastpos = t;
-                            } else if (pick < 0) {
-                                P += wv;
-                                if (P > r) pick = t;
-                            }
-                        }
-                        if (pass == 0) r = u24d(selw) * S;
-                    }
-                    sel = pick >= 0 ? pick : lastpos;
-                    logS = (float)(log(S) - bmin);
-                }
-            }
+            redecide<G, T, LJ>(a, w, g, chain, i, nn, selw, logm, ehx, ehy, ehz, elx, ely, elz,
+                               sel, logS, dead_at);
+            exact_upto = i - 1;
         }
         if (dead_at) break;
 
         // ---- 6. commit ----------------------------------------------------
         {
-            const int src = (T == 1) ? sel : sel / T;
-            const int ss = (T == 1) ? 0 : sel % T;
+            const int ss = sel % T;
             float vx = 0.f, vy = 0.f, vz = 0.f;
 #pragma unroll
             for (int s = 0; s < T; ++s)
@@ -540,84 +608,129 @@ __global__ void __launch_bounds__(256) offlattice_warp_kernel(const OffArgs a, i
                     vy = uy[s];
                     vz = uz[s];
                 }
-            vx = 0.5f * __shfl_sync(0xffffffffu, vx, src);
-            vy = 0.5f * __shfl_sync(0xffffffffu, vy, src);
-            vz = 0.5f * __shfl_sync(0xffffffffu, vz, src);
+            const int src = sel / T;
+            vx = 0.5f * g.bcast(vx, src);
+            vy = 0.5f * g.bcast(vy, src);
+            vz = 0.5f * g.bcast(vz, src);
             ff_add(ehx, elx, vx);
             ff_add(ehy, ely, vy);
             ff_add(ehz, elz, vz);
-            if (lane == 0) {
-                w.hx[i] = ehx;
-                w.hy[i] = ehy;
-                w.hz[i] = ehz;
-                w.lx[i] = elx;
-                w.ly[i] = ely;
-                w.lz[i] = elz;
+            if (g.gl == 0) {
+                w.hi[i] = make_float4(ehx, ehy, ehz, 0.f);
+                w.lo[i] = make_float4(elx, ely, elz, 0.f);
                 w.tr[i] = (uint8_t)sel;
             }
             lw += logS;
         }
-        __syncwarp();
+        __syncwarp(g.mask);
     }
 
-    if (a.counters && lane == 0) {
+    if (a.counters && g.gl == 0) {
         if (rechecks) atomicAdd(&a.counters[0], (unsigned long long)rechecks);
         atomicAdd(&a.counters[1], 1ull);
         atomicAdd(&a.counters[2], listed);
     }
     const int64_t C = a.C;
     if (dead_at) {
-        if (lane == 0) {
+        if (g.gl == 0) {
             if (a.logw) a.logw[c] = -INFINITY;
             if (a.r2) a.r2[c] = 0.f;
             if (a.rg2) a.rg2[c] = 0.f;
             if (a.alive) a.alive[c] = 0;
         }
         if (a.trace)
-            for (int s = 1 + lane; s < N; s += kWarp)
+            for (int s = 1 + g.gl; s < N; s += G)
                 a.trace[(int64_t)(s - 1) * C + c] =
                     s < dead_at ? w.tr[s] : (s == dead_at ? 0xFEu : 0xFFu);
         if (a.coords)
-            for (int s = lane; s < N; s += kWarp) {
+            for (int s = g.gl; s < N; s += G) {
                 const bool keep = s < dead_at;
-                a.coords[((int64_t)s * 3 + 0) * C + c] = keep ? w.hx[s] + w.lx[s] : 0.f;
-                a.coords[((int64_t)s * 3 + 1) * C + c] = keep ? w.hy[s] + w.ly[s] : 0.f;
-                a.coords[((int64_t)s * 3 + 2) * C + c] = keep ? w.hz[s] + w.lz[s] : 0.f;
+                const float4 h = w.hi[s], l = w.lo[s];
+                a.coords[((int64_t)s * 3 + 0) * C + c] = keep ? h.x + l.x : 0.f;
+                a.coords[((int64_t)s * 3 + 1) * C + c] = keep ? h.y + l.y : 0.f;
+                a.coords[((int64_t)s * 3 + 2) * C + c] = keep ? h.z + l.z : 0.f;
             }
         return;
     }
     // Observables: R_ee^2 and R_g^2 about the centre of mass.
     float sx = 0.f, sy = 0.f, sz = 0.f;
-    for (int s = lane; s < N; s += kWarp) {
-        sx += w.hx[s] + w.lx[s];
-        sy += w.hy[s] + w.ly[s];
-        sz += w.hz[s] + w.lz[s];
+    for (int s = g.gl; s < N; s += G) {
+        const float4 h = w.hi[s], l = w.lo[s];
+        sx += h.x + l.x;
+        sy += h.y + l.y;
+        sz += h.z + l.z;
     }
     const float inv = 1.f / (float)N;
-    const float mx = warp_sum(sx) * inv, my = warp_sum(sy) * inv, mz = warp_sum(sz) * inv;
-    float g = 0.f;
-    for (int s = lane; s < N; s += kWarp) {
-        const float dx = (w.hx[s] - mx) + w.lx[s];
-        const float dy = (w.hy[s] - my) + w.ly[s];
-        const float dz = (w.hz[s] - mz) + w.lz[s];
-        g += dx * dx + dy * dy + dz * dz;
+    const float mx = g.sum(sx) * inv, my = g.sum(sy) * inv, mz = g.sum(sz) * inv;
+    float gg = 0.f;
+    for (int s = g.gl; s < N; s += G) {
+        const float4 h = w.hi[s], l = w.lo[s];
+        const float dx = (h.x - mx) + l.x, dy = (h.y - my) + l.y, dz = (h.z - mz) + l.z;
+        gg += dx * dx + dy * dy + dz * dz;
     }
-    g = warp_sum(g) * inv;
-    if (lane == 0) {
-        const float x = ehx + elx, y = ehy + ely, z = ehz + elz;
+    gg = g.sum(gg) * inv;
+    if (g.gl == 0) {
+        const float xe = ehx + elx, ye = ehy + ely, ze = ehz + elz;
         if (a.logw) a.logw[c] = lw;
-        if (a.r2) a.r2[c] = x * x + y * y + z * z;
-        if (a.rg2) a.rg2[c] = g;
+        if (a.r2) a.r2[c] = xe * xe + ye * ye + ze * ze;
+        if (a.rg2) a.rg2[c] = gg;
         if (a.alive) a.alive[c] = 1;
     }
     if (a.trace)
-        for (int s = 1 + lane; s < N; s += kWarp) a.trace[(int64_t)(s - 1) * C + c] = w.tr[s];
+        for (int s = 1 + g.gl; s < N; s += G) a.trace[(int64_t)(s - 1) * C + c] = w.tr[s];
     if (a.coords)
-        for (int s = lane; s < N; s += kWarp) {
-            a.coords[((int64_t)s * 3 + 0) * C + c] = w.hx[s] + w.lx[s];
-            a.coords[((int64_t)s * 3 + 1) * C + c] = w.hy[s] + w.ly[s];
-            a.coords[((int64_t)s * 3 + 2) * C + c] = w.hz[s] + w.lz[s];
+        for (int s = g.gl; s < N; s += G) {
+            const float4 h = w.hi[s], l = w.lo[s];
+            a.coords[((int64_t)s * 3 + 0) * C + c] = h.x + l.x;
+            a.coords[((int64_t)s * 3 + 1) * C + c] = h.y + l.y;
+            a.coords[((int64_t)s * 3 + 2) * C + c] = h.z + l.z;
         }
+}
+
+// Directions exactly as the growth kernels compute them (for verification).
+__global__ void sphere_points_kernel(const uint2 *words, int64_t n, float *out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const uint2 v = words[q];
+    const float3 u = dir32(v.x, v.y);
+    out[3 * q + 0] = u.x;
+    out[3 * q + 1] = u.y;
+    out[3 * q + 2] = u.z;
+}
+
+template <int G, int T, bool LJ>
+int launch_one(const OffArgs &a, int N, cudaStream_t s)
+{
+    const size_t per_chain = chain_smem_bytes(N, LJ);
+    if (per_chain % 16 != 0)
+        return set_error(ROSEN_ECUDA, "rosen_offlattice_grow: internal shared-memory layout");
+    int chains = 256 / G;
+    while (chains > 32 / G && (size_t)chains * per_chain > 96 * 1024) chains -= 32 / G;
+    const size_t smem = 132 * sizeof(float) + (size_t)chains * per_chain;
+    const int threads = chains * G;
+    const int64_t blocks = (a.C + chains - 1) / chains;
+    cudaFuncSetAttribute(offlattice_group_kernel<G, T, LJ>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    offlattice_group_kernel<G, T, LJ><<<(unsigned)blocks, threads, smem, s>>>(a, chains);
+    return check_launch("rosen_offlattice_grow");
+}
+
+template <int G, bool LJ>
+int launch_g(const OffArgs &a, int N, int k, cudaStream_t s)
+{
+    const int T = (k + G - 1) / G;
+    if (T <= 1) return launch_one<G, 1, LJ>(a, N, s);
+    if (T <= 2) return launch_one<G, 2, LJ>(a, N, s);
+    return launch_one<G, 4, LJ>(a, N, s);
+}
+
+template <bool LJ>
+int launch_lj(const OffArgs &a, int G, int N, int k, cudaStream_t s)
+{
+    if (G == 8) return launch_g<8, LJ>(a, N, k, s);
+    if (G == 16) return launch_g<16, LJ>(a, N, k, s);
+    return launch_g<32, LJ>(a, N, k, s);
 }
 
 }  // namespace
@@ -651,17 +764,23 @@ int offlattice_validate(const rosen_offlattice_params *p, const rosen_offlattice
         return set_error(ROSEN_EINVAL, "rosen_offlattice_grow: ROSEN_STORE_TRACE without trace");
     if ((p->flags & ROSEN_STORE_COORDS) && !o->coords)
         return set_error(ROSEN_EINVAL, "rosen_offlattice_grow: ROSEN_STORE_COORDS without coords");
-    if (p->lanes_per_chain != 0 && p->lanes_per_chain != 32)
-        return set_error(ROSEN_EINVAL, "rosen_offlattice_grow: lanes_per_chain must be 0 or 32");
+    const int G = p->lanes_per_chain;
+    if (G != 0 && G != 8 && G != 16 && G != 32)
+        return set_error(ROSEN_EINVAL,
+                         "rosen_offlattice_grow: lanes_per_chain must be 0, 8, 16 or 32");
+    if (G != 0 && (p->k + G - 1) / G > 4)
+        return set_error(ROSEN_EINVAL,
+                         "rosen_offlattice_grow: k = %d needs more than 4 trials per lane", p->k);
     return ROSEN_OK;
 }
 
-static int warps_per_block(int N)
+// Default lanes per chain: several chains per warp share the per-step
+// selection and commit work, with at most four trials per lane.
+int offlattice_default_lanes(int k)
 {
-    const size_t budget = 100 * 1024;
-    int W = 8;
-    while (W > 1 && (size_t)W * warp_smem_bytes(N) > budget) --W;
-    return W;
+    if (k <= 16) return 8;
+    if (k <= 64) return 16;
+    return 32;
 }
 
 int offlattice_launch(const rosen_offlattice_params *p, const rosen_offlattice_out *o,
@@ -674,27 +793,22 @@ int offlattice_launch(const rosen_offlattice_params *p, const rosen_offlattice_o
     a.chain0 = (uint32_t)p->chain0;
     a.N = p->N;
     a.k = p->k;
-    a.lj = p->potential == ROSEN_LJ;
     a.C = p->C;
+    const bool lj = p->potential == ROSEN_LJ;
     const double sig = p->sigma;
-    const double R = a.lj ? p->cutoff : sig;
+    const double R = lj ? p->cutoff : sig;
     a.sig2 = (float)(sig * sig);
-    a.rc2 = a.lj ? (float)(p->cutoff * p->cutoff) : 0.f;
+    a.rc2 = lj ? (float)(p->cutoff * p->cutoff) : 0.f;
     a.rf2 = (float)((1.0 + R) * (1.0 + R) * 1.001 + 1e-3);
-    a.beta4 = a.lj ? (float)(4.0 * p->beta_eps) : 0.f;
-    // Decision band: |d^2 (FP32) - d^2 (FP64)| <= 2 (1+R) (i e_u + e_g) + e_eval
-    // with e_u = 4e-7 (per-step direction error), e_g = 4.1e-7 (rounding of g)
-    // and e_eval the three FMA roundings of values up to (1+R)^2; doubled.
-    const double f = 2.0 * (1.0 + R);
-    const double ev = 3.0 * 0.5 * 1.19209290e-7 * (1.0 + R) * (1.0 + R) * 2.0;
-    a.band1 = (float)(2.0 * f * 4e-7);
-    a.band0 = (float)(2.0 * (f * (4e-7 + 4.1e-7) + ev));
-    if (a.lj) {
+    a.rf = (float)sqrt((double)a.rf2 * 1.0001);
+    a.beta4 = lj ? (float)(4.0 * p->beta_eps) : 0.f;
+    a.dband = (float)(lj ? p->cutoff : sig * 1.001);
+    if (lj) {
         const double sc = (sig * sig) / (p->cutoff * p->cutoff), s3 = sc * sc * sc;
         a.ucut2 = (float)(2.0 * fabs(s3 * (s3 - 1.0)));
     }
     a.sig2d = sig * sig;
-    a.rc2d = a.lj ? p->cutoff * p->cutoff : 0.0;
+    a.rc2d = lj ? p->cutoff * p->cutoff : 0.0;
     a.beta_eps = p->beta_eps;
     a.logw = o->logw;
     a.r2 = o->r2;
@@ -703,24 +817,8 @@ int offlattice_launch(const rosen_offlattice_params *p, const rosen_offlattice_o
     a.trace = (p->flags & ROSEN_STORE_TRACE) ? o->trace : nullptr;
     a.coords = (p->flags & ROSEN_STORE_COORDS) ? o->coords : nullptr;
     a.counters = counters;
-
-    const int W = warps_per_block(p->N);
-    const size_t smem = (size_t)W * warp_smem_bytes(p->N);
-    const int64_t blocks = (p->C + W - 1) / W;
-    if (p->k <= 32) {
-        cudaFuncSetAttribute(offlattice_warp_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        offlattice_warp_kernel<1><<<(unsigned)blocks, 32 * W, smem, s>>>(a, W);
-    } else if (p->k <= 64) {
-        cudaFuncSetAttribute(offlattice_warp_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        offlattice_warp_kernel<2><<<(unsigned)blocks, 32 * W, smem, s>>>(a, W);
-    } else {
-        cudaFuncSetAttribute(offlattice_warp_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
-        offlattice_warp_kernel<4><<<(unsigned)blocks, 32 * W, smem, s>>>(a, W);
-    }
-    return check_launch("rosen_offlattice_grow");
+    const int G = p->lanes_per_chain ? p->lanes_per_chain : offlattice_default_lanes(p->k);
+    return lj ? launch_lj<true>(a, G, p->N, p->k, s) : launch_lj<false>(a, G, p->N, p->k, s);
 }
 
 }  // namespace rosen
@@ -735,4 +833,17 @@ extern "C" int rosen_offlattice_grow(const rosen_offlattice_params *p,
     if (p->C == 0) return ROSEN_OK;
     return offlattice_launch(p, o, reinterpret_cast<unsigned long long *>(o->counters),
                              (cudaStream_t)stream);
+}
+
+extern "C" int rosen_sphere_points(const uint32_t *words, int64_t n, float *out, void *stream)
+{
+    if (n < 0) return set_error(ROSEN_EINVAL, "rosen_sphere_points: n < 0");
+    if (n > 0 && (!words || !out)) return set_error(ROSEN_EINVAL, "rosen_sphere_points: NULL");
+    if (reinterpret_cast<uintptr_t>(words) & 7u)
+        return set_error(ROSEN_EINVAL, "rosen_sphere_points: words must be 8-byte aligned");
+    if (n == 0) return ROSEN_OK;
+    const int threads = 256;
+    sphere_points_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0,
+                           (cudaStream_t)stream>>>(reinterpret_cast<const uint2 *>(words), n, out);
+    return check_launch("rosen_sphere_points");
 }

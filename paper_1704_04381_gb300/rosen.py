@@ -103,6 +103,8 @@ def load():
     L.rosen_offlattice_grow.argtypes = [ctypes.POINTER(rosen_offlattice_params),
                                         ctypes.POINTER(rosen_offlattice_out), _vp]
     L.rosen_offlattice_grow.restype = ctypes.c_int
+    L.rosen_sphere_points.argtypes = [_vp, ctypes.c_int64, _vp, _vp]
+    L.rosen_sphere_points.restype = ctypes.c_int
     L.rosen_reduce_workspace_size.argtypes = [ctypes.c_int64]
     L.rosen_reduce_workspace_size.restype = ctypes.c_size_t
     L.rosen_reduce.argtypes = [ctypes.POINTER(rosen_reduce_in), _vp, _vp, ctypes.c_size_t, _vp]
@@ -172,6 +174,12 @@ def rosen_offlattice_grow(params, out, stream=None):
                              trace=_ptr(out.get("trace")), coords=_ptr(out.get("coords")),
                              counters=_ptr(out.get("counters")))
     _check(load().rosen_offlattice_grow(ctypes.byref(params), ctypes.byref(o), _stream(stream)))
+
+
+def rosen_sphere_points(words, out, stream=None):
+    """out [n, 3] float32 <- the kernels' trial directions of word pairs words [n, 2]."""
+    n = words.shape[0]
+    _check(load().rosen_sphere_points(_ptr(words), int(n), _ptr(out), _stream(stream)))
 
 
 def rosen_reduce_workspace_size(C):

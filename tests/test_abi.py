@@ -145,7 +145,7 @@ def _grow_off(rosen, **kw):
     dict(potential=2), dict(sigma=-1.0), dict(sigma=float("nan")), dict(sigma=5.0),
     dict(potential=1, cutoff=0.0), dict(potential=1, cutoff=9.0), dict(potential=1, sigma=0.0),
     dict(beta_eps=-1.0), dict(beta_eps=float("inf")), dict(flags=4), dict(flags=1),
-    dict(lanes_per_chain=7),
+    dict(lanes_per_chain=7), dict(lanes_per_chain=8, k=33),
 ])
 def test_offlattice_rejects_bad_parameters(rosen, kw):
     assert _grow_off(rosen, **kw) == rosen.ROSEN_EINVAL

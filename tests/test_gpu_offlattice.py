@@ -33,13 +33,13 @@ def rosen():
 
 
 def grow(rosen, seed, N, C, k, potential=0, beta_eps=0.0, sigma=1.0, cutoff=2.5, chain0=0,
-         ensemble=0, coords=False):
+         ensemble=0, coords=False, lanes=0):
     flags = rosen.ROSEN_STORE_TRACE | (rosen.ROSEN_STORE_COORDS if coords else 0)
     out = rosen.offlattice_outputs(N, C, trace=True, coords=coords, counters=True)
     rosen.rosen_offlattice_grow(
         rosen.offlattice_params(seed, N, C, k, potential=potential, beta_eps=beta_eps,
                                 sigma=sigma, cutoff=cutoff, chain0=chain0, ensemble=ensemble,
-                                flags=flags), out)
+                                flags=flags, lanes_per_chain=lanes), out)
     torch.cuda.synchronize()
     return {k_: v.cpu().numpy() for k_, v in out.items()}
 
@@ -149,3 +149,13 @@ def test_full_size_hard_sphere_sampled(rosen):
     assert cnt[1] == C
     alive = out["alive"].cpu().numpy()
     assert 0.99 < alive.mean() < 1.0
+
+
+@pytest.mark.parametrize("lanes,k,potential", [(8, 32, 0), (16, 32, 0), (32, 32, 0), (32, 128, 0),
+                                               (8, 16, 1), (32, 16, 1), (16, 64, 1)])
+def test_lane_mappings_agree(rosen, lanes, k, potential):
+    # Every lanes-per-chain mapping grows the same chains as the oracle.
+    N, C = 40, 1500
+    g = grow(rosen, 31, N, C, k, potential=potential, beta_eps=0.6, lanes=lanes)
+    o = oracle.offlattice_run(31, N, C, k, potential=potential, beta_eps=0.6, trace=True)
+    compare(g, o, N, 0.6 if potential else 0.0, min_same=1.0)
