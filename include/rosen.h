@@ -244,6 +244,67 @@ ROSEN_API size_t rosen_reduce_workspace_size(int64_t C);
 ROSEN_API int rosen_reduce(const rosen_reduce_in *in, rosen_stats *out, void *workspace,
                  size_t workspace_bytes, void *stream);
 
+/* ---- batched growth: many ensembles, one graph launch ---------------- */
+#define ROSEN_MODEL_LATTICE 0
+#define ROSEN_MODEL_OFFLATTICE 1
+
+typedef struct rosen_ensemble {
+    int32_t model;       /* ROSEN_MODEL_LATTICE or ROSEN_MODEL_OFFLATTICE        */
+    int32_t N;           /* monomers per chain (lattice <= 512, real <= 1024)    */
+    int64_t C;           /* chains, >= 1; chain indices 0 .. C-1                 */
+    uint64_t seed;
+    uint32_t ensemble;   /* ensemble id, part of the Philox counter              */
+    int32_t k;           /* real space: trial directions per step                */
+    int32_t potential;   /* real space: ROSEN_HARD_SPHERE or ROSEN_LJ            */
+    int32_t reserved;    /* set to 0                                             */
+    double beta_eps;     /* lattice: contact attraction; LJ: well depth / kT     */
+    double sigma;        /* real space: bead diameter / LJ sigma                 */
+    double cutoff;       /* LJ truncation radius                                 */
+} rosen_ensemble;
+
+typedef struct rosen_batch rosen_batch;   /* opaque */
+
+/*
+ * Plan a batch: validate every ensemble (the rules of rosen_lattice_grow /
+ * rosen_offlattice_grow), group them into classes that share a kernel shape,
+ * and allocate (with cudaMalloc, on the current device) the per-chain outputs
+ * of every ensemble, the work queues and the statistics.  The batch owns all
+ * of it until rosen_batch_destroy.  Errors: EINVAL (names the ensemble),
+ * ECUDA.
+ */
+ROSEN_API int rosen_batch_create(const rosen_ensemble *ens, int32_t n, rosen_batch **out);
+/*
+ * Pick each class's kernel shape by timing the candidates on a sample of its
+ * chains (synchronous; writes sample outputs that the next run overwrites),
+ * then capture the whole batch -- persistent growth kernels on forked
+ * streams and the FP64 reduction of every ensemble -- into a CUDA graph.
+ */
+ROSEN_API int rosen_batch_tune(rosen_batch *b, void *stream);
+/* Enqueue one pass over the batch (one graph launch) on stream; tunes and
+ * captures first if that has not happened. */
+ROSEN_API int rosen_batch_run(rosen_batch *b, void *stream);
+/* Device pointer to the batch's statistics, one rosen_stats per ensemble,
+ * valid after a run completes; identical to rosen_reduce of that ensemble
+ * grown alone. */
+ROSEN_API int rosen_batch_stats(rosen_batch *b, rosen_stats **stats);
+/* Device views of ensemble e's per-chain outputs (owned by the batch). */
+ROSEN_API int rosen_batch_lattice_outputs(rosen_batch *b, int32_t e, rosen_lattice_out *out);
+ROSEN_API int rosen_batch_offlattice_outputs(rosen_batch *b, int32_t e, rosen_offlattice_out *out);
+/* Enqueue copies of the statistics (dst: device, n rosen_stats) or of
+ * ensemble e's per-chain outputs (the non-NULL fields of dst, device) on
+ * stream. */
+ROSEN_API int rosen_batch_copy_stats(rosen_batch *b, rosen_stats *dst, void *stream);
+ROSEN_API int rosen_batch_copy_lattice(rosen_batch *b, int32_t e, const rosen_lattice_out *dst,
+                                       void *stream);
+ROSEN_API int rosen_batch_copy_offlattice(rosen_batch *b, int32_t e,
+                                          const rosen_offlattice_out *dst, void *stream);
+/* Enqueue a copy of the real-space counters (see rosen_offlattice_out),
+ * accumulated over every run of the batch, into dst (device, 3 uint64). */
+ROSEN_API int rosen_batch_counters(rosen_batch *b, uint64_t *dst, void *stream);
+/* JSON description of the classes and their (tuned) shapes, into buf. */
+ROSEN_API int rosen_batch_describe(rosen_batch *b, char *buf, size_t len);
+ROSEN_API int rosen_batch_destroy(rosen_batch *b);
+
 /* ---- reduction without device allocation ---------------------------- */
 /*
  * No counterpart in the paper: this entry point exists for callers that

@@ -26,6 +26,21 @@ int check_launch(const char *what)
     return ROSEN_OK;
 }
 
+int max_dynamic_smem()
+{
+    static thread_local int cached_dev = -1, cached = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 48 * 1024;
+    if (dev != cached_dev) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+            v = 48 * 1024;
+        cached = v;
+        cached_dev = dev;
+    }
+    return cached;
+}
+
 __global__ void philox_fill_kernel(uint32_t k0, uint32_t k1, uint32_t ens, uint32_t step,
                                    uint32_t slot, uint32_t chain0, int64_t n, uint4 *out)
 {

@@ -67,10 +67,33 @@ __device__ __forceinline__ uint4 philox(uint4 c, const PhiloxKeys &K)
 __device__ __forceinline__ float u24f(uint32_t x) { return (float)(x >> 8) * 0x1p-24f; }
 __device__ __forceinline__ double u24d(uint32_t x) { return (double)(x >> 8) * 0x1p-24; }
 
+// One unit of work of a persistent batch kernel: chains c0 .. c0+n-1 of
+// ensemble ens.
+struct BatchItem {
+    uint32_t ens;
+    uint32_t n;
+    int64_t c0;
+};
+
 // ---------------------------------------------------------------------------
 // Host-side status helpers (defined in abi.cu).
 // ---------------------------------------------------------------------------
 int set_error(int status, const char *fmt, ...);
 int check_launch(const char *what);
+// Largest dynamic shared memory a block may opt into on the current device.
+int max_dynamic_smem();
+
+// Allow a kernel the device's full opt-in shared memory.  The attribute is a
+// per-function ceiling, so kernels launched with different sizes (or from
+// several threads) never undercut one another.
+template <class F>
+inline cudaError_t allow_max_smem(F *fn)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                max_dynamic_smem() - (int)fa.sharedSizeBytes);
+}
 
 }  // namespace rosen

@@ -32,6 +32,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "internal.cuh"
 
 namespace rosen {
 namespace {
@@ -84,10 +85,18 @@ __device__ uint8_t nth_set_bit(uint32_t mask, uint32_t idx)
     return 0xFFu;
 }
 
+__device__ __forceinline__ void fill_tables(uint32_t *lut, uint8_t *seltab)
+{
+    for (int q = threadIdx.x; q < kLutWords; q += blockDim.x) {
+        lut[q] = lut_entry(q);
+        seltab[q] = nth_set_bit((uint32_t)q >> 3, (uint32_t)q & 7u);
+    }
+}
+
 struct LatticeArgs {
     PhiloxKeys key;
     uint32_t ens, chain0;
-    int32_t N;
+    int32_t N, isaw;
     int64_t C;
     float wt32[8];    // exp(beta_eps * c), c = 0..5, rounded to FP32
     double wt64[8];   // the same in FP64
@@ -128,33 +137,16 @@ __device__ __noinline__ int select_fp64(uint32_t freem, uint32_t acc, uint32_t x
     return sel;
 }
 
+// Grow chain c (local index) of the ensemble described by a, in this lane.
+// my points at the lane's column of the [monomer][lane] key array (stride B).
 template <bool kIsaw>
-__global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a)
+__device__ __forceinline__ void lattice_chain(const LatticeArgs &a, int64_t c, uint32_t *my, int B,
+                                              const uint32_t *lut, const uint8_t *seltab,
+                                              const float *wt32, const double *wt64)
 {
-    extern __shared__ __align__(16) uint32_t smem[];
-    uint32_t *lut = smem;
-    uint8_t *seltab = reinterpret_cast<uint8_t *>(smem + kLutWords);
-    float *wt32 = reinterpret_cast<float *>(smem + kLutWords + kSelBytes / 4);
-    double *wt64 = reinterpret_cast<double *>(smem + kLutWords + kSelBytes / 4 + 8);
-    uint32_t *keys = smem + kLutWords + kSelBytes / 4 + 8 + 16;
-
-    for (int q = threadIdx.x; q < kLutWords; q += blockDim.x) {
-        lut[q] = lut_entry(q);
-        seltab[q] = nth_set_bit((uint32_t)q >> 3, (uint32_t)q & 7u);
-    }
-    if (threadIdx.x < 8) {
-        wt32[threadIdx.x] = a.wt32[threadIdx.x];
-        wt64[threadIdx.x] = a.wt64[threadIdx.x];
-    }
-    __syncthreads();
-
-    const int B = blockDim.x;
-    const int64_t c = (int64_t)blockIdx.x * B + threadIdx.x;
-    if (c >= a.C) return;
     const uint32_t chain = a.chain0 + (uint32_t)c;
     const int N = a.N;
     const int64_t C = a.C;
-    uint32_t *my = keys + threadIdx.x;
 
     uint32_t key = kOriginKey;
     my[0] = key;
@@ -271,12 +263,78 @@ __global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a)
                      ((int64_t)sx * sx + (int64_t)sy * sy + (int64_t)sz * sz);
 }
 
+
+template <bool kIsaw>
+__global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *lut = smem;
+    uint8_t *seltab = reinterpret_cast<uint8_t *>(smem + kLutWords);
+    float *wt32 = reinterpret_cast<float *>(smem + kLutWords + kSelBytes / 4);
+    double *wt64 = reinterpret_cast<double *>(smem + kLutWords + kSelBytes / 4 + 8);
+    uint32_t *keys = smem + kLutWords + kSelBytes / 4 + 8 + 16;
+
+    fill_tables(lut, seltab);
+    if (threadIdx.x < 8) {
+        wt32[threadIdx.x] = a.wt32[threadIdx.x];
+        wt64[threadIdx.x] = a.wt64[threadIdx.x];
+    }
+    __syncthreads();
+
+    const int B = blockDim.x;
+    const int64_t c = (int64_t)blockIdx.x * B + threadIdx.x;
+    if (c >= a.C) return;
+    lattice_chain<kIsaw>(a, c, keys + threadIdx.x, B, lut, seltab, wt32, wt64);
+}
+
+// Persistent batch kernel: blocks take (ensemble, chain range) items from a
+// queue (items sorted by decreasing cost) until it is empty; every chain is
+// grown by the same lattice_chain code as in the single-ensemble kernel, so
+// its results do not depend on the batch it is grown in.
+__global__ void __launch_bounds__(256) lattice_batch_kernel(const LatticeArgs *__restrict__ ens,
+                                                            const BatchItem *__restrict__ items,
+                                                            int n_items, int *head)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ LatticeArgs sa;
+    __shared__ int s_item;
+    uint32_t *lut = smem;
+    uint8_t *seltab = reinterpret_cast<uint8_t *>(smem + kLutWords);
+    float *wt32 = reinterpret_cast<float *>(smem + kLutWords + kSelBytes / 4);
+    double *wt64 = reinterpret_cast<double *>(smem + kLutWords + kSelBytes / 4 + 8);
+    uint32_t *keys = smem + kLutWords + kSelBytes / 4 + 8 + 16;
+    fill_tables(lut, seltab);
+    const int B = blockDim.x;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(head, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const BatchItem bi = items[it];
+        constexpr int kWords = (int)(sizeof(LatticeArgs) / 4);
+        for (int q = threadIdx.x; q < kWords; q += B)
+            reinterpret_cast<uint32_t *>(&sa)[q] = reinterpret_cast<const uint32_t *>(&ens[bi.ens])[q];
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            wt32[threadIdx.x] = sa.wt32[threadIdx.x];
+            wt64[threadIdx.x] = sa.wt64[threadIdx.x];
+        }
+        __syncthreads();
+        if (threadIdx.x < (int)bi.n) {
+            if (sa.isaw)
+                lattice_chain<true>(sa, bi.c0 + threadIdx.x, keys + threadIdx.x, B, lut, seltab,
+                                    wt32, wt64);
+            else
+                lattice_chain<false>(sa, bi.c0 + threadIdx.x, keys + threadIdx.x, B, lut, seltab,
+                                     wt32, wt64);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
-}  // namespace rosen
 
-using namespace rosen;
-
-static size_t lattice_smem_bytes(int N, int B)
+size_t lattice_smem_bytes(int N, int B)
 {
     return (size_t)(kLutWords + kSelBytes / 4 + 8 + 16) * 4 + (size_t)N * B * 4;
 }
@@ -284,7 +342,7 @@ static size_t lattice_smem_bytes(int N, int B)
 // Block size: the largest multiple of 32 (at most 256) whose coordinate
 // tile fits in about half of an SM's shared memory, so that at least two
 // blocks are resident per SM.
-static int lattice_block(int N)
+int lattice_block(int N)
 {
     const size_t budget = 110 * 1024;
     int B = 256;
@@ -292,8 +350,7 @@ static int lattice_block(int N)
     return B;
 }
 
-extern "C" int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lattice_out *o,
-                                  void *stream)
+int lattice_validate(const rosen_lattice_params *p, const rosen_lattice_out *o)
 {
     if (!p || !o) return set_error(ROSEN_EINVAL, "rosen_lattice_grow: NULL params or outputs");
     if (p->N < 2 || p->N > ROSEN_LATTICE_NMAX)
@@ -314,14 +371,21 @@ extern "C" int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lat
         return set_error(ROSEN_EINVAL, "rosen_lattice_grow: ROSEN_STORE_COORDS without coords");
     if (o->counts && (reinterpret_cast<uintptr_t>(o->counts) & 15u))
         return set_error(ROSEN_EINVAL, "rosen_lattice_grow: counts must be 16-byte aligned");
-    if (p->C == 0) return ROSEN_OK;
+    return ROSEN_OK;
+}
 
+size_t lattice_args_size() { return sizeof(LatticeArgs); }
+
+// Kernel arguments of one ensemble (params already validated).
+void lattice_make_args(const rosen_lattice_params *p, const rosen_lattice_out *o, void *out)
+{
     LatticeArgs a;
     memset(&a, 0, sizeof a);
     a.key = philox_keys(p->seed);
     a.ens = p->ensemble;
     a.chain0 = (uint32_t)p->chain0;
     a.N = p->N;
+    a.isaw = p->beta_eps != 0.0;
     a.C = p->C;
     for (int q = 0; q < 8; ++q) {
         a.wt64[q] = exp(p->beta_eps * (double)q);
@@ -334,18 +398,49 @@ extern "C" int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lat
     a.n2rg2 = o->n2rg2;
     a.trace = (p->flags & ROSEN_STORE_TRACE) ? o->trace : nullptr;
     a.coords = (p->flags & ROSEN_STORE_COORDS) ? o->coords : nullptr;
+    memcpy(out, &a, sizeof a);
+}
 
+int lattice_batch_prepare(int B, int Nmax, size_t *smem, int *blocks_per_sm)
+{
+    *smem = lattice_smem_bytes(Nmax, B);
+    cudaError_t e = allow_max_smem(lattice_batch_kernel);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, lattice_batch_kernel, B,
+                                                          *smem);
+    if (e != cudaSuccess)
+        return set_error(ROSEN_ECUDA, "lattice batch set-up: %s", cudaGetErrorString(e));
+    return ROSEN_OK;
+}
+
+void lattice_batch_launch(const void *dev_args, const BatchItem *items, int n_items, int *head,
+                          int B, size_t smem, int grid, cudaStream_t s)
+{
+    lattice_batch_kernel<<<grid, B, smem, s>>>(reinterpret_cast<const LatticeArgs *>(dev_args),
+                                               items, n_items, head);
+}
+
+}  // namespace rosen
+
+using namespace rosen;
+
+extern "C" int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lattice_out *o,
+                                  void *stream)
+{
+    const int st = lattice_validate(p, o);
+    if (st != ROSEN_OK) return st;
+    if (p->C == 0) return ROSEN_OK;
+    LatticeArgs a;
+    lattice_make_args(p, o, &a);
     const int B = lattice_block(p->N);
     const size_t smem = lattice_smem_bytes(p->N, B);
     const int64_t blocks = (p->C + B - 1) / B;
     cudaStream_t s = (cudaStream_t)stream;
     if (p->beta_eps == 0.0) {
-        cudaFuncSetAttribute(lattice_lane_kernel<false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_smem(lattice_lane_kernel<false>);
         lattice_lane_kernel<false><<<(unsigned)blocks, B, smem, s>>>(a);
     } else {
-        cudaFuncSetAttribute(lattice_lane_kernel<true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_smem(lattice_lane_kernel<true>);
         lattice_lane_kernel<true><<<(unsigned)blocks, B, smem, s>>>(a);
     }
     return check_launch("rosen_lattice_grow");

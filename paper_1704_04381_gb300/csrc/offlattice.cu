@@ -27,6 +27,7 @@
 #include <string.h>
 
 #include "common.cuh"
+#include "internal.cuh"
 
 namespace rosen {
 namespace {
@@ -373,22 +374,13 @@ __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, c
     }
 }
 
+// Grow chain c (local index) of the ensemble a with the G lanes of group g,
+// in the per-chain shared memory w.
 template <int G, int T, bool LJ>
-__global__ void __launch_bounds__(256, 4) offlattice_group_kernel(const OffArgs a, int chains_per_block)
+__device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const ChainSmem &w,
+                                          const Group<G> &g, const float *logm)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *logm = reinterpret_cast<float *>(smem_raw);          // log m, m = 0..128
-    constexpr int kTable = 132;   // 528 bytes: keeps the per-chain areas 16-byte aligned
-    for (int q = threadIdx.x; q < kTable; q += blockDim.x) logm[q] = q ? logf((float)q) : 0.f;
-    __syncthreads();
-
-    const Group<G> g;
-    const int cib = threadIdx.x / G;
-    const int64_t c = (int64_t)blockIdx.x * chains_per_block + cib;
-    if (c >= a.C) return;     // whole groups leave together
     const int N = a.N, k = a.k;
-    const ChainSmem w =
-        carve(smem_raw + kTable * sizeof(float) + (size_t)cib * chain_smem_bytes(N, LJ), N, LJ);
     const uint32_t chain = a.chain0 + (uint32_t)c;
 
     if (g.gl == 0) {
@@ -687,6 +679,64 @@ __global__ void __launch_bounds__(256, 4) offlattice_group_kernel(const OffArgs 
         }
 }
 
+
+constexpr int kTable = 132;   // log m, m = 0..131: 528 bytes keep per-chain areas aligned
+
+__device__ __forceinline__ void fill_log_table(float *logm)
+{
+    for (int q = threadIdx.x; q < kTable; q += blockDim.x) logm[q] = q ? logf((float)q) : 0.f;
+}
+
+template <int G, int T, bool LJ>
+__global__ void __launch_bounds__(256, 4) offlattice_group_kernel(const OffArgs a, int chains_per_block)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *logm = reinterpret_cast<float *>(smem_raw);
+    fill_log_table(logm);
+    __syncthreads();
+
+    const Group<G> g;
+    const int cib = threadIdx.x / G;
+    const int64_t c = (int64_t)blockIdx.x * chains_per_block + cib;
+    if (c >= a.C) return;     // whole groups leave together
+    const ChainSmem w = carve(smem_raw + kTable * sizeof(float) +
+                                  (size_t)cib * chain_smem_bytes(a.N, LJ), a.N, LJ);
+    off_chain<G, T, LJ>(a, c, w, g, logm);
+}
+
+// Persistent batch kernel for one (G, T, potential) class: blocks take
+// (ensemble, chain range) items from a queue sorted by decreasing cost; every
+// chain is grown by the same off_chain code as in the single-ensemble kernel.
+template <int G, int T, bool LJ>
+__global__ void __launch_bounds__(256, 4) offlattice_batch_kernel(const OffArgs *__restrict__ ens,
+                                                                  const BatchItem *__restrict__ items,
+                                                                  int n_items, int *head,
+                                                                  int chains_per_block, int Nmax)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ OffArgs sa;
+    __shared__ int s_item;
+    float *logm = reinterpret_cast<float *>(smem_raw);
+    fill_log_table(logm);
+    const Group<G> g;
+    const int cib = threadIdx.x / G;
+    const ChainSmem w = carve(smem_raw + kTable * sizeof(float) +
+                                  (size_t)cib * chain_smem_bytes(Nmax, LJ), Nmax, LJ);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(head, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const BatchItem bi = items[it];
+        constexpr int kWords = (int)(sizeof(OffArgs) / 4);
+        for (int q = threadIdx.x; q < kWords; q += blockDim.x)
+            reinterpret_cast<uint32_t *>(&sa)[q] = reinterpret_cast<const uint32_t *>(&ens[bi.ens])[q];
+        __syncthreads();
+        if (cib < (int)bi.n) off_chain<G, T, LJ>(sa, bi.c0 + cib, w, g, logm);
+        __syncthreads();
+    }
+}
+
 // Directions exactly as the growth kernels compute them (for verification).
 __global__ void sphere_points_kernel(const uint2 *words, int64_t n, float *out)
 {
@@ -699,19 +749,24 @@ __global__ void sphere_points_kernel(const uint2 *words, int64_t n, float *out)
     out[3 * q + 2] = u.z;
 }
 
+// Chains per block: 256 threads, fewer if the chains' shared memory would
+// exceed 96 KB (at least one warp).
+int chains_per_block_for(int G, int N, bool lj)
+{
+    const size_t per_chain = chain_smem_bytes(N, lj);
+    int chains = 256 / G;
+    while (chains > 32 / G && (size_t)chains * per_chain > 96 * 1024) chains -= 32 / G;
+    return chains;
+}
+
 template <int G, int T, bool LJ>
 int launch_one(const OffArgs &a, int N, cudaStream_t s)
 {
-    const size_t per_chain = chain_smem_bytes(N, LJ);
-    if (per_chain % 16 != 0)
-        return set_error(ROSEN_ECUDA, "rosen_offlattice_grow: internal shared-memory layout");
-    int chains = 256 / G;
-    while (chains > 32 / G && (size_t)chains * per_chain > 96 * 1024) chains -= 32 / G;
-    const size_t smem = 132 * sizeof(float) + (size_t)chains * per_chain;
+    const int chains = chains_per_block_for(G, N, LJ);
+    const size_t smem = kTable * sizeof(float) + (size_t)chains * chain_smem_bytes(N, LJ);
     const int threads = chains * G;
     const int64_t blocks = (a.C + chains - 1) / chains;
-    cudaFuncSetAttribute(offlattice_group_kernel<G, T, LJ>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem(offlattice_group_kernel<G, T, LJ>);
     offlattice_group_kernel<G, T, LJ><<<(unsigned)blocks, threads, smem, s>>>(a, chains);
     return check_launch("rosen_offlattice_grow");
 }
@@ -731,6 +786,26 @@ int launch_lj(const OffArgs &a, int G, int N, int k, cudaStream_t s)
     if (G == 8) return launch_g<8, LJ>(a, N, k, s);
     if (G == 16) return launch_g<16, LJ>(a, N, k, s);
     return launch_g<32, LJ>(a, N, k, s);
+}
+
+// The batch kernel of class (G, T, LJ) through one function pointer type.
+using BatchFn = void (*)(const OffArgs *, const BatchItem *, int, int *, int, int);
+
+template <int G, int T, bool LJ>
+BatchFn batch_fn()
+{
+    return offlattice_batch_kernel<G, T, LJ>;
+}
+
+BatchFn pick_batch(int G, int T, bool lj)
+{
+#define ROSEN_PICK(GG, TT)                                                              \
+    if (G == GG && T == TT) return lj ? batch_fn<GG, TT, true>() : batch_fn<GG, TT, false>();
+    ROSEN_PICK(8, 1) ROSEN_PICK(8, 2) ROSEN_PICK(8, 4)
+    ROSEN_PICK(16, 1) ROSEN_PICK(16, 2) ROSEN_PICK(16, 4)
+    ROSEN_PICK(32, 1) ROSEN_PICK(32, 2) ROSEN_PICK(32, 4)
+#undef ROSEN_PICK
+    return nullptr;
 }
 
 }  // namespace
@@ -783,8 +858,10 @@ int offlattice_default_lanes(int k)
     return 32;
 }
 
-int offlattice_launch(const rosen_offlattice_params *p, const rosen_offlattice_out *o,
-                      unsigned long long *counters, cudaStream_t s)
+size_t offlattice_args_size() { return sizeof(OffArgs); }
+
+void offlattice_make_args(const rosen_offlattice_params *p, const rosen_offlattice_out *o,
+                          unsigned long long *counters, void *out)
 {
     OffArgs a;
     memset(&a, 0, sizeof a);
@@ -817,8 +894,42 @@ int offlattice_launch(const rosen_offlattice_params *p, const rosen_offlattice_o
     a.trace = (p->flags & ROSEN_STORE_TRACE) ? o->trace : nullptr;
     a.coords = (p->flags & ROSEN_STORE_COORDS) ? o->coords : nullptr;
     a.counters = counters;
+    memcpy(out, &a, sizeof a);
+}
+
+int offlattice_launch(const rosen_offlattice_params *p, const rosen_offlattice_out *o,
+                      unsigned long long *counters, cudaStream_t s)
+{
+    OffArgs a;
+    offlattice_make_args(p, o, counters, &a);
+    const bool lj = p->potential == ROSEN_LJ;
     const int G = p->lanes_per_chain ? p->lanes_per_chain : offlattice_default_lanes(p->k);
     return lj ? launch_lj<true>(a, G, p->N, p->k, s) : launch_lj<false>(a, G, p->N, p->k, s);
+}
+
+int offlattice_batch_prepare(int G, int T, bool lj, int Nmax, int *chains_per_block, size_t *smem,
+                             int *blocks_per_sm)
+{
+    const BatchFn fn = pick_batch(G, T, lj);
+    if (!fn) return set_error(ROSEN_EINVAL, "no real-space batch kernel for G=%d T=%d", G, T);
+    *chains_per_block = chains_per_block_for(G, Nmax, lj);
+    *smem = kTable * sizeof(float) + (size_t)(*chains_per_block) * chain_smem_bytes(Nmax, lj);
+    cudaError_t e = allow_max_smem(fn);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn,
+                                                          (*chains_per_block) * G, *smem);
+    if (e != cudaSuccess)
+        return set_error(ROSEN_ECUDA, "real-space batch set-up: %s", cudaGetErrorString(e));
+    return ROSEN_OK;
+}
+
+void offlattice_batch_launch(int G, int T, bool lj, const void *dev_args, const BatchItem *items,
+                             int n_items, int *head, int chains_per_block, int Nmax, size_t smem,
+                             int grid, cudaStream_t s)
+{
+    const BatchFn fn = pick_batch(G, T, lj);
+    fn<<<grid, chains_per_block * G, smem, s>>>(reinterpret_cast<const OffArgs *>(dev_args), items,
+                                               n_items, head, chains_per_block, Nmax);
 }
 
 }  // namespace rosen

@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "internal.cuh"
 
 namespace rosen {
 namespace {
@@ -90,11 +91,12 @@ __device__ __forceinline__ void merge(double &Ma, double *sa, double &na, double
     na += nb;
 }
 
-__global__ void __launch_bounds__(kThreads) reduce_tiles_kernel(const ReduceArgs a, Partial *part)
+// Reduce tile `tile` of the ensemble a into *out (one block of kThreads).
+__device__ __forceinline__ void reduce_tile(const ReduceArgs &a, int64_t tile, Partial *out)
 {
     __shared__ double red[kThreads / 32][10];
     __shared__ double tileM;
-    const int64_t c0 = (int64_t)blockIdx.x * kTile;
+    const int64_t c0 = tile * kTile;
     double lw[kPerThread], A1[kPerThread], A2[kPerThread];
     double m = -INFINITY;
 #pragma unroll
@@ -161,14 +163,18 @@ __global__ void __launch_bounds__(kThreads) reduce_tiles_kernel(const ReduceArgs
         for (int w = 0; w < kThreads / 32; ++w) al += red[w][8];
         P.alive = al;
         P.pad[0] = P.pad[1] = 0.0;
-        part[blockIdx.x] = P;
+        *out = P;
     }
 }
 
-__global__ void __launch_bounds__(kFinalThreads) reduce_final_kernel(const Partial *part,
-                                                                     int64_t ntiles,
-                                                                     const ReduceArgs a,
-                                                                     rosen_stats *out)
+__global__ void __launch_bounds__(kThreads) reduce_tiles_kernel(const ReduceArgs a, Partial *part)
+{
+    reduce_tile(a, blockIdx.x, &part[blockIdx.x]);
+}
+
+// Merge the ntiles partials of one ensemble in a fixed tree (one block).
+__device__ __forceinline__ void reduce_final(const Partial *part, int64_t ntiles,
+                                             const ReduceArgs &a, rosen_stats *out)
 {
     __shared__ double sM[kFinalThreads], sS[kFinalThreads][8], sN[kFinalThreads];
     double M = -INFINITY, S[8] = {0, 0, 0, 0, 0, 0, 0, 0}, na = 0.0;
@@ -224,10 +230,75 @@ __global__ void __launch_bounds__(kFinalThreads) reduce_final_kernel(const Parti
     *out = r;
 }
 
+__global__ void __launch_bounds__(kFinalThreads) reduce_final_kernel(const Partial *part,
+                                                                     int64_t ntiles,
+                                                                     const ReduceArgs a,
+                                                                     rosen_stats *out)
+{
+    reduce_final(part, ntiles, a, out);
+}
+
+// Batched: block b reduces global tile b; tile_off[e] .. tile_off[e+1]-1 are
+// the tiles of ensemble e.
+__global__ void __launch_bounds__(kThreads) reduce_tiles_batch_kernel(const ReduceArgs *args,
+                                                                      const int64_t *tile_off,
+                                                                      int n_ens, Partial *part)
+{
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = n_ens;            // largest e with tile_off[e] <= b
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (tile_off[mid] <= b) lo = mid;
+        else hi = mid;
+    }
+    reduce_tile(args[lo], b - tile_off[lo], &part[b]);
+}
+
+__global__ void __launch_bounds__(kFinalThreads) reduce_final_batch_kernel(const Partial *part,
+                                                                           const int64_t *tile_off,
+                                                                           const ReduceArgs *args,
+                                                                           rosen_stats *out)
+{
+    const int e = blockIdx.x;
+    reduce_final(part + tile_off[e], tile_off[e + 1] - tile_off[e], args[e], out + e);
+}
+
 }  // namespace
 
 // Shared with the other translation units that reduce on the device.
 int64_t reduce_tiles(int64_t C) { return (C + kTile - 1) / kTile; }
+
+size_t reduce_args_size() { return sizeof(ReduceArgs); }
+size_t reduce_partial_bytes() { return sizeof(Partial); }
+
+void reduce_make_args(const rosen_reduce_in *in, void *out)
+{
+    ReduceArgs a;
+    memset(&a, 0, sizeof a);
+    a.kind = in->kind;
+    a.N = in->N;
+    a.k = in->k;
+    a.use_counts = in->use_counts;
+    a.C = in->C;
+    a.logw = in->logw;
+    a.counts = reinterpret_cast<const uint4 *>(in->counts);
+    a.r2_i = in->r2_i;
+    a.n2rg2 = in->n2rg2;
+    a.r2_f = in->r2_f;
+    a.rg2_f = in->rg2_f;
+    for (int q = 0; q < 8; ++q) a.logm[q] = q >= 1 ? log((double)q) : 0.0;
+    a.inv_n2 = 1.0 / ((double)in->N * (double)in->N);
+    memcpy(out, &a, sizeof a);
+}
+
+void reduce_batch_launch(const void *dev_args, const int64_t *dev_tile_off, int n_ens,
+                         int64_t total_tiles, void *part, rosen_stats *out, cudaStream_t s)
+{
+    const ReduceArgs *args = reinterpret_cast<const ReduceArgs *>(dev_args);
+    Partial *p = reinterpret_cast<Partial *>(part);
+    reduce_tiles_batch_kernel<<<(unsigned)total_tiles, kThreads, 0, s>>>(args, dev_tile_off, n_ens, p);
+    reduce_final_batch_kernel<<<n_ens, kFinalThreads, 0, s>>>(p, dev_tile_off, args, out);
+}
 
 int reduce_launch(const rosen_reduce_in *in, rosen_stats *out, void *part_ws, cudaStream_t s)
 {

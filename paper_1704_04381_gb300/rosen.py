@@ -71,6 +71,18 @@ class rosen_reduce_in(ctypes.Structure):
                 ("rg2_f", _vp)]
 
 
+ROSEN_MODEL_LATTICE = 0
+ROSEN_MODEL_OFFLATTICE = 1
+
+
+class rosen_ensemble(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("N", ctypes.c_int32), ("C", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("ensemble", ctypes.c_uint32), ("k", ctypes.c_int32),
+                ("potential", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("beta_eps", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("cutoff", ctypes.c_double)]
+
+
 _LIB = None
 
 
@@ -109,6 +121,26 @@ def load():
     L.rosen_reduce_workspace_size.restype = ctypes.c_size_t
     L.rosen_reduce.argtypes = [ctypes.POINTER(rosen_reduce_in), _vp, _vp, ctypes.c_size_t, _vp]
     L.rosen_reduce.restype = ctypes.c_int
+    L.rosen_batch_create.argtypes = [ctypes.POINTER(rosen_ensemble), ctypes.c_int32,
+                                     ctypes.POINTER(_vp)]
+    L.rosen_batch_create.restype = ctypes.c_int
+    for name in ("rosen_batch_tune", "rosen_batch_run"):
+        getattr(L, name).argtypes = [_vp, _vp]
+        getattr(L, name).restype = ctypes.c_int
+    L.rosen_batch_copy_stats.argtypes = [_vp, _vp, _vp]
+    L.rosen_batch_copy_stats.restype = ctypes.c_int
+    L.rosen_batch_copy_lattice.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(rosen_lattice_out),
+                                           _vp]
+    L.rosen_batch_copy_lattice.restype = ctypes.c_int
+    L.rosen_batch_copy_offlattice.argtypes = [_vp, ctypes.c_int32,
+                                              ctypes.POINTER(rosen_offlattice_out), _vp]
+    L.rosen_batch_copy_offlattice.restype = ctypes.c_int
+    L.rosen_batch_counters.argtypes = [_vp, _vp, _vp]
+    L.rosen_batch_counters.restype = ctypes.c_int
+    L.rosen_batch_describe.argtypes = [_vp, ctypes.c_char_p, ctypes.c_size_t]
+    L.rosen_batch_describe.restype = ctypes.c_int
+    L.rosen_batch_destroy.argtypes = [_vp]
+    L.rosen_batch_destroy.restype = ctypes.c_int
     L.rosen_reduce_noalloc.argtypes = [ctypes.POINTER(rosen_reduce_in), _vp, _vp]
     L.rosen_reduce_noalloc.restype = ctypes.c_int
     _LIB = L
@@ -274,3 +306,74 @@ def stats_dict(t):
 def reduce_workspace(C, device="cuda"):
     nbytes = rosen_reduce_workspace_size(C)
     return torch.empty((nbytes + 15) // 16 * 2, dtype=torch.float64, device=device)
+
+
+# ---- batched growth ----------------------------------------------------------
+def ensemble(model, N, C, seed, ensemble_id=0, k=0, potential=ROSEN_HARD_SPHERE, beta_eps=0.0,
+             sigma=1.0, cutoff=2.5):
+    return rosen_ensemble(model=int(model), N=int(N), C=int(C), seed=int(seed),
+                          ensemble=int(ensemble_id), k=int(k), potential=int(potential),
+                          reserved=0, beta_eps=float(beta_eps), sigma=float(sigma),
+                          cutoff=float(cutoff))
+
+
+class RosenBatch:
+    """A planned batch of ensembles (rosen_batch_*): tune, run, read back."""
+
+    def __init__(self, ensembles):
+        arr = (rosen_ensemble * len(ensembles))(*ensembles)
+        self.ensembles = list(ensembles)
+        h = _vp()
+        _check(load().rosen_batch_create(arr, len(ensembles), ctypes.byref(h)))
+        self.handle = h
+
+    def tune(self, stream=None):
+        _check(load().rosen_batch_tune(self.handle, _stream(stream)))
+
+    def run(self, stream=None):
+        _check(load().rosen_batch_run(self.handle, _stream(stream)))
+
+    def stats(self, out=None, stream=None):
+        if out is None:
+            out = torch.empty((len(self.ensembles), len(STAT_KEYS)), dtype=torch.float64,
+                              device="cuda")
+        _check(load().rosen_batch_copy_stats(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def lattice_outputs(self, e, stream=None):
+        ens = self.ensembles[e]
+        out = lattice_outputs(ens.N, ens.C)
+        o = rosen_lattice_out(counts=_ptr(out["counts"]), logw=_ptr(out["logw"]),
+                              r2=_ptr(out["r2"]), n2rg2=_ptr(out["n2rg2"]))
+        _check(load().rosen_batch_copy_lattice(self.handle, int(e), ctypes.byref(o), _stream(stream)))
+        return out
+
+    def offlattice_outputs(self, e, stream=None):
+        ens = self.ensembles[e]
+        out = offlattice_outputs(ens.N, ens.C)
+        o = rosen_offlattice_out(logw=_ptr(out["logw"]), r2=_ptr(out["r2"]),
+                                 rg2=_ptr(out["rg2"]), alive=_ptr(out["alive"]))
+        _check(load().rosen_batch_copy_offlattice(self.handle, int(e), ctypes.byref(o),
+                                                  _stream(stream)))
+        return out
+
+    def counters(self, stream=None):
+        out = torch.zeros(3, dtype=torch.int64, device="cuda")
+        _check(load().rosen_batch_counters(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def describe(self):
+        buf = ctypes.create_string_buffer(1 << 16)
+        _check(load().rosen_batch_describe(self.handle, buf, len(buf)))
+        return buf.value.decode()
+
+    def close(self):
+        if self.handle:
+            load().rosen_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -58,6 +58,7 @@ def test_struct_layout_matches_c(rosen, tmp_path):
         "rosen_reduce_in": rosen.rosen_reduce_in,
         "rosen_offlattice_params": rosen.rosen_offlattice_params,
         "rosen_offlattice_out": rosen.rosen_offlattice_out,
+        "rosen_ensemble": rosen.rosen_ensemble,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rosen.h"', "int main(void){"]
     for name, cls in structs.items():
@@ -154,3 +155,16 @@ def test_offlattice_rejects_bad_parameters(rosen, kw):
 
 def test_offlattice_empty_launch_is_a_no_op(rosen):
     assert _grow_off(rosen, C=0) == rosen.ROSEN_OK
+
+
+@pytest.mark.parametrize("bad", [
+    dict(model=2), dict(N=1), dict(C=0), dict(model=0, N=600), dict(model=1, k=0),
+    dict(model=1, potential=5), dict(beta_eps=-1.0),
+])
+def test_batch_rejects_bad_ensembles(rosen, bad):
+    good = dict(model=1, N=16, C=100, seed=1, k=16, potential=1, beta_eps=0.5)
+    ens = [rosen.ensemble(**good), rosen.ensemble(**{**good, **bad})]
+    arr = (rosen.rosen_ensemble * 2)(*ens)
+    h = ctypes.c_void_p()
+    assert rosen.load().rosen_batch_create(arr, 2, ctypes.byref(h)) == rosen.ROSEN_EINVAL
+    assert "ensemble 1" in rosen.last_error()
