@@ -305,6 +305,71 @@ ROSEN_API int rosen_batch_counters(rosen_batch *b, uint64_t *dst, void *stream);
 ROSEN_API int rosen_batch_describe(rosen_batch *b, char *buf, size_t len);
 ROSEN_API int rosen_batch_destroy(rosen_batch *b);
 
+/* ---- serving: a request loop with continuous admission --------------- */
+typedef struct rosen_serve_config {
+    uint64_t mem_budget_bytes; /* device memory the requests may hold at once  */
+    int32_t max_slots;         /* requests on the GPU at once, 1..1024          */
+    int32_t max_queue;         /* waiting requests before submit says EBUSY     */
+    int32_t device;            /* CUDA device                                   */
+    int32_t reserved;          /* set to 0                                      */
+} rosen_serve_config;
+
+typedef struct rosen_request {
+    int32_t model;       /* ROSEN_MODEL_LATTICE or ROSEN_MODEL_OFFLATTICE        */
+    int32_t N;
+    int64_t C;
+    uint64_t seed;
+    uint32_t ensemble;
+    int32_t k;           /* real space: trial directions per step                */
+    int32_t potential;   /* real space: ROSEN_HARD_SPHERE or ROSEN_LJ            */
+    int32_t store_coords;/* 1: keep the conformations (FP32 / int32 [N][3][C])   */
+    double beta_eps, sigma, cutoff;
+} rosen_request;
+
+typedef struct rosen_result {
+    uint64_t ticket;
+    int32_t status;      /* ROSEN_OK, ROSEN_ECLOSED (cancelled), or the failure  */
+    int32_t reserved;
+    rosen_stats stats;   /* the ensemble's statistics (rosen_reduce)             */
+    int64_t t_submit_ns, t_admit_ns, t_done_ns;   /* steady-clock times          */
+    void *coords;        /* device conformations if store_coords, owned by the
+                            server until rosen_serve_release                     */
+    char message[256];   /* failure detail                                       */
+} rosen_result;
+
+typedef struct rosen_serve_counters {
+    uint64_t submitted, rejected, completed, failed;
+    uint64_t queued, running, bytes_in_use;
+} rosen_serve_counters;
+
+typedef struct rosen_server rosen_server;   /* opaque */
+
+/*
+ * Start a server: a scheduler thread that admits submitted requests in
+ * arrival order as soon as a slot and enough of the memory budget are free,
+ * and runs each admitted request (growth + FP64 reduction) on a stream of
+ * its own, concurrently with the others.  Errors: EINVAL, ECUDA.
+ */
+ROSEN_API int rosen_serve_create(const rosen_serve_config *cfg, rosen_server **out);
+/* Submit from any thread.  EINVAL if the request is invalid or needs more
+ * than the whole budget; EBUSY if max_queue requests are waiting; ECLOSED
+ * after rosen_serve_destroy began. */
+ROSEN_API int rosen_serve_submit(rosen_server *s, const rosen_request *r, uint64_t *ticket);
+/* ROSEN_OK with the result once the request finished, ROSEN_EAGAIN while it
+ * is queued or running, ROSEN_ENOTFOUND for an unknown ticket. */
+ROSEN_API int rosen_serve_poll(rosen_server *s, uint64_t ticket, rosen_result *out);
+/* Wait at most timeout_ns (host-side, bounded); ROSEN_ETIMEOUT if not done. */
+ROSEN_API int rosen_serve_wait(rosen_server *s, uint64_t ticket, int64_t timeout_ns,
+                               rosen_result *out);
+/* Cancel a request that is still queued (ROSEN_EBUSY once admitted); its
+ * result then has status ROSEN_ECLOSED. */
+ROSEN_API int rosen_serve_cancel(rosen_server *s, uint64_t ticket);
+/* Forget a finished ticket and free its stored conformations. */
+ROSEN_API int rosen_serve_release(rosen_server *s, uint64_t ticket);
+ROSEN_API int rosen_serve_info(rosen_server *s, rosen_serve_counters *out);
+/* Stop accepting, cancel queued requests, let running ones finish, free. */
+ROSEN_API int rosen_serve_destroy(rosen_server *s);
+
 /* ---- reduction without device allocation ---------------------------- */
 /*
  * No counterpart in the paper: this entry point exists for callers that

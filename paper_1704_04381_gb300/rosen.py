@@ -377,3 +377,126 @@ class RosenBatch:
             self.close()
         except Exception:
             pass
+
+
+# ---- serving -----------------------------------------------------------------
+class rosen_stats_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in STAT_KEYS]
+
+
+class rosen_serve_config(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
+                ("max_queue", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class rosen_request(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("N", ctypes.c_int32), ("C", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("ensemble", ctypes.c_uint32), ("k", ctypes.c_int32),
+                ("potential", ctypes.c_int32), ("store_coords", ctypes.c_int32),
+                ("beta_eps", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("cutoff", ctypes.c_double)]
+
+
+class rosen_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("stats", rosen_stats_t),
+                ("t_submit_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64), ("coords", _vp), ("message", ctypes.c_char * 256)]
+
+
+class rosen_serve_counters(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "rejected", "completed", "failed",
+                                               "queued", "running", "bytes_in_use")]
+
+
+_SERVE_SIGS = {
+    "rosen_serve_create": [ctypes.POINTER(rosen_serve_config), ctypes.POINTER(_vp)],
+    "rosen_serve_submit": [_vp, ctypes.POINTER(rosen_request), ctypes.POINTER(ctypes.c_uint64)],
+    "rosen_serve_poll": [_vp, ctypes.c_uint64, ctypes.POINTER(rosen_result)],
+    "rosen_serve_wait": [_vp, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(rosen_result)],
+    "rosen_serve_cancel": [_vp, ctypes.c_uint64],
+    "rosen_serve_release": [_vp, ctypes.c_uint64],
+    "rosen_serve_info": [_vp, ctypes.POINTER(rosen_serve_counters)],
+    "rosen_serve_destroy": [_vp],
+}
+
+
+def _serve_lib():
+    L = load()
+    for name, args in _SERVE_SIGS.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    return L
+
+
+def request(model, N, C, seed, ensemble_id=0, k=0, potential=ROSEN_HARD_SPHERE, beta_eps=0.0,
+            sigma=1.0, cutoff=2.5, store_coords=False):
+    return rosen_request(model=int(model), N=int(N), C=int(C), seed=int(seed),
+                         ensemble=int(ensemble_id), k=int(k), potential=int(potential),
+                         store_coords=int(bool(store_coords)), beta_eps=float(beta_eps),
+                         sigma=float(sigma), cutoff=float(cutoff))
+
+
+def result_dict(r):
+    return {"ticket": r.ticket, "status": r.status,
+            "stats": {k: getattr(r.stats, k) for k in STAT_KEYS},
+            "t_submit_ns": r.t_submit_ns, "t_admit_ns": r.t_admit_ns, "t_done_ns": r.t_done_ns,
+            "coords": r.coords, "message": r.message.decode(errors="replace")}
+
+
+class RosenServer:
+    """The request loop (rosen_serve_*): submit, poll/wait, release."""
+
+    def __init__(self, mem_budget_bytes, max_slots=32, max_queue=4096, device=0):
+        cfg = rosen_serve_config(mem_budget_bytes=int(mem_budget_bytes), max_slots=int(max_slots),
+                                 max_queue=int(max_queue), device=int(device), reserved=0)
+        h = _vp()
+        _check(_serve_lib().rosen_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+
+    def submit(self, req):
+        """Return the ticket, or raise RosenError (EBUSY, EINVAL, ECLOSED)."""
+        t = ctypes.c_uint64()
+        _check(_serve_lib().rosen_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        return t.value
+
+    def try_submit(self, req):
+        """(status, ticket) without raising."""
+        t = ctypes.c_uint64()
+        st = _serve_lib().rosen_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(t))
+        return st, t.value
+
+    def poll(self, ticket):
+        r = rosen_result()
+        st = _serve_lib().rosen_serve_poll(self.handle, int(ticket), ctypes.byref(r))
+        return st, (result_dict(r) if st == ROSEN_OK else None)
+
+    def wait(self, ticket, timeout_s=60.0):
+        r = rosen_result()
+        st = _serve_lib().rosen_serve_wait(self.handle, int(ticket), int(timeout_s * 1e9),
+                                           ctypes.byref(r))
+        return st, (result_dict(r) if st == ROSEN_OK else None)
+
+    def cancel(self, ticket):
+        return _serve_lib().rosen_serve_cancel(self.handle, int(ticket))
+
+    def release(self, ticket):
+        return _serve_lib().rosen_serve_release(self.handle, int(ticket))
+
+    def info(self):
+        c = rosen_serve_counters()
+        _check(_serve_lib().rosen_serve_info(self.handle, ctypes.byref(c)))
+        return {k: getattr(c, k) for k, _ in c._fields_}
+
+    def close(self):
+        if self.handle:
+            _serve_lib().rosen_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

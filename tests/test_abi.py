@@ -59,6 +59,10 @@ def test_struct_layout_matches_c(rosen, tmp_path):
         "rosen_offlattice_params": rosen.rosen_offlattice_params,
         "rosen_offlattice_out": rosen.rosen_offlattice_out,
         "rosen_ensemble": rosen.rosen_ensemble,
+        "rosen_serve_config": rosen.rosen_serve_config,
+        "rosen_request": rosen.rosen_request,
+        "rosen_result": rosen.rosen_result,
+        "rosen_serve_counters": rosen.rosen_serve_counters,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rosen.h"', "int main(void){"]
     for name, cls in structs.items():
