@@ -39,8 +39,26 @@ WORKLOAD = ("N=64, 1e7 chains per ensemble: lattice ISAW beta*eps {0, 0.2, 0.4} 
 METRIC = "monomer insertions/s at N=64 (lattice & real space) vs roofline; served p50/p99 latency"
 UNIT = "insertions/s"
 
-# Algorithmic work in 32-bit lane operations (the model is stated with the
-# roofline in the design doc):
+# Roofline work per chain, the per-unit figures of the hot-path survey: the
+# brute-force method tests every earlier monomer against every trial.
+#  lattice: (N-1)(N-2)/2 pair tests at 7 INT ops, a 70-op Philox call and 30
+#    ops of selection and log per step (20,000 ops/chain at N = 64);
+#  real space: k (N-1)(N-2)/2 pair tests at 8 FP32 ops, and per step k
+#    Philox calls and directions at 90 ops (~6.8e5 ops/chain at N = 64, k = 32).
+SURVEY_LAT_PAIR, SURVEY_LAT_STEP = 7, 100
+SURVEY_OFF_PAIR, SURVEY_OFF_TRIAL = 8, 90
+
+
+def survey_lattice_ops(N):
+    return SURVEY_LAT_PAIR * (N - 1) * (N - 2) // 2 + SURVEY_LAT_STEP * (N - 1)
+
+
+def survey_offlattice_ops(N, k):
+    return SURVEY_OFF_PAIR * k * (N - 1) * (N - 2) // 2 + SURVEY_OFF_TRIAL * k * (N - 1)
+
+
+# Work the kernels actually execute, in 32-bit lane operations (they test only
+# the monomers that can reach a trial; the model is stated in the design doc):
 #  lattice: 6 per pair test (add, range test, gather multiply, shift, table
 #    load, accumulate), 100 per step (Philox 70, selection and log 30);
 #    athermal steps test only monomers of the matching parity;
@@ -251,20 +269,24 @@ def run_ours(args):
                 "n_alive": st["n_alive"]}
         if it["kind"] == "lattice":
             ops = lattice_ops_per_chain(N, it["athermal"]) * C
+            sops = survey_lattice_ops(N) * C
             kname = "lattice_lane_kernel<%s>" % ("athermal" if it["athermal"] else "isaw")
         else:
             cnt = it["out"]["counters"].cpu().tolist()
             reps = max(1, args.steps)
             listed = cnt[2] / reps
             ops = offlattice_ops(N, K_TRIALS, C, listed)
+            sops = survey_offlattice_ops(N, K_TRIALS) * C
             part.update({"fp64_redecided_steps": cnt[0] / reps,
                          "listed_beads_per_step": listed / (C * (N - 1))})
-            kname = "offlattice_warp_kernel<1>"
+            kname = "offlattice_group_kernel<16,2,hard sphere>"
         part["ops_per_chain"] = ops / C
+        part["survey_ops_per_chain"] = sops / C
         parts[it["name"]] = part
-        rooflines.append((kms, ops, kname))
-    kms, ops, kname = max(rooflines)
-    achieved = ops / (kms / 1e3)
+        rooflines.append((kms, sops, ops, kname))
+    kms, sops, ops, kname = max(rooflines)
+    achieved = sops / (kms / 1e3)
+    executed = ops / (kms / 1e3)
 
     e2e = None if args.no_e2e else measure_e2e(args, rosen, torch, dev, stream, chain0, ens)
     if world > 1:
@@ -283,7 +305,9 @@ def run_ours(args):
         "parts": parts,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "Tops/s (32-bit lane ops)", "frac": achieved / peak,
-                     "traffic": None, "kernel": kname, "ops_per_chain": ops / C,
+                     "traffic": None, "kernel": kname, "ops_per_chain": sops / C,
+                     "ops_basis": "survey per-unit figure (brute-force pair tests)",
+                     "executed_ops_per_chain": ops / C, "executed_frac": executed / peak,
                      "peak_basis": "%d SMs x 128 lanes x %.0f MHz (max SM clock)" % (sms, mhz)},
         "clocks": clocks.summary(),
         "e2e": e2e,
@@ -400,6 +424,181 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Batched and served modes (not part of the default step).
+# ---------------------------------------------------------------------------
+def batch_config(rosen, n_ens=256, seed=4, scale=1.0):
+    """The batched configuration: 256 ensembles, N uniform in [8, 256], chain
+    counts log-uniform in [1e3, 1e6], alternating lattice ISAW (beta eps in
+    [0, 0.5]) and Lennard-Jones beads (sigma 1, cutoff 2.5, beta eps in [0, 1],
+    k in {16, 32, 64}); seeds 1000 + e; drawn with numpy's default_rng(seed)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    ens = []
+    for e in range(n_ens):
+        N = int(rng.integers(8, 257))
+        C = max(1, int(10 ** rng.uniform(3, 6) * scale))
+        if e % 2 == 0:
+            ens.append(rosen.ensemble(rosen.ROSEN_MODEL_LATTICE, N, C, 1000 + e, e,
+                                      beta_eps=float(rng.uniform(0, 0.5))))
+        else:
+            ens.append(rosen.ensemble(rosen.ROSEN_MODEL_OFFLATTICE, N, C, 1000 + e, e,
+                                      k=int(rng.choice([16, 32, 64])), potential=rosen.ROSEN_LJ,
+                                      beta_eps=float(rng.uniform(0, 1))))
+    return ens
+
+
+def run_batched(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1704_04381_gb300 import rosen
+    torch.cuda.set_device(0)
+    ens = batch_config(rosen, scale=args.batch_scale)
+    ins = sum(e.C * (e.N - 1) for e in ens)
+    b = rosen.RosenBatch(ens)
+    t = time.perf_counter()
+    b.tune()
+    tune_s = time.perf_counter() - t
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, args.warmup)):
+        b.run(stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            b.run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1) / args.steps
+    # The plain single-ensemble path on the same ensembles, one after another.
+    outs = {}
+    ws = rosen.reduce_workspace(max(e.C for e in ens))
+    st = rosen.stats_tensor()
+
+    def singles():
+        for i, e in enumerate(ens):
+            if e.model == rosen.ROSEN_MODEL_LATTICE:
+                o = outs.get(i) or rosen.lattice_outputs(e.N, e.C)
+                rosen.rosen_lattice_grow(rosen.lattice_params(e.seed, e.N, e.C, beta_eps=e.beta_eps,
+                                                              ensemble=e.ensemble), o, stream)
+                rosen.rosen_reduce(rosen.lattice_reduce_in(o, e.N, int(e.beta_eps == 0.0)), st, ws,
+                                   stream)
+            else:
+                o = outs.get(i) or rosen.offlattice_outputs(e.N, e.C)
+                rosen.rosen_offlattice_grow(
+                    rosen.offlattice_params(e.seed, e.N, e.C, e.k, potential=e.potential,
+                                            beta_eps=e.beta_eps, ensemble=e.ensemble), o, stream)
+                rosen.rosen_reduce(rosen.offlattice_reduce_in(o, e.N, e.k), st, ws, stream)
+            outs[i] = o
+    singles()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    singles()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    single_ms = e0.elapsed_time(e1)
+    cnt = b.counters().cpu().tolist()
+    import json as _json
+    line = {
+        "metric": "batched monomer insertions/s (256 mixed ensembles, one graph launch)",
+        "value": ins / (batch_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True,
+        "dtype": "int32+fp32", "data": "synthetic",
+        "config": {"workload": "256 ensembles: N~U{8..256}, C log-uniform [1e3,1e6] x %g, "
+                               "lattice ISAW / LJ k in {16,32,64}" % args.batch_scale,
+                   "chains": sum(e.C for e in ens), "insertions": ins},
+        "single_ensemble_path": {"ms": single_ms, "insertions_per_s": ins / (single_ms / 1e3)},
+        "batched_over_single": single_ms / batch_ms,
+        "tune_s": tune_s, "classes": _json.loads(b.describe()),
+        "fp64_redecided_steps_total": cnt[0],
+        "clocks": clocks.summary(),
+    }
+    b.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_served(args):
+    import random
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1704_04381_gb300 import rosen
+    torch.cuda.set_device(0)
+    # Request mix: the batched configuration's distribution, 20% with stored
+    # conformations; Poisson arrivals at args.rate per second.
+    pool = batch_config(rosen, n_ens=4096, seed=5, scale=args.batch_scale)
+    rng = random.Random(5)
+    srv = rosen.RosenServer(mem_budget_bytes=int(args.budget_gb * (1 << 30)), max_slots=64,
+                            max_queue=args.max_queue)
+    done, rejected, tickets = [], 0, []
+    lock = threading.Lock()
+    stop = threading.Event()
+
+    def collector():
+        while not stop.is_set() or tickets:
+            with lock:
+                pending = list(tickets)
+            for t in pending:
+                st, res = srv.poll(t)
+                if st == rosen.ROSEN_OK:
+                    done.append(res)
+                    srv.release(t)
+                    with lock:
+                        tickets.remove(t)
+            time.sleep(0.001)
+
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    t_next = t0
+    n = 0
+    chains_offered = 0
+    while True:
+        t_next += rng.expovariate(args.rate)
+        if t_next - t0 > args.duration:
+            break
+        now = time.perf_counter()
+        if t_next > now:
+            time.sleep(t_next - now)
+        e = pool[n % len(pool)]
+        n += 1
+        req = rosen.request(e.model, e.N, e.C, e.seed + 7919 * n, e.ensemble, k=e.k,
+                            potential=e.potential, beta_eps=e.beta_eps,
+                            store_coords=rng.random() < 0.2)
+        chains_offered += e.C
+        st, t = srv.try_submit(req)
+        if st == rosen.ROSEN_OK:
+            with lock:
+                tickets.append(t)
+        else:
+            rejected += 1
+    stop.set()
+    th.join(timeout=args.duration * 4 + 120)
+    wall = time.perf_counter() - t0
+    srv.close()
+    import numpy as np
+    ok = [r for r in done if r["status"] == rosen.ROSEN_OK]
+    lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in ok]) if ok else np.zeros(1)
+    chains = sum(int(r["stats"]["n"]) for r in ok)
+    line = {
+        "metric": "served chains/s with p50/p99 latency (Poisson arrivals)",
+        "value": chains / wall, "unit": "chains/s", "n_gpus": 1,
+        "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": "requests from the batched distribution x %g, 20%% store "
+                               "conformations" % args.batch_scale, "rate_per_s": args.rate,
+                   "duration_s": args.duration, "budget_gb": args.budget_gb,
+                   "max_queue": args.max_queue},
+        "offered_requests": n, "rejected_busy": rejected, "completed": len(ok),
+        "offered_chains_per_s": chains_offered / args.duration,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max())},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,7 +610,18 @@ def main():
     ap.add_argument("--lattice-only", action="store_true")
     ap.add_argument("--chains", type=int, default=None,
                     help="chains per ensemble (default 10^7); smaller values are for profiling")
+    ap.add_argument("--workload", default="step", choices=["step", "batched", "served"])
+    ap.add_argument("--batch-scale", type=float, default=1.0,
+                    help="scale of the chain counts in the batched/served modes")
+    ap.add_argument("--rate", type=float, default=2000.0, help="served: arrivals per second")
+    ap.add_argument("--duration", type=float, default=20.0, help="served: seconds of arrivals")
+    ap.add_argument("--budget-gb", type=float, default=40.0)
+    ap.add_argument("--max-queue", type=int, default=256)
     args = ap.parse_args()
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     if args.chains:
         global C
         C = args.chains

@@ -56,13 +56,13 @@ struct ClassPlan {
     double tuned_ms_per_work = 0.0;
 };
 
+// Chain-length bucket of a class: a class's shared memory is sized for its
+// longest chain, so buckets are narrow enough (32 monomers up to 256, then
+// 128) that shorter members do not lose much occupancy.
 int bucket_of(int N)
 {
-    if (N <= 64) return 64;
-    if (N <= 128) return 128;
-    if (N <= 256) return 256;
-    if (N <= 512) return 512;
-    return 1024;
+    if (N <= 256) return (N + 31) / 32 * 32;
+    return (N + 127) / 128 * 128;
 }
 
 }  // namespace
@@ -477,7 +477,7 @@ int create(rosen_batch *b, const rosen_ensemble *ens, int n)
             c.B = 128;
             while (c.B > 32 && lattice_smem_bytes(c.Nmax, c.B) > 200 * 1024) c.B /= 2;
         } else {
-            c.G = offlattice_default_lanes(c.k);
+            c.G = offlattice_default_lanes(c.k, c.lj);
         }
         int st = shape_class(b, c);
         if (st != ROSEN_OK) return st;
