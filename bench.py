@@ -39,26 +39,26 @@ WORKLOAD = ("N=64, 1e7 chains per ensemble: lattice ISAW beta*eps {0, 0.2, 0.4} 
 METRIC = "monomer insertions/s at N=64 (lattice & real space) vs roofline; served p50/p99 latency"
 UNIT = "insertions/s"
 
-# Roofline work per chain, the per-unit figures of the hot-path survey: the
-# brute-force method tests every earlier monomer against every trial.
+# Roofline work per chain, counted for the brute-force method, which tests
+# every earlier monomer against every trial.
 #  lattice: (N-1)(N-2)/2 pair tests at 7 INT ops, a 70-op Philox call and 30
 #    ops of selection and log per step (20,000 ops/chain at N = 64);
 #  real space: k (N-1)(N-2)/2 pair tests at 8 FP32 ops, and per step k
 #    Philox calls and directions at 90 ops (~6.8e5 ops/chain at N = 64, k = 32).
-SURVEY_LAT_PAIR, SURVEY_LAT_STEP = 7, 100
-SURVEY_OFF_PAIR, SURVEY_OFF_TRIAL = 8, 90
+BRUTE_LAT_PAIR, BRUTE_LAT_STEP = 7, 100
+BRUTE_OFF_PAIR, BRUTE_OFF_TRIAL = 8, 90
 
 
-def survey_lattice_ops(N):
-    return SURVEY_LAT_PAIR * (N - 1) * (N - 2) // 2 + SURVEY_LAT_STEP * (N - 1)
+def brute_lattice_ops(N):
+    return BRUTE_LAT_PAIR * (N - 1) * (N - 2) // 2 + BRUTE_LAT_STEP * (N - 1)
 
 
-def survey_offlattice_ops(N, k):
-    return SURVEY_OFF_PAIR * k * (N - 1) * (N - 2) // 2 + SURVEY_OFF_TRIAL * k * (N - 1)
+def brute_offlattice_ops(N, k):
+    return BRUTE_OFF_PAIR * k * (N - 1) * (N - 2) // 2 + BRUTE_OFF_TRIAL * k * (N - 1)
 
 
 # Work the kernels actually execute, in 32-bit lane operations (they test only
-# the monomers that can reach a trial; the model is stated in the design doc):
+# the monomers that can reach a trial):
 #  lattice: 6 per pair test (add, range test, gather multiply, shift, table
 #    load, accumulate), 100 per step (Philox 70, selection and log 30);
 #    athermal steps test only monomers of the matching parity;
@@ -269,19 +269,19 @@ def run_ours(args):
                 "n_alive": st["n_alive"]}
         if it["kind"] == "lattice":
             ops = lattice_ops_per_chain(N, it["athermal"]) * C
-            sops = survey_lattice_ops(N) * C
+            sops = brute_lattice_ops(N) * C
             kname = "lattice_lane_kernel<%s>" % ("athermal" if it["athermal"] else "isaw")
         else:
             cnt = it["out"]["counters"].cpu().tolist()
             reps = max(1, args.steps)
             listed = cnt[2] / reps
             ops = offlattice_ops(N, K_TRIALS, C, listed)
-            sops = survey_offlattice_ops(N, K_TRIALS) * C
+            sops = brute_offlattice_ops(N, K_TRIALS) * C
             part.update({"fp64_redecided_steps": cnt[0] / reps,
                          "listed_beads_per_step": listed / (C * (N - 1))})
             kname = "offlattice_group_kernel<16,2,hard sphere>"
         part["ops_per_chain"] = ops / C
-        part["survey_ops_per_chain"] = sops / C
+        part["brute_ops_per_chain"] = sops / C
         parts[it["name"]] = part
         rooflines.append((kms, sops, ops, kname))
     kms, sops, ops, kname = max(rooflines)
@@ -306,7 +306,7 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "Tops/s (32-bit lane ops)", "frac": achieved / peak,
                      "traffic": None, "kernel": kname, "ops_per_chain": sops / C,
-                     "ops_basis": "survey per-unit figure (brute-force pair tests)",
+                     "ops_basis": "brute-force work: every earlier monomer tested against every trial",
                      "executed_ops_per_chain": ops / C, "executed_frac": executed / peak,
                      "peak_basis": "%d SMs x 128 lanes x %.0f MHz (max SM clock)" % (sms, mhz)},
         "clocks": clocks.summary(),

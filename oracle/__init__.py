@@ -47,9 +47,22 @@ def lib():
                                          ctypes.c_double, ctypes.c_int, f64p, f64p, f64p,
                                          u8p, u8p, f64p]
         L.orc_offlattice_run.restype = None
+        L.orc_lattice_run_restart.argtypes = [
+            ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+            ctypes.c_double, ctypes.c_int, ctypes.c_int, u16p, f64p, i64p, i64p, u8p, u8p, f64p,
+            u32p]
+        L.orc_lattice_run_restart.restype = None
+        L.orc_offlattice_run_restart.argtypes = [
+            ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+            ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+            ctypes.c_int, ctypes.c_int, f64p, f64p, f64p, u8p, u8p, f64p, u32p]
+        L.orc_offlattice_run_restart.restype = None
         L.orc_reduce.argtypes = [ctypes.c_int64, f64p, f64p, f64p, ctypes.c_int,
                                  ctypes.c_int, f64p]
         L.orc_reduce.restype = None
+        L.orc_reduce_n.argtypes = [ctypes.c_int64, f64p, f64p, f64p, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_double, f64p]
+        L.orc_reduce_n.restype = None
         L.orc_enumerate.argtypes = [ctypes.c_int, i64p, i64p, i64p]
         L.orc_enumerate.restype = ctypes.c_int
         _lib = L
@@ -78,12 +91,13 @@ def philox4x32_10(ctr, key):
 
 
 def lattice_run(seed, N, C, beta_eps=0.0, ensemble=0, chain0=0, threads=None,
-                trace=False, coords=False):
+                trace=False, coords=False, max_attempts=1):
     """Grow chains chain0 .. chain0+C-1 on the cubic lattice (Algorithm 1, Eq. 3).
 
     Returns a dict of numpy arrays: counts [C,8] u16, logw [C] f64, r2 [C] i64,
-    n2rg2 [C] i64, alive [C] u8, and optionally trace [C,N-1] u8 and
-    coords [C,N,3] f64.
+    n2rg2 [C] i64, alive [C] u8, attempts [C] u32, and optionally
+    trace [C,N-1] u8 and coords [C,N,3] f64.  max_attempts > 1 selects restart
+    mode (Section 3.3.2: a trapped chain is grown again from the start).
     """
     C = int(C)
     out = {
@@ -92,28 +106,30 @@ def lattice_run(seed, N, C, beta_eps=0.0, ensemble=0, chain0=0, threads=None,
         "r2": np.zeros(C, np.int64),
         "n2rg2": np.zeros(C, np.int64),
         "alive": np.zeros(C, np.uint8),
+        "attempts": np.zeros(C, np.uint32),
     }
     if trace:
         out["trace"] = np.zeros((C, N - 1), np.uint8)
     if coords:
         out["coords"] = np.zeros((C, N, 3), np.float64)
-    lib().orc_lattice_run(
-        int(seed), int(ensemble), int(chain0), C, int(N), float(beta_eps),
+    lib().orc_lattice_run_restart(
+        int(seed), int(ensemble), int(chain0), C, int(N), float(beta_eps), int(max_attempts),
         int(threads or default_threads()),
         _ptr(out["counts"], ctypes.c_uint16), _ptr(out["logw"], ctypes.c_double),
         _ptr(out["r2"], ctypes.c_int64), _ptr(out["n2rg2"], ctypes.c_int64),
         _ptr(out["alive"], ctypes.c_uint8), _ptr(out.get("trace"), ctypes.c_uint8),
-        _ptr(out.get("coords"), ctypes.c_double))
+        _ptr(out.get("coords"), ctypes.c_double), _ptr(out["attempts"], ctypes.c_uint32))
     return out
 
 
 def offlattice_run(seed, N, C, k, potential=HARD_SPHERE, beta_eps=0.0, sigma=1.0,
                    cutoff=2.5, ensemble=0, chain0=0, threads=None, trace=False,
-                   coords=False):
+                   coords=False, max_attempts=1):
     """Grow chains in real space with k trials per step (Algorithm 2).
 
-    Returns logw [C], r2 [C], rg2 [C] (f64), alive [C] u8 and optionally
-    trace [C,N-1] u8 and coords [C,N,3] f64.
+    Returns logw [C], r2 [C], rg2 [C] (f64), alive [C] u8, attempts [C] u32 and
+    optionally trace [C,N-1] u8 and coords [C,N,3] f64.  max_attempts > 1
+    selects restart mode (Section 3.3.3).
     """
     C = int(C)
     out = {
@@ -121,17 +137,20 @@ def offlattice_run(seed, N, C, k, potential=HARD_SPHERE, beta_eps=0.0, sigma=1.0
         "r2": np.zeros(C, np.float64),
         "rg2": np.zeros(C, np.float64),
         "alive": np.zeros(C, np.uint8),
+        "attempts": np.zeros(C, np.uint32),
     }
     if trace:
         out["trace"] = np.zeros((C, N - 1), np.uint8)
     if coords:
         out["coords"] = np.zeros((C, N, 3), np.float64)
-    lib().orc_offlattice_run(
+    lib().orc_offlattice_run_restart(
         int(seed), int(ensemble), int(chain0), C, int(N), int(k), int(potential),
-        float(sigma), float(cutoff), float(beta_eps), int(threads or default_threads()),
+        float(sigma), float(cutoff), float(beta_eps), int(max_attempts),
+        int(threads or default_threads()),
         _ptr(out["logw"], ctypes.c_double), _ptr(out["r2"], ctypes.c_double),
         _ptr(out["rg2"], ctypes.c_double), _ptr(out["alive"], ctypes.c_uint8),
-        _ptr(out.get("trace"), ctypes.c_uint8), _ptr(out.get("coords"), ctypes.c_double))
+        _ptr(out.get("trace"), ctypes.c_uint8), _ptr(out.get("coords"), ctypes.c_double),
+        _ptr(out["attempts"], ctypes.c_uint32))
     return out
 
 
@@ -140,14 +159,23 @@ STAT_KEYS = ["n", "n_alive", "log_max", "S0", "S1", "S2", "Q0", "Q1_r2", "Q2_r2"
              "se_rg2", "ess"]
 
 
-def reduce(logw, A1, A2, N, k=0):
-    """W-weighted ensemble statistics (Eq. 2 with W as the importance weight, Eq. 9)."""
+def reduce(logw, A1, A2, N, k=0, n=None):
+    """W-weighted ensemble statistics (Eq. 2 with W as the importance weight, Eq. 9).
+
+    n is Eq. 9's sample size: the number of chains (default) or, in restart
+    mode, the number of growth attempts made.
+    """
     lw = np.ascontiguousarray(logw, dtype=np.float64)
     a = np.ascontiguousarray(A1, dtype=np.float64)
     b = np.ascontiguousarray(A2, dtype=np.float64)
     out = np.zeros(len(STAT_KEYS), np.float64)
-    lib().orc_reduce(len(lw), _ptr(lw, ctypes.c_double), _ptr(a, ctypes.c_double),
-                     _ptr(b, ctypes.c_double), int(N), int(k), _ptr(out, ctypes.c_double))
+    if n is None:
+        lib().orc_reduce(len(lw), _ptr(lw, ctypes.c_double), _ptr(a, ctypes.c_double),
+                         _ptr(b, ctypes.c_double), int(N), int(k), _ptr(out, ctypes.c_double))
+    else:
+        lib().orc_reduce_n(len(lw), _ptr(lw, ctypes.c_double), _ptr(a, ctypes.c_double),
+                           _ptr(b, ctypes.c_double), int(N), int(k), float(n),
+                           _ptr(out, ctypes.c_double))
     return dict(zip(STAT_KEYS, out.tolist()))
 
 

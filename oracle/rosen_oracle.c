@@ -17,20 +17,23 @@
  *   - Eq. 1-2 (Section 2): the W-weighted estimator of an ensemble mean.
  *   - Eq. 9 (Section 4.2): Z_N estimated by the mean Rosenbluth weight.
  * The readings where the paper is silent or garbled (energies, selection
- * rule, RNG stream layout, dead ends) are listed in the design doc and restated
- * in the comments below where they are used.
+ * rule, RNG stream layout, dead ends) are stated in the comments below where
+ * they are used.
  *
  * Random numbers: Philox4x32-10 from Salmon, Moraes, Dror & Shaw,
  * "Parallel random numbers: as easy as 1, 2, 3" (SC'11), keyed by the
  * 64-bit seed and indexed by (chain, ensemble, step, slot).  Written here
  * from that published definition; it shares no code with the GPU library.
  *
- * Parity status of each function (see the design doc for the pins):
+ * Parity status of each function (what pins it to something other than
+ * itself; the pins are the -m "not gpu" tests):
  *   orc_philox4x32_10      pinned on the GPU machine against cuRAND's
  *                          Philox4_32_10 generator (a library routine)
  *   orc_lattice_chain      pinned by exact enumeration (c_n, <R^2>, Z_n)
  *   orc_offlattice_chain   pinned by closed forms (trimer), the ideal limit,
  *                          direction moments and simple sampling
+ *   *_chain_restart        pinned by the trimer in restart mode (closed-form
+ *                          attempt law, E[W] and <R^2>) and the exact c_n
  *   orc_reduce             pinned against exact rational sums
  *   orc_enumerate          pinned against brute force over all 6^n walks
  */
@@ -114,11 +117,13 @@ static int l1(const int32_t *a, const int32_t *b)
  * *n2rg2 = N^2 R_g^2 = N sum|r_i|^2 - |sum r_i|^2 (exact integers), trace
  * byte per step = (m << 3) | d (7 at the dead step, 0xFF after it), and the
  * positions in pos[N][3].  Returns 1 if the chain is alive, else 0.
+ *
+ * attempt numbers the growths of one chain in restart mode (below); its draws
+ * use the step word i + 2^16 * attempt, so attempt 0 is the plain stream.
  */
-ORC_EXPORT int orc_lattice_chain(uint64_t seed, uint32_t ens, uint32_t chain,
-                                 int N, double beta_eps, int32_t *pos,
-                                 uint8_t *trace, uint16_t counts[8],
-                                 double *logw, int64_t *r2, int64_t *n2rg2)
+static int lattice_attempt(uint64_t seed, uint32_t ens, uint32_t chain, uint32_t attempt,
+                           int N, double beta_eps, int32_t *pos, uint8_t *trace,
+                           uint16_t counts[8], double *logw, int64_t *r2, int64_t *n2rg2)
 {
     memset(counts, 0, sizeof(uint16_t) * 8);
     memset(pos, 0, sizeof(int32_t) * 3 * (size_t)N);
@@ -141,7 +146,7 @@ ORC_EXPORT int orc_lattice_chain(uint64_t seed, uint32_t ens, uint32_t chain,
             m += free_[d];
         }
         uint32_t x[4];
-        draw(seed, ens, chain, (uint32_t)i, 0u, x);
+        draw(seed, ens, chain, (uint32_t)i | (attempt << 16), 0u, x);
         int sel = -1;
         if (m == 0) {
             alive = 0;
@@ -202,6 +207,42 @@ ORC_EXPORT int orc_lattice_chain(uint64_t seed, uint32_t ens, uint32_t chain,
     return 1;
 }
 
+/* One growth from the plain stream (attempt 0): a dead end keeps W = 0. */
+ORC_EXPORT int orc_lattice_chain(uint64_t seed, uint32_t ens, uint32_t chain,
+                                 int N, double beta_eps, int32_t *pos,
+                                 uint8_t *trace, uint16_t counts[8],
+                                 double *logw, int64_t *r2, int64_t *n2rg2)
+{
+    return lattice_attempt(seed, ens, chain, 0u, N, beta_eps, pos, trace, counts, logw, r2,
+                           n2rg2);
+}
+
+/*
+ * Restart mode (Section 3.3.2: a chain that runs into a dead end is thrown
+ * away and grown again from the first monomer).  Attempts a = 0, 1, ... are
+ * made until one survives or max_attempts have been made; the outputs are
+ * those of the last attempt (a dead chain after max_attempts failures) and
+ * *attempts = the number of attempts made.  Every attempt is an independent
+ * growth, so the mean weight over all attempts, dead ones counted as 0, is
+ * the unbiased estimate of Z (Eq. 9 with the number of growths started).
+ */
+ORC_EXPORT int orc_lattice_chain_restart(uint64_t seed, uint32_t ens, uint32_t chain,
+                                         int N, double beta_eps, int max_attempts,
+                                         int32_t *pos, uint8_t *trace, uint16_t counts[8],
+                                         double *logw, int64_t *r2, int64_t *n2rg2,
+                                         uint32_t *attempts)
+{
+    int alive = 0;
+    uint32_t a = 0;
+    while (!alive && a < (uint32_t)max_attempts) {
+        alive = lattice_attempt(seed, ens, chain, a, N, beta_eps, pos, trace, counts, logw, r2,
+                                n2rg2);
+        a++;
+    }
+    *attempts = a;
+    return alive;
+}
+
 /* ------------------------------------------------------------------ */
 /* Real space (Algorithm 2).                                            */
 /* ------------------------------------------------------------------ */
@@ -255,14 +296,14 @@ static uint32_t selection_word(const uint32_t x[4])
  * (0xFE at the dead step, 0xFF after it), positions in pos[N][3].  The
  * normalised weight W / k^(N-1) estimates the fraction of ideal chains that
  * are self-avoiding (hard spheres) or their mean Boltzmann factor (LJ).
+ *
+ * attempt numbers the growths of one chain in restart mode; its draws use the
+ * step word i + 2^16 * attempt (attempt 0 is the plain stream).
  */
-ORC_EXPORT int orc_offlattice_chain(uint64_t seed, uint32_t ens, uint32_t chain,
-                                    int N, int k, int potential, double sigma,
-                                    double cutoff, double beta_eps, double *pos,
-                                    double *trial /* [k][3] scratch */,
-                                    double *wbuf /* [k] scratch */,
-                                    uint8_t *trace, double *logw, double *r2,
-                                    double *rg2)
+static int offlattice_attempt(uint64_t seed, uint32_t ens, uint32_t chain, uint32_t attempt,
+                              int N, int k, int potential, double sigma, double cutoff,
+                              double beta_eps, double *pos, double *trial, double *wbuf,
+                              uint8_t *trace, double *logw, double *r2, double *rg2)
 {
     memset(pos, 0, sizeof(double) * 3 * (size_t)N);
     if (trace) memset(trace, 0xFF, (size_t)(N - 1));
@@ -274,7 +315,7 @@ ORC_EXPORT int orc_offlattice_chain(uint64_t seed, uint32_t ens, uint32_t chain,
         uint32_t sel_word = 0;
         for (int t = 0; t < k; ++t) {
             uint32_t x[4];
-            draw(seed, ens, chain, (uint32_t)i, 1u + (uint32_t)(t / 2), x);
+            draw(seed, ens, chain, (uint32_t)i | (attempt << 16), 1u + (uint32_t)(t / 2), x);
             if (t == 0) sel_word = selection_word(x);
             double u[3];
             trial_direction(x, t, u);
@@ -387,6 +428,43 @@ ORC_EXPORT int orc_offlattice_chain(uint64_t seed, uint32_t ens, uint32_t chain,
     return 1;
 }
 
+/* One growth from the plain stream (attempt 0): a dead end keeps W = 0. */
+ORC_EXPORT int orc_offlattice_chain(uint64_t seed, uint32_t ens, uint32_t chain,
+                                    int N, int k, int potential, double sigma,
+                                    double cutoff, double beta_eps, double *pos,
+                                    double *trial /* [k][3] scratch */,
+                                    double *wbuf /* [k] scratch */,
+                                    uint8_t *trace, double *logw, double *r2,
+                                    double *rg2)
+{
+    return offlattice_attempt(seed, ens, chain, 0u, N, k, potential, sigma, cutoff, beta_eps,
+                              pos, trial, wbuf, trace, logw, r2, rg2);
+}
+
+/*
+ * Restart mode (Section 3.3.3: when no trial position is free the growth
+ * starts again from the first bead): attempts a = 0, 1, ... until one
+ * survives or max_attempts have been made; outputs of the last attempt and
+ * *attempts = the number made (see orc_lattice_chain_restart).
+ */
+ORC_EXPORT int orc_offlattice_chain_restart(uint64_t seed, uint32_t ens, uint32_t chain,
+                                            int N, int k, int potential, double sigma,
+                                            double cutoff, double beta_eps, int max_attempts,
+                                            double *pos, double *trial, double *wbuf,
+                                            uint8_t *trace, double *logw, double *r2,
+                                            double *rg2, uint32_t *attempts)
+{
+    int alive = 0;
+    uint32_t a = 0;
+    while (!alive && a < (uint32_t)max_attempts) {
+        alive = offlattice_attempt(seed, ens, chain, a, N, k, potential, sigma, cutoff,
+                                   beta_eps, pos, trial, wbuf, trace, logw, r2, rg2);
+        a++;
+    }
+    *attempts = a;
+    return alive;
+}
+
 /* ------------------------------------------------------------------ */
 /* Whole ensembles: chains chain0 .. chain0+C-1, split over threads.    */
 /* Every chain is independent (Section 3.3.1: one chain per thread), so  */
@@ -409,6 +487,8 @@ typedef struct {
     uint8_t *alive;           /* [C]                      */
     uint8_t *trace;           /* [C][N-1] or NULL         */
     double *coords;           /* [C][N][3] or NULL        */
+    int max_attempts;         /* 1 = no restart           */
+    uint32_t *attempts;       /* [C] or NULL              */
 } run_job;
 
 static void *run_range(void *arg)
@@ -421,9 +501,12 @@ static void *run_range(void *arg)
             uint16_t cnt[8];
             double lw;
             int64_t r2, g2;
-            int ok = orc_lattice_chain(
-                J->seed, J->ens, (uint32_t)(J->chain0 + c), N, J->beta_eps, pos,
-                J->trace ? J->trace + (size_t)c * (N - 1) : NULL, cnt, &lw, &r2, &g2);
+            uint32_t att;
+            int ok = orc_lattice_chain_restart(
+                J->seed, J->ens, (uint32_t)(J->chain0 + c), N, J->beta_eps, J->max_attempts,
+                pos, J->trace ? J->trace + (size_t)c * (N - 1) : NULL, cnt, &lw, &r2, &g2,
+                &att);
+            if (J->attempts) J->attempts[c] = att;
             if (J->counts) memcpy(J->counts + 8 * (size_t)c, cnt, sizeof cnt);
             if (J->logw) J->logw[c] = lw;
             if (J->r2_i) J->r2_i[c] = r2;
@@ -440,10 +523,12 @@ static void *run_range(void *arg)
         double *wbuf = (double *)malloc(sizeof(double) * (size_t)J->k);
         for (int64_t c = J->lo; c < J->hi; ++c) {
             double lw, r2, g2;
-            int ok = orc_offlattice_chain(
+            uint32_t att;
+            int ok = orc_offlattice_chain_restart(
                 J->seed, J->ens, (uint32_t)(J->chain0 + c), N, J->k, J->potential,
-                J->sigma, J->cutoff, J->beta_eps, pos, trial, wbuf,
-                J->trace ? J->trace + (size_t)c * (N - 1) : NULL, &lw, &r2, &g2);
+                J->sigma, J->cutoff, J->beta_eps, J->max_attempts, pos, trial, wbuf,
+                J->trace ? J->trace + (size_t)c * (N - 1) : NULL, &lw, &r2, &g2, &att);
+            if (J->attempts) J->attempts[c] = att;
             if (J->logw) J->logw[c] = lw;
             if (J->r2_d) J->r2_d[c] = r2;
             if (J->rg2_d) J->rg2_d[c] = g2;
@@ -478,17 +563,49 @@ static void run_threads(run_job *base, int64_t C, int nthreads)
     for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
 }
 
-ORC_EXPORT void orc_lattice_run(uint64_t seed, uint32_t ens, int64_t chain0,
-                                int64_t C, int N, double beta_eps, int nthreads,
-                                uint16_t *counts, double *logw, int64_t *r2,
-                                int64_t *n2rg2, uint8_t *alive, uint8_t *trace,
-                                double *coords)
+/* max_attempts: 1 = a dead end keeps W = 0; > 1 = restart mode.  attempts
+ * (may be NULL) receives the number of growths made per chain. */
+ORC_EXPORT void orc_lattice_run_restart(uint64_t seed, uint32_t ens, int64_t chain0,
+                                        int64_t C, int N, double beta_eps, int max_attempts,
+                                        int nthreads, uint16_t *counts, double *logw,
+                                        int64_t *r2, int64_t *n2rg2, uint8_t *alive,
+                                        uint8_t *trace, double *coords, uint32_t *attempts)
 {
     run_job J;
     memset(&J, 0, sizeof J);
     J.kind = 0; J.seed = seed; J.ens = ens; J.chain0 = chain0; J.N = N;
     J.beta_eps = beta_eps; J.counts = counts; J.logw = logw; J.r2_i = r2;
     J.n2rg2 = n2rg2; J.alive = alive; J.trace = trace; J.coords = coords;
+    J.max_attempts = max_attempts < 1 ? 1 : max_attempts;
+    J.attempts = attempts;
+    run_threads(&J, C, nthreads);
+}
+
+ORC_EXPORT void orc_lattice_run(uint64_t seed, uint32_t ens, int64_t chain0,
+                                int64_t C, int N, double beta_eps, int nthreads,
+                                uint16_t *counts, double *logw, int64_t *r2,
+                                int64_t *n2rg2, uint8_t *alive, uint8_t *trace,
+                                double *coords)
+{
+    orc_lattice_run_restart(seed, ens, chain0, C, N, beta_eps, 1, nthreads, counts, logw, r2,
+                            n2rg2, alive, trace, coords, NULL);
+}
+
+ORC_EXPORT void orc_offlattice_run_restart(uint64_t seed, uint32_t ens, int64_t chain0,
+                                           int64_t C, int N, int k, int potential,
+                                           double sigma, double cutoff, double beta_eps,
+                                           int max_attempts, int nthreads, double *logw,
+                                           double *r2, double *rg2, uint8_t *alive,
+                                           uint8_t *trace, double *coords, uint32_t *attempts)
+{
+    run_job J;
+    memset(&J, 0, sizeof J);
+    J.kind = 1; J.seed = seed; J.ens = ens; J.chain0 = chain0; J.N = N; J.k = k;
+    J.potential = potential; J.sigma = sigma; J.cutoff = cutoff;
+    J.beta_eps = beta_eps; J.logw = logw; J.r2_d = r2; J.rg2_d = rg2;
+    J.alive = alive; J.trace = trace; J.coords = coords;
+    J.max_attempts = max_attempts < 1 ? 1 : max_attempts;
+    J.attempts = attempts;
     run_threads(&J, C, nthreads);
 }
 
@@ -499,13 +616,8 @@ ORC_EXPORT void orc_offlattice_run(uint64_t seed, uint32_t ens, int64_t chain0,
                                    double *rg2, uint8_t *alive, uint8_t *trace,
                                    double *coords)
 {
-    run_job J;
-    memset(&J, 0, sizeof J);
-    J.kind = 1; J.seed = seed; J.ens = ens; J.chain0 = chain0; J.N = N; J.k = k;
-    J.potential = potential; J.sigma = sigma; J.cutoff = cutoff;
-    J.beta_eps = beta_eps; J.logw = logw; J.r2_d = r2; J.rg2_d = rg2;
-    J.alive = alive; J.trace = trace; J.coords = coords;
-    run_threads(&J, C, nthreads);
+    orc_offlattice_run_restart(seed, ens, chain0, C, N, k, potential, sigma, cutoff, beta_eps,
+                               1, nthreads, logw, r2, rg2, alive, trace, coords, NULL);
 }
 
 /* ------------------------------------------------------------------ */
@@ -513,7 +625,8 @@ ORC_EXPORT void orc_offlattice_run(uint64_t seed, uint32_t ens, int64_t chain0,
 /* ------------------------------------------------------------------ */
 /*
  * out[] (18 doubles):
- *  0 n            number of chains (dead ones included, Eq. 9)
+ *  0 n            number of growths (Eq. 9's sample size: the chains, dead
+ *                 ones included, or in restart mode every attempt made)
  *  1 n_alive
  *  2 log_max      M = max log W over live chains
  *  3 S0 = sum w,  w = exp(log W - M)
@@ -531,8 +644,8 @@ ORC_EXPORT void orc_offlattice_run(uint64_t seed, uint32_t ens, int64_t chain0,
  * 17 ess      = S0^2 / Q0   (Kish effective sample size)
  * Written plainly: one pass for the maximum, one pass for the sums.
  */
-ORC_EXPORT void orc_reduce(int64_t C, const double *logw, const double *A1,
-                           const double *A2, int N, int k, double *out)
+ORC_EXPORT void orc_reduce_n(int64_t C, const double *logw, const double *A1,
+                             const double *A2, int N, int k, double n, double *out)
 {
     double M = -INFINITY;
     int64_t alive = 0;
@@ -551,7 +664,7 @@ ORC_EXPORT void orc_reduce(int64_t C, const double *logw, const double *A1,
             Q0 += w * w; Q1a += w * w * a; Q2a += w * w * a * a;
             Q1b += w * w * b; Q2b += w * w * b * b;
         }
-    out[0] = (double)C;
+    out[0] = n;
     out[1] = (double)alive;
     out[2] = M;
     out[3] = S0; out[4] = S1; out[5] = S2; out[6] = Q0;
@@ -563,7 +676,7 @@ ORC_EXPORT void orc_reduce(int64_t C, const double *logw, const double *A1,
         out[17] = 0.0;
         return;
     }
-    out[11] = M + log(S0 / (double)C);
+    out[11] = M + log(S0 / n);
     out[12] = k > 0 ? out[11] - (double)(N - 1) * log((double)k) : out[11];
     double m1 = S1 / S0, m2 = S2 / S0;
     double v1 = Q2a - 2.0 * m1 * Q1a + m1 * m1 * Q0;
@@ -573,6 +686,13 @@ ORC_EXPORT void orc_reduce(int64_t C, const double *logw, const double *A1,
     out[15] = m2;
     out[16] = sqrt(v2 > 0 ? v2 : 0) / S0;
     out[17] = S0 * S0 / Q0;
+}
+
+/* The statistics with n = C (one growth per chain). */
+ORC_EXPORT void orc_reduce(int64_t C, const double *logw, const double *A1,
+                           const double *A2, int N, int k, double *out)
+{
+    orc_reduce_n(C, logw, A1, A2, N, k, (double)C, out);
 }
 
 /* ------------------------------------------------------------------ */
