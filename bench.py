@@ -18,6 +18,7 @@ the roofline figure.  --impl reference times the FP64 CPU oracle instead, on a
 bounded sample of the same workload.
 """
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -161,21 +162,24 @@ def dist_env():
 class Ensembles:
     """The step's ensembles: parameters, output tensors, reduction inputs."""
 
-    def __init__(self, rosen, torch, dev, chain0, with_hs=True):
+    def __init__(self, rosen, torch, dev, chain0, with_hs=True, max_attempts=0):
         self.rosen = rosen
         self.items = []
+        restart = max_attempts > 1
         for b, seed in LATTICE:
-            out = rosen.lattice_outputs(N, C, device=dev)
+            out = rosen.lattice_outputs(N, C, device=dev, attempts=restart)
             self.items.append({
                 "name": "lattice_beps%.1f" % b, "kind": "lattice", "athermal": b == 0.0,
-                "params": rosen.lattice_params(seed, N, C, beta_eps=b, chain0=chain0),
+                "params": rosen.lattice_params(seed, N, C, beta_eps=b, chain0=chain0,
+                                               max_attempts=max_attempts),
                 "out": out, "rin": rosen.lattice_reduce_in(out, N, use_counts=int(b == 0.0)),
                 "stats": rosen.stats_tensor(dev)})
         if with_hs:
-            out = rosen.offlattice_outputs(N, C, device=dev, counters=True)
+            out = rosen.offlattice_outputs(N, C, device=dev, counters=True, attempts=restart)
             self.items.append({
                 "name": "hard_sphere_k32", "kind": "offlattice",
-                "params": rosen.offlattice_params(HS_SEED, N, C, K_TRIALS, chain0=chain0),
+                "params": rosen.offlattice_params(HS_SEED, N, C, K_TRIALS, chain0=chain0,
+                                                  max_attempts=max_attempts),
                 "out": out, "rin": rosen.offlattice_reduce_in(out, N, K_TRIALS),
                 "stats": rosen.stats_tensor(dev)})
         self.ws = rosen.reduce_workspace(C, dev)
@@ -210,7 +214,8 @@ def run_ours(args):
     # Weak scaling: every rank grows its own C chains of each ensemble (global
     # chain indices rank*C .. rank*C + C - 1); no data-path collective.
     chain0 = rank * C
-    ens = Ensembles(rosen, torch, dev, chain0, with_hs=not args.lattice_only)
+    ens = Ensembles(rosen, torch, dev, chain0, with_hs=not args.lattice_only,
+                    max_attempts=args.max_attempts)
     kernel_ev = []
 
     def step(record=False):
@@ -266,7 +271,7 @@ def run_ours(args):
         st = rosen.stats_dict(it["stats"])
         part = {"kernel_ms": kms, "insertions_per_s": C * (N - 1) / (kms / 1e3),
                 "mean_r2": st["mean_r2"], "se_r2": st["se_r2"], "logZ": st["logZ"],
-                "n_alive": st["n_alive"]}
+                "n_alive": st["n_alive"], "growths": st["n"]}
         if it["kind"] == "lattice":
             ops = lattice_ops_per_chain(N, it["athermal"]) * C
             sops = brute_lattice_ops(N) * C
@@ -300,6 +305,7 @@ def run_ours(args):
         "data": "synthetic (Philox-seeded growth; no input data)",
         "config": {"workload": WORKLOAD, "N": N, "chains_per_ensemble": C * world,
                    "lattice_beta_eps": [b for b, _ in LATTICE], "hs_k": K_TRIALS,
+                   "max_attempts": max(1, args.max_attempts),
                    "l2": "no inputs; outputs 160-320 MB per ensemble > 129 MB L2, no flush",
                    "parallelism": "dp%d (chain ranges per GPU)" % world},
         "parts": parts,
@@ -331,7 +337,7 @@ def measure_e2e(args, rosen, torch, dev, stream, chain0, ens):
         hs = torch.empty(len(rosen.STAT_KEYS), dtype=torch.float64, pin_memory=True)
         host.append((h, hs))
         d2h += sum(v.numel() * v.element_size() for v in h.values()) + hs.numel() * 8
-    h2d = sum(48 if it["kind"] == "lattice" else 72 for it in ens.items)
+    h2d = sum(ctypes.sizeof(it["params"]) for it in ens.items)
 
     def step():
         for it, (h, hs) in zip(ens.items, host):
@@ -617,6 +623,8 @@ def main():
     ap.add_argument("--duration", type=float, default=20.0, help="served: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=40.0)
     ap.add_argument("--max-queue", type=int, default=256)
+    ap.add_argument("--max-attempts", type=int, default=0,
+                    help="step: restart mode, growths per chain (0/1: dead ends keep W = 0)")
     args = ap.parse_args()
     if args.workload == "batched":
         return run_batched(args)

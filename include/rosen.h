@@ -59,6 +59,7 @@ extern "C" {
 #define ROSEN_OFFLATTICE_NMAX 1024
 #define ROSEN_KMAX 128            /* real-space trials per step             */
 
+#define ROSEN_MAX_ATTEMPTS 65535  /* restart mode: growths per chain        */
 #define ROSEN_STORE_TRACE 1u      /* write the per-step trace bytes         */
 #define ROSEN_STORE_COORDS 2u     /* write the chain coordinates            */
 
@@ -94,6 +95,12 @@ typedef struct rosen_lattice_params {
                                  energy -eps (interacting SAW)              */
     uint32_t flags;           /* ROSEN_STORE_TRACE | ROSEN_STORE_COORDS     */
     int32_t lanes_per_chain;  /* 0 = automatic; else 1 (one chain per lane) */
+    int32_t max_attempts;     /* 0 or 1: a trapped chain keeps W = 0.  2 ..
+                                 ROSEN_MAX_ATTEMPTS: restart mode (Section
+                                 3.3.2): a trapped chain is grown again from
+                                 monomer 0, at most max_attempts growths in
+                                 all; growth a draws from the step word
+                                 i + 2^16 a (a = 0 is the plain stream)    */
 } rosen_lattice_params;
 
 typedef struct rosen_lattice_out {
@@ -114,6 +121,9 @@ typedef struct rosen_lattice_out {
     int32_t *coords;  /* [N][3][C] optional (needs ROSEN_STORE_COORDS):
                          monomer i, axis a of chain c at [i][a][c]; zero
                          after a dead end                                   */
+    uint16_t *attempts; /* [C] optional: growths made (1 unless restart
+                         mode); every other output is the last growth's.
+                         Eq. 9's sample size is the sum (rosen_reduce_in) */
 } rosen_lattice_out;
 
 /*
@@ -126,7 +136,8 @@ typedef struct rosen_lattice_out {
  * sequential implementation of the same rule in FP64 (the FP32 selection
  * falls back to FP64 whenever rounding could change the choice).
  * Errors: EINVAL for N outside [2, 512], C < 0, chain0 + C > 2^32,
- * beta_eps < 0 or not finite, unknown flags or lanes_per_chain.
+ * beta_eps < 0 or not finite, unknown flags or lanes_per_chain,
+ * max_attempts outside [0, ROSEN_MAX_ATTEMPTS].
  */
 ROSEN_API int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lattice_out *o,
                        void *stream);
@@ -147,6 +158,11 @@ typedef struct rosen_offlattice_params {
     uint32_t flags;           /* ROSEN_STORE_TRACE | ROSEN_STORE_COORDS     */
     int32_t lanes_per_chain;  /* 0 = automatic; else 8, 16 or 32 lanes grow
                                  one chain (k <= 4 * lanes_per_chain)       */
+    int32_t max_attempts;     /* 0 or 1: a dead end keeps W = 0.  2 ..
+                                 ROSEN_MAX_ATTEMPTS: restart mode (Section
+                                 3.3.3): the chain is grown again from bead
+                                 0; growth a draws from the step word
+                                 i + 2^16 a                                 */
 } rosen_offlattice_params;
 
 typedef struct rosen_offlattice_out {
@@ -164,6 +180,8 @@ typedef struct rosen_offlattice_out {
                           caller zeroes them): steps re-decided in FP64,
                           chains grown, beads listed near the chain end
                           (each listed bead is tested against all k trials) */
+    uint16_t *attempts;/* [C] optional: growths made (1 unless restart mode);
+                          the other outputs are the last growth's           */
 } rosen_offlattice_out;
 
 /*
@@ -179,7 +197,7 @@ typedef struct rosen_offlattice_out {
  * implementation of the same rule.
  * Errors: EINVAL for N outside [2, 1024], k outside [1, 128], bad chain
  * range, unknown potential, sigma/cutoff/beta_eps out of range, unknown
- * flags or lanes_per_chain.
+ * flags or lanes_per_chain, max_attempts outside [0, ROSEN_MAX_ATTEMPTS].
  */
 ROSEN_API int rosen_offlattice_grow(const rosen_offlattice_params *p,
                                     const rosen_offlattice_out *o, void *stream);
@@ -211,11 +229,15 @@ typedef struct rosen_reduce_in {
     const int64_t *n2rg2;    /* [C] lattice N^2 R_g^2                        */
     const float *r2_f;       /* [C] real-space R_ee^2                        */
     const float *rg2_f;      /* [C] real-space R_g^2                         */
+    const uint16_t *attempts;/* [C] optional (restart mode): growths made per
+                                chain; Eq. 9's n is then their sum (every
+                                discarded growth counts with W = 0), else C */
 } rosen_reduce_in;
 
 /* Ensemble statistics, all FP64.  With w_c = exp(log W_c - log_max):     */
 typedef struct rosen_stats {
-    double n;          /* chains, dead ones included (Eq. 9)               */
+    double n;          /* growths: chains, dead ones included (Eq. 9), or
+                          the sum of attempts in restart mode              */
     double n_alive;
     double log_max;    /* max log W over live chains                       */
     double S0, S1, S2; /* sum w, sum w R_ee^2, sum w R_g^2                 */
@@ -256,7 +278,9 @@ typedef struct rosen_ensemble {
     uint32_t ensemble;   /* ensemble id, part of the Philox counter              */
     int32_t k;           /* real space: trial directions per step                */
     int32_t potential;   /* real space: ROSEN_HARD_SPHERE or ROSEN_LJ            */
-    int32_t reserved;    /* set to 0                                             */
+    int32_t max_attempts;/* 0 or 1: dead ends keep W = 0; else restart mode (see
+                            the growth parameters); the batch then keeps the
+                            attempts per chain and reduces over all growths   */
     double beta_eps;     /* lattice: contact attraction; LJ: well depth / kT     */
     double sigma;        /* real space: bead diameter / LJ sigma                 */
     double cutoff;       /* LJ truncation radius                                 */
@@ -292,7 +316,8 @@ ROSEN_API int rosen_batch_lattice_outputs(rosen_batch *b, int32_t e, rosen_latti
 ROSEN_API int rosen_batch_offlattice_outputs(rosen_batch *b, int32_t e, rosen_offlattice_out *out);
 /* Enqueue copies of the statistics (dst: device, n rosen_stats) or of
  * ensemble e's per-chain outputs (the non-NULL fields of dst, device) on
- * stream. */
+ * stream.  attempts is copied only for an ensemble in restart mode (the
+ * batch keeps no attempts otherwise; dst->attempts is then left as is). */
 ROSEN_API int rosen_batch_copy_stats(rosen_batch *b, rosen_stats *dst, void *stream);
 ROSEN_API int rosen_batch_copy_lattice(rosen_batch *b, int32_t e, const rosen_lattice_out *dst,
                                        void *stream);
@@ -324,6 +349,8 @@ typedef struct rosen_request {
     int32_t potential;   /* real space: ROSEN_HARD_SPHERE or ROSEN_LJ            */
     int32_t store_coords;/* 1: keep the conformations (FP32 / int32 [N][3][C])   */
     double beta_eps, sigma, cutoff;
+    int32_t max_attempts;/* 0 or 1: dead ends keep W = 0; else restart mode      */
+    int32_t reserved;    /* set to 0                                             */
 } rosen_request;
 
 typedef struct rosen_result {

@@ -116,6 +116,7 @@ rosen_lattice_params lat_params(const rosen_ensemble &e)
     p.beta_eps = e.beta_eps;
     p.flags = 0;
     p.lanes_per_chain = 0;
+    p.max_attempts = e.max_attempts;
     return p;
 }
 
@@ -135,6 +136,7 @@ rosen_offlattice_params off_params(const rosen_ensemble &e, int lanes)
     p.beta_eps = e.beta_eps;
     p.flags = 0;
     p.lanes_per_chain = lanes;
+    p.max_attempts = e.max_attempts;
     return p;
 }
 
@@ -387,6 +389,7 @@ int create(rosen_batch *b, const rosen_ensemble *ens, int n)
             total += align256(16 * C) + align256(4 * C) + align256(4 * C) + align256(8 * C);
         else
             total += align256(4 * C) * 3 + align256(C);
+        if (ens[e].max_attempts > 1) total += align256(2 * C);   // attempts (restart mode)
     }
     CK(cudaMalloc(&b->d_out, std::max<size_t>(total, 256)));
     CK(cudaMalloc(&b->d_counters, 3 * sizeof(unsigned long long)));
@@ -412,6 +415,9 @@ int create(rosen_batch *b, const rosen_ensemble *ens, int n)
             o.r2 = reinterpret_cast<int32_t *>(p);
             p += align256(4 * C);
             o.n2rg2 = reinterpret_cast<int64_t *>(p);
+            p += align256(8 * C);
+            if (ens[e].max_attempts > 1) o.attempts = reinterpret_cast<uint16_t *>(p);
+            in.attempts = o.attempts;
             in.kind = ROSEN_REDUCE_LATTICE;
             in.use_counts = ens[e].beta_eps == 0.0;
             in.logw = o.logw;
@@ -428,6 +434,9 @@ int create(rosen_batch *b, const rosen_ensemble *ens, int n)
             o.rg2 = reinterpret_cast<float *>(p);
             p += align256(4 * C);
             o.alive = p;
+            p += align256(C);
+            if (ens[e].max_attempts > 1) o.attempts = reinterpret_cast<uint16_t *>(p);
+            in.attempts = o.attempts;
             in.kind = ROSEN_REDUCE_OFFLATTICE;
             in.k = ens[e].k;
             in.logw = o.logw;
@@ -611,6 +620,8 @@ extern "C" int rosen_batch_copy_lattice(rosen_batch *b, int32_t e, const rosen_l
         r = cudaMemcpyAsync(dst->r2, src.r2, 4 * C, cudaMemcpyDeviceToDevice, s);
     if (dst->n2rg2 && r == cudaSuccess)
         r = cudaMemcpyAsync(dst->n2rg2, src.n2rg2, 8 * C, cudaMemcpyDeviceToDevice, s);
+    if (dst->attempts && src.attempts && r == cudaSuccess)
+        r = cudaMemcpyAsync(dst->attempts, src.attempts, 2 * C, cudaMemcpyDeviceToDevice, s);
     return r == cudaSuccess ? ROSEN_OK : cuda_fail("rosen_batch_copy_lattice", r);
 }
 
@@ -632,6 +643,8 @@ extern "C" int rosen_batch_copy_offlattice(rosen_batch *b, int32_t e, const rose
         r = cudaMemcpyAsync(dst->rg2, src.rg2, 4 * C, cudaMemcpyDeviceToDevice, s);
     if (dst->alive && r == cudaSuccess)
         r = cudaMemcpyAsync(dst->alive, src.alive, C, cudaMemcpyDeviceToDevice, s);
+    if (dst->attempts && src.attempts && r == cudaSuccess)
+        r = cudaMemcpyAsync(dst->attempts, src.attempts, 2 * C, cudaMemcpyDeviceToDevice, s);
     return r == cudaSuccess ? ROSEN_OK : cuda_fail("rosen_batch_copy_offlattice", r);
 }
 

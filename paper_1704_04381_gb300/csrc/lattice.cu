@@ -107,6 +107,8 @@ struct LatticeArgs {
     int64_t *n2rg2;
     uint8_t *trace;   // [N-1][C]
     int32_t *coords;  // [N][3][C]
+    uint16_t *attempts;   // [C]
+    uint32_t max_att;     // growths per chain (1: no restart)
 };
 
 // The FP64 selection, in exactly the order of the sequential definition:
@@ -139,6 +141,8 @@ __device__ __noinline__ int select_fp64(uint32_t freem, uint32_t acc, uint32_t x
 
 // Grow chain c (local index) of the ensemble described by a, in this lane.
 // my points at the lane's column of the [monomer][lane] key array (stride B).
+// In restart mode a trapped growth is thrown away and the chain grown again
+// from the origin with the next attempt index in the step word.
 template <bool kIsaw>
 __device__ __forceinline__ void lattice_chain(const LatticeArgs &a, int64_t c, uint32_t *my, int B,
                                               const uint32_t *lut, const uint8_t *seltab,
@@ -148,87 +152,98 @@ __device__ __forceinline__ void lattice_chain(const LatticeArgs &a, int64_t c, u
     const int N = a.N;
     const int64_t C = a.C;
 
-    uint32_t key = kOriginKey;
-    my[0] = key;
-    int sx = 0, sy = 0, sz = 0, sq = 0;
-    int ex = 0, ey = 0, ez = 0;
-    uint64_t cnt = 0;      // 9-bit field m holds the number of steps with m free sites
-    float lw = 0.f;
-    int dead_at = 0;
+    uint32_t key;
+    int sx, sy, sz, sq;
+    int ex, ey, ez;
+    uint64_t cnt;      // 9-bit field m holds the number of steps with m free sites
+    float lw;
+    int dead_at;
     if (a.coords) {
         a.coords[(0 * 3 + 0) * C + c] = 0;
         a.coords[(0 * 3 + 1) * C + c] = 0;
         a.coords[(0 * 3 + 2) * C + c] = 0;
     }
+    uint32_t att = 0;
+    for (;;) {
+        key = kOriginKey;
+        my[0] = key;
+        sx = sy = sz = sq = 0;
+        ex = ey = ez = 0;
+        cnt = 0;
+        lw = 0.f;
+        dead_at = 0;
 
-    for (int i = 1; i < N; ++i) {
-        uint32_t acc = 0u;
-        const uint32_t kb = kNearBias - key;
-        if (kIsaw) {
+        for (int i = 1; i < N; ++i) {
+            uint32_t acc = 0u;
+            const uint32_t kb = kNearBias - key;
+            if (kIsaw) {
 #pragma unroll 4
-            for (int j = 0; j <= i - 2; ++j) {
-                acc += lut[lut_slot(my[j * B] + kb)];
-            }
-        } else {
-#pragma unroll 4
-            for (int j = i & 1; j <= i - 2; j += 2) {
-                acc += lut[lut_slot(my[j * B] + kb)];
-            }
-        }
-        const uint32_t freem = ~acc & 63u;
-        const int m = __popc(freem);
-        if (m == 0) {
-            dead_at = i;
-            break;
-        }
-        const uint32_t x = philox(make_uint4(chain, a.ens, (uint32_t)i, 0u), a.key).x;
-        int sel;
-        if (!kIsaw) {
-            sel = seltab[(freem << 3) | __umulhi(x, (uint32_t)m)];
-        } else {
-            float w[6], S = 0.f;
-#pragma unroll
-            for (int d = 0; d < 6; ++d) {
-                const uint32_t cd = (acc >> (8 + 3 * d)) & 7u;
-                w[d] = ((freem >> d) & 1u) ? wt32[cd] : 0.f;
-                S += w[d];
-            }
-            const float r = u24f(x) * S;
-            float P = 0.f, lo = 0.f, hi = 0.f;
-            sel = -1;
-#pragma unroll
-            for (int d = 0; d < 6; ++d) {
-                const float Pn = P + w[d];
-                if (sel < 0 && Pn > r) {
-                    sel = d;
-                    lo = P;
-                    hi = Pn;
+                for (int j = 0; j <= i - 2; ++j) {
+                    acc += lut[lut_slot(my[j * B] + kb)];
                 }
-                P = Pn;
+            } else {
+#pragma unroll 4
+                for (int j = i & 1; j <= i - 2; j += 2) {
+                    acc += lut[lut_slot(my[j * B] + kb)];
+                }
             }
-            const float tol = S * 0x1p-18f;
-            if (sel < 0 || !(r - lo > tol) || !(hi - r > tol)) sel = select_fp64(freem, acc, x, wt64);
-            lw += logf(S);
+            const uint32_t freem = ~acc & 63u;
+            const int m = __popc(freem);
+            if (m == 0) {
+                dead_at = i;
+                break;
+            }
+            const uint32_t x = philox(make_uint4(chain, a.ens, (uint32_t)i | (att << 16), 0u), a.key).x;
+            int sel;
+            if (!kIsaw) {
+                sel = seltab[(freem << 3) | __umulhi(x, (uint32_t)m)];
+            } else {
+                float w[6], S = 0.f;
+#pragma unroll
+                for (int d = 0; d < 6; ++d) {
+                    const uint32_t cd = (acc >> (8 + 3 * d)) & 7u;
+                    w[d] = ((freem >> d) & 1u) ? wt32[cd] : 0.f;
+                    S += w[d];
+                }
+                const float r = u24f(x) * S;
+                float P = 0.f, lo = 0.f, hi = 0.f;
+                sel = -1;
+#pragma unroll
+                for (int d = 0; d < 6; ++d) {
+                    const float Pn = P + w[d];
+                    if (sel < 0 && Pn > r) {
+                        sel = d;
+                        lo = P;
+                        hi = Pn;
+                    }
+                    P = Pn;
+                }
+                const float tol = S * 0x1p-18f;
+                if (sel < 0 || !(r - lo > tol) || !(hi - r > tol)) sel = select_fp64(freem, acc, x, wt64);
+                lw += logf(S);
+            }
+            cnt += 1ull << (9 * m);
+            const uint32_t axis_step = 1u << (10 * (sel >> 1));
+            key = (sel & 1) ? key - axis_step : key + axis_step;
+            my[i * B] = key;
+            ex = (int)(key & 1023u) - 512;
+            ey = (int)((key >> 10) & 1023u) - 512;
+            ez = (int)(key >> 20) - 512;
+            sx += ex;
+            sy += ey;
+            sz += ez;
+            sq += ex * ex + ey * ey + ez * ez;
+            if (a.trace) a.trace[(int64_t)(i - 1) * C + c] = (uint8_t)((m << 3) | sel);
+            if (a.coords) {
+                a.coords[((int64_t)i * 3 + 0) * C + c] = ex;
+                a.coords[((int64_t)i * 3 + 1) * C + c] = ey;
+                a.coords[((int64_t)i * 3 + 2) * C + c] = ez;
+            }
         }
-        cnt += 1ull << (9 * m);
-        const uint32_t axis_step = 1u << (10 * (sel >> 1));
-        key = (sel & 1) ? key - axis_step : key + axis_step;
-        my[i * B] = key;
-        ex = (int)(key & 1023u) - 512;
-        ey = (int)((key >> 10) & 1023u) - 512;
-        ez = (int)(key >> 20) - 512;
-        sx += ex;
-        sy += ey;
-        sz += ez;
-        sq += ex * ex + ey * ey + ez * ez;
-        if (a.trace) a.trace[(int64_t)(i - 1) * C + c] = (uint8_t)((m << 3) | sel);
-        if (a.coords) {
-            a.coords[((int64_t)i * 3 + 0) * C + c] = ex;
-            a.coords[((int64_t)i * 3 + 1) * C + c] = ey;
-            a.coords[((int64_t)i * 3 + 2) * C + c] = ez;
-        }
+        if (!dead_at || att + 1 >= a.max_att) break;
+        ++att;
     }
-
+    if (a.attempts) a.attempts[c] = (uint16_t)(att + 1);
     if (dead_at) cnt += 1ull;   // counts[0] = 1 marks the dead end
     uint32_t cm[7];
 #pragma unroll
@@ -237,8 +252,8 @@ __device__ __forceinline__ void lattice_chain(const LatticeArgs &a, int64_t c, u
         a.counts[c] = make_uint4(cm[0] | (cm[1] << 16), cm[2] | (cm[3] << 16),
                                  cm[4] | (cm[5] << 16), cm[6]);
     if (dead_at) {
-        // Trapped (Section 3.3.2 restarts such chains; here W = 0 is kept and
-        // the counts of the steps before the dead end stay recorded).
+        // Trapped (in every attempt made): W = 0 is kept and the counts of
+        // the steps before the dead end stay recorded.
         if (a.logw) a.logw[c] = -INFINITY;
         if (a.r2) a.r2[c] = 0;
         if (a.n2rg2) a.n2rg2[c] = 0;
@@ -365,6 +380,9 @@ int lattice_validate(const rosen_lattice_params *p, const rosen_lattice_out *o)
         return set_error(ROSEN_EINVAL, "rosen_lattice_grow: unknown flags 0x%x", p->flags);
     if (p->lanes_per_chain != 0 && p->lanes_per_chain != 1)
         return set_error(ROSEN_EINVAL, "rosen_lattice_grow: lanes_per_chain must be 0 or 1");
+    if (p->max_attempts < 0 || p->max_attempts > ROSEN_MAX_ATTEMPTS)
+        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: max_attempts = %d outside [0, %d]",
+                         p->max_attempts, ROSEN_MAX_ATTEMPTS);
     if ((p->flags & ROSEN_STORE_TRACE) && !o->trace)
         return set_error(ROSEN_EINVAL, "rosen_lattice_grow: ROSEN_STORE_TRACE without trace");
     if ((p->flags & ROSEN_STORE_COORDS) && !o->coords)
@@ -398,6 +416,8 @@ void lattice_make_args(const rosen_lattice_params *p, const rosen_lattice_out *o
     a.n2rg2 = o->n2rg2;
     a.trace = (p->flags & ROSEN_STORE_TRACE) ? o->trace : nullptr;
     a.coords = (p->flags & ROSEN_STORE_COORDS) ? o->coords : nullptr;
+    a.attempts = o->attempts;
+    a.max_att = p->max_attempts > 1 ? (uint32_t)p->max_attempts : 1u;
     memcpy(out, &a, sizeof a);
 }
 

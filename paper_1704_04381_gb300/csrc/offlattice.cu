@@ -48,6 +48,8 @@ struct OffArgs {
     uint8_t *alive, *trace;
     float *coords;
     unsigned long long *counters;   // optional [3]: steps re-decided, chains, listed beads
+    uint16_t *attempts;             // optional [C]
+    uint32_t max_att;               // growths per chain (1: no restart)
 };
 
 // Per-chain shared memory: float-float positions, the near list, the trace.
@@ -229,8 +231,8 @@ struct Group {
 // are stored back into the float-float arrays and the end returned.
 template <int G>
 __device__ __noinline__ void replay_positions(const OffArgs &a, const ChainSmem &w,
-                                              const Group<G> &g, uint32_t chain, int i,
-                                              double &ex, double &ey, double &ez)
+                                              const Group<G> &g, uint32_t chain, uint32_t aw,
+                                              int i, double &ex, double &ey, double &ez)
 {
     double cx = 0.0, cy = 0.0, cz = 0.0;
     for (int b0 = 1; b0 <= i - 1; b0 += G) {
@@ -239,7 +241,7 @@ __device__ __noinline__ void replay_positions(const OffArgs &a, const ChainSmem 
         if (s <= i - 1) {
             const int t = w.tr[s];
             const uint4 q =
-                philox(make_uint4(chain, a.ens, (uint32_t)s, 1u + (uint32_t)(t >> 1)), a.key);
+                philox(make_uint4(chain, a.ens, (uint32_t)s | aw, 1u + (uint32_t)(t >> 1)), a.key);
             uint32_t wa, wb;
             trial_words(q, t, wa, wb);
             dir64(wa, wb, x, y, z);
@@ -267,14 +269,14 @@ __device__ __noinline__ void replay_positions(const OffArgs &a, const ChainSmem 
 // the sequential FP64 arithmetic of the definition.
 template <int G, int T, bool LJ>
 __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, const Group<G> &g,
-                                      uint32_t chain, int i, int nn, uint32_t selw,
+                                      uint32_t chain, uint32_t aw, int i, int nn, uint32_t selw,
                                       const float *logm, float &ehx, float &ehy, float &ehz,
                                       float &elx, float &ely, float &elz, int &sel, float &logS,
                                       int &dead_at)
 {
     const int k = a.k;
     double ex, ey, ez;
-    replay_positions<G>(a, w, g, chain, i, ex, ey, ez);
+    replay_positions<G>(a, w, g, chain, aw, i, ex, ey, ez);
     // The exact end, back into the float-float registers.
     ehx = (float)ex;
     elx = (float)(ex - ehx);
@@ -287,7 +289,7 @@ __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, c
     for (int s = 0; s < T; ++s) {
         const int t = T * g.gl + s;
         const uint4 xx =
-            philox(make_uint4(chain, a.ens, (uint32_t)i, 1u + (uint32_t)(t >> 1)), a.key);
+            philox(make_uint4(chain, a.ens, (uint32_t)i | aw, 1u + (uint32_t)(t >> 1)), a.key);
         uint32_t wa, wb;
         trial_words(xx, t, wa, wb);
         double dx, dy, dz;
@@ -380,7 +382,9 @@ __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, c
 }
 
 // Grow chain c (local index) of the ensemble a with the G lanes of group g,
-// in the per-chain shared memory w.
+// in the per-chain shared memory w.  In restart mode a growth that reaches a
+// dead end is thrown away and the chain grown again from bead 0, with the
+// attempt index in the high half of the step word.
 template <int G, int T, bool LJ>
 __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const ChainSmem &w,
                                           const Group<G> &g, const float *logm)
@@ -392,236 +396,249 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const Cha
         w.hi[0] = make_float4(0.f, 0.f, 0.f, 0.f);
         w.lo[0] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    float ehx = 0.f, ehy = 0.f, ehz = 0.f, elx = 0.f, ely = 0.f, elz = 0.f;
-    float lw = 0.f;
-    int dead_at = 0;
-    int exact_upto = 0;   // beads 0..exact_upto are exact (r_0; after a replay at step i: all < i)
+    float ehx, ehy, ehz, elx, ely, elz;
+    float lw;
+    int dead_at;
+    int exact_upto;   // beads 0..exact_upto are exact (r_0; after a replay at step i: all < i)
     unsigned rechecks = 0;
     unsigned long long listed = 0;
+    uint32_t att = 0;
+    for (;;) {
+        const uint32_t aw = att << 16;
+        ehx = ehy = ehz = elx = ely = elz = 0.f;
+        lw = 0.f;
+        dead_at = 0;
+        exact_upto = 0;
 
-    for (int i = 1; i < N; ++i) {
-        // ---- 1. near list (ascending bead index) --------------------------
-        int nn = 0;
-        float band = 0.f;    // largest bead band of the step (hard spheres)
-        for (int b0 = 0; b0 <= i - 2; b0 += G) {
-            const int j = b0 + g.gl;
-            float4 L = make_float4(0.f, 0.f, 0.f, 0.f);
-            bool near = false;
-            if (j <= i - 2) {
-                const float4 h = w.hi[j], l = w.lo[j];
-                const float gx = (ehx - h.x) + (elx - l.x);
-                const float gy = (ehy - h.y) + (ely - l.y);
-                const float gz = (ehz - h.z) + (elz - l.z);
-                const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-                L = make_float4(gx, gy, gz, 1.f + g2);
-                near = g2 < a.rf2;
-            }
-            const unsigned m = g.ballot(near);
-            if (near) {
-                const int slot = nn + __popc(m & ((1u << g.gl) - 1u));
-                w.nl[slot] = L;
-                w.nj[slot] = j;
-                if (LJ) {
-                    const float gn = sqrtf(L.w - 1.f) * 1.001f + 1e-6f;
-                    w.nb[slot] =
-                        pair_band(gn, L.w, i - 1 - max(j, exact_upto), fminf(1.f + gn, a.dband));
+        for (int i = 1; i < N; ++i) {
+            // ---- 1. near list (ascending bead index) --------------------------
+            int nn = 0;
+            float band = 0.f;    // largest bead band of the step (hard spheres)
+            for (int b0 = 0; b0 <= i - 2; b0 += G) {
+                const int j = b0 + g.gl;
+                float4 L = make_float4(0.f, 0.f, 0.f, 0.f);
+                bool near = false;
+                if (j <= i - 2) {
+                    const float4 h = w.hi[j], l = w.lo[j];
+                    const float gx = (ehx - h.x) + (elx - l.x);
+                    const float gy = (ehy - h.y) + (ely - l.y);
+                    const float gz = (ehz - h.z) + (elz - l.z);
+                    const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+                    L = make_float4(gx, gy, gz, 1.f + g2);
+                    near = g2 < a.rf2;
                 }
+                const unsigned m = g.ballot(near);
+                if (near) {
+                    const int slot = nn + __popc(m & ((1u << g.gl) - 1u));
+                    w.nl[slot] = L;
+                    w.nj[slot] = j;
+                    if (LJ) {
+                        const float gn = sqrtf(L.w - 1.f) * 1.001f + 1e-6f;
+                        w.nb[slot] =
+                            pair_band(gn, L.w, i - 1 - max(j, exact_upto), fminf(1.f + gn, a.dband));
+                    }
+                }
+                nn += __popc(m);
             }
-            nn += __popc(m);
-        }
-        listed += (unsigned)nn;
-        __syncwarp(g.mask);
-        if (!LJ && nn > 0) {
-            // One band for the step: the oldest listed bead drifted longest, and
-            // |g| <= sqrt(rf2), c <= 1 + rf2 for every listed bead.
-            const int D = i - 1 - max(w.nj[0], exact_upto);
-            band = pair_band(a.rf, 1.f + a.rf2, D, a.dband);
-        }
+            listed += (unsigned)nn;
+            __syncwarp(g.mask);
+            if (!LJ && nn > 0) {
+                // One band for the step: the oldest listed bead drifted longest, and
+                // |g| <= sqrt(rf2), c <= 1 + rf2 for every listed bead.
+                const int D = i - 1 - max(w.nj[0], exact_upto);
+                band = pair_band(a.rf, 1.f + a.rf2, D, a.dband);
+            }
 
-        // ---- 2. trials ----------------------------------------------------
-        float ux[T], uy[T], uz[T];
-        bool valid[T];
-        uint32_t selw = 0;
-        uint4 x = make_uint4(0u, 0u, 0u, 0u);
+            // ---- 2. trials ----------------------------------------------------
+            float ux[T], uy[T], uz[T];
+            bool valid[T];
+            uint32_t selw = 0;
+            uint4 x = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-        for (int s = 0; s < T; ++s) {
-            const int t = T * g.gl + s;
-            valid[s] = t < k;
-            if (T == 1 || (s & 1) == 0)
-                x = philox(make_uint4(chain, a.ens, (uint32_t)i, 1u + (uint32_t)(t >> 1)), a.key);
-            if (s == 0)
-                selw = (x.x & 0xFFu) | ((x.y & 0xFFu) << 8) | ((x.z & 0xFFu) << 16) |
-                       ((x.w & 0xFFu) << 24);
-            uint32_t wa, wb;
-            trial_words(x, t, wa, wb);
-            const float3 u = dir32(wa, wb);
-            ux[s] = 2.f * u.x;   // 2u: d^2 = c + (2u).g
-            uy[s] = 2.f * u.y;
-            uz[s] = 2.f * u.z;
-        }
-        selw = g.bcast(selw, 0);
+            for (int s = 0; s < T; ++s) {
+                const int t = T * g.gl + s;
+                valid[s] = t < k;
+                if (T == 1 || (s & 1) == 0)
+                    x = philox(make_uint4(chain, a.ens, (uint32_t)i | aw, 1u + (uint32_t)(t >> 1)),
+                               a.key);
+                if (s == 0)
+                    selw = (x.x & 0xFFu) | ((x.y & 0xFFu) << 8) | ((x.z & 0xFFu) << 16) |
+                           ((x.w & 0xFFu) << 24);
+                uint32_t wa, wb;
+                trial_words(x, t, wa, wb);
+                const float3 u = dir32(wa, wb);
+                ux[s] = 2.f * u.x;   // 2u: d^2 = c + (2u).g
+                uy[s] = 2.f * u.y;
+                uz[s] = 2.f * u.z;
+            }
+            selw = g.bcast(selw, 0);
 
-        // ---- 3. pair loop -----------------------------------------------
-        float mind[T], U[T], Ub[T], Ua[T];
-        int ncut[T];
+            // ---- 3. pair loop -----------------------------------------------
+            float mind[T], U[T], Ub[T], Ua[T];
+            int ncut[T];
 #pragma unroll
-        for (int s = 0; s < T; ++s) {
-            mind[s] = INFINITY;
-            U[s] = 0.f;
-            Ub[s] = 0.f;
-            Ua[s] = 0.f;
-            ncut[s] = 0;
-        }
+            for (int s = 0; s < T; ++s) {
+                mind[s] = INFINITY;
+                U[s] = 0.f;
+                Ub[s] = 0.f;
+                Ua[s] = 0.f;
+                ncut[s] = 0;
+            }
 #pragma unroll 2
-        for (int q = 0; q < nn; ++q) {
-            const float4 L = w.nl[q];
-            const float bq = LJ ? w.nb[q] : 0.f;
+            for (int q = 0; q < nn; ++q) {
+                const float4 L = w.nl[q];
+                const float bq = LJ ? w.nb[q] : 0.f;
 #pragma unroll
-            for (int s = 0; s < T; ++s) {
-                const float d2 = fmaf(ux[s], L.x, fmaf(uy[s], L.y, fmaf(uz[s], L.z, L.w)));
-                if (!LJ) {
-                    mind[s] = fminf(mind[s], d2);
-                } else {
-                    if (d2 < a.rc2) {
-                        const float sr = __fdividef(a.sig2, d2);
-                        const float s3 = sr * sr * sr;
-                        const float e = s3 * (s3 - 1.f);
-                        U[s] += e;
-                        Ua[s] += fabsf(e);
-                        Ub[s] = fmaf(sr * s3, fabsf(2.f * s3 - 1.f) * bq, Ub[s]);
-                    }
-                    ncut[s] += fabsf(d2 - a.rc2) < bq;
-                }
-            }
-        }
-
-        // ---- 4. weights, selection, error bounds ---------------------------
-        int sel = -1;
-        float logS = 0.f;
-        bool ok = true;
-        if (!LJ) {
-            bool fr[T], flag = false;
-            int cnt = 0;
-#pragma unroll
-            for (int s = 0; s < T; ++s) {
-                fr[s] = valid[s] && mind[s] >= a.sig2;
-                flag |= valid[s] && fabsf(mind[s] - a.sig2) < band;
-                cnt += fr[s];
-            }
-            if (g.ballot(flag)) {
-                ok = false;
-            } else {
-                const int incl = g.scan(cnt);
-                const int m = g.bcast(incl, G - 1);
-                if (m == 0) {
-                    dead_at = i;
-                } else {
-                    const int idx = (int)__umulhi(selw, (uint32_t)m);
-                    int mine = -1, seen = incl - cnt;
-#pragma unroll
-                    for (int s = 0; s < T; ++s)
-                        if (fr[s]) {
-                            if (seen == idx) mine = T * g.gl + s;
-                            ++seen;
+                for (int s = 0; s < T; ++s) {
+                    const float d2 = fmaf(ux[s], L.x, fmaf(uy[s], L.y, fmaf(uz[s], L.z, L.w)));
+                    if (!LJ) {
+                        mind[s] = fminf(mind[s], d2);
+                    } else {
+                        if (d2 < a.rc2) {
+                            const float sr = __fdividef(a.sig2, d2);
+                            const float s3 = sr * sr * sr;
+                            const float e = s3 * (s3 - 1.f);
+                            U[s] += e;
+                            Ua[s] += fabsf(e);
+                            Ub[s] = fmaf(sr * s3, fabsf(2.f * s3 - 1.f) * bq, Ub[s]);
                         }
-                    const unsigned who = g.ballot(mine >= 0);
-                    sel = g.bcast(mine, __ffs(who) - 1);
-                    logS = logm[m];
-                }
-            }
-        } else {
-            float bu[T], bmin = INFINITY;
-#pragma unroll
-            for (int s = 0; s < T; ++s) {
-                bu[s] = valid[s] ? (a.beta4 == 0.f ? 0.f : a.beta4 * U[s]) : INFINITY;
-                bmin = fminf(bmin, bu[s]);
-            }
-            bmin = g.min(bmin);
-            if (bmin == INFINITY) {
-                dead_at = i;
-            } else {
-                float wt[T], own = 0.f, err = 0.f;
-#pragma unroll
-                for (int s = 0; s < T; ++s) {
-                    wt[s] = exp2f(-(bu[s] - bmin) * 1.4426950408889634f);
-                    own += wt[s];
-                    // |d(bu)/d(d^2)| = 4 beta eps (3 / sigma^2) s^4 |2 s^6 - 1| per
-                    // pair, the FP32 rounding of the pair terms, and the jump of
-                    // pairs within the band of the cutoff; doubled.
-                    // (Ub already carries each bead's own band.)  Trials of
-                    // zero weight contribute no error (and would give 0 * inf).
-                    const float dbu = a.beta4 * (6.f / a.sig2 * Ub[s] + 1e-6f * Ua[s] +
-                                                 a.ucut2 * (float)ncut[s]);
-                    if (wt[s] > 0.f) err += wt[s] * (dbu + 1.2e-7f * (bu[s] - bmin) + 3e-7f);
-                }
-                const float incl = g.scan(own);
-                const float S = g.bcast(incl, G - 1);
-                const float E = g.sum(err) + S * 6e-8f * (float)(k + 2);
-                const float r = u24f(selw) * S;
-                float P = incl - own;
-                int mine = -1;
-                float lo = 0.f, hi = 0.f;
-#pragma unroll
-                for (int s = 0; s < T; ++s) {
-                    const float Pn = P + wt[s];
-                    if (mine < 0 && Pn > r && wt[s] > 0.f) {
-                        mine = T * g.gl + s;
-                        lo = P;
-                        hi = Pn;
+                        ncut[s] += fabsf(d2 - a.rc2) < bq;
                     }
-                    P = Pn;
                 }
-                const unsigned who = g.ballot(mine >= 0);
-                if (who == 0u) {
+            }
+
+            // ---- 4. weights, selection, error bounds ---------------------------
+            int sel = -1;
+            float logS = 0.f;
+            bool ok = true;
+            if (!LJ) {
+                bool fr[T], flag = false;
+                int cnt = 0;
+#pragma unroll
+                for (int s = 0; s < T; ++s) {
+                    fr[s] = valid[s] && mind[s] >= a.sig2;
+                    flag |= valid[s] && fabsf(mind[s] - a.sig2) < band;
+                    cnt += fr[s];
+                }
+                if (g.ballot(flag)) {
                     ok = false;
                 } else {
-                    const int src = __ffs(who) - 1;
-                    sel = g.bcast(mine, src);
-                    lo = g.bcast(lo, src);
-                    hi = g.bcast(hi, src);
-                    if (!(r - lo > E) || !(hi - r > E)) ok = false;
-                    logS = __logf(S) - bmin;
-                }
-            }
-        }
-
-        // ---- 5. FP64 re-decision of an ambiguous step -------------------
-        if (!ok) {
-            ++rechecks;
-            redecide<G, T, LJ>(a, w, g, chain, i, nn, selw, logm, ehx, ehy, ehz, elx, ely, elz,
-                               sel, logS, dead_at);
-            exact_upto = i - 1;
-        }
-        if (dead_at) break;
-
-        // ---- 6. commit ----------------------------------------------------
-        {
-            const int ss = sel % T;
-            float vx = 0.f, vy = 0.f, vz = 0.f;
+                    const int incl = g.scan(cnt);
+                    const int m = g.bcast(incl, G - 1);
+                    if (m == 0) {
+                        dead_at = i;
+                    } else {
+                        const int idx = (int)__umulhi(selw, (uint32_t)m);
+                        int mine = -1, seen = incl - cnt;
 #pragma unroll
-            for (int s = 0; s < T; ++s)
-                if (s == ss) {
-                    vx = ux[s];
-                    vy = uy[s];
-                    vz = uz[s];
+                        for (int s = 0; s < T; ++s)
+                            if (fr[s]) {
+                                if (seen == idx) mine = T * g.gl + s;
+                                ++seen;
+                            }
+                        const unsigned who = g.ballot(mine >= 0);
+                        sel = g.bcast(mine, __ffs(who) - 1);
+                        logS = logm[m];
+                    }
                 }
-            const int src = sel / T;
-            vx = 0.5f * g.bcast(vx, src);
-            vy = 0.5f * g.bcast(vy, src);
-            vz = 0.5f * g.bcast(vz, src);
-            ff_add(ehx, elx, vx);
-            ff_add(ehy, ely, vy);
-            ff_add(ehz, elz, vz);
-            if (g.gl == 0) {
-                w.hi[i] = make_float4(ehx, ehy, ehz, 0.f);
-                w.lo[i] = make_float4(elx, ely, elz, 0.f);
-                w.tr[i] = (uint8_t)sel;
+            } else {
+                float bu[T], bmin = INFINITY;
+#pragma unroll
+                for (int s = 0; s < T; ++s) {
+                    bu[s] = valid[s] ? (a.beta4 == 0.f ? 0.f : a.beta4 * U[s]) : INFINITY;
+                    bmin = fminf(bmin, bu[s]);
+                }
+                bmin = g.min(bmin);
+                if (bmin == INFINITY) {
+                    dead_at = i;
+                } else {
+                    float wt[T], own = 0.f, err = 0.f;
+#pragma unroll
+                    for (int s = 0; s < T; ++s) {
+                        wt[s] = exp2f(-(bu[s] - bmin) * 1.4426950408889634f);
+                        own += wt[s];
+                        // |d(bu)/d(d^2)| = 4 beta eps (3 / sigma^2) s^4 |2 s^6 - 1| per
+                        // pair, the FP32 rounding of the pair terms, and the jump of
+                        // pairs within the band of the cutoff; doubled.
+                        // (Ub already carries each bead's own band.)  Trials of
+                        // zero weight contribute no error (and would give 0 * inf).
+                        const float dbu = a.beta4 * (6.f / a.sig2 * Ub[s] + 1e-6f * Ua[s] +
+                                                     a.ucut2 * (float)ncut[s]);
+                        if (wt[s] > 0.f) err += wt[s] * (dbu + 1.2e-7f * (bu[s] - bmin) + 3e-7f);
+                    }
+                    const float incl = g.scan(own);
+                    const float S = g.bcast(incl, G - 1);
+                    const float E = g.sum(err) + S * 6e-8f * (float)(k + 2);
+                    const float r = u24f(selw) * S;
+                    float P = incl - own;
+                    int mine = -1;
+                    float lo = 0.f, hi = 0.f;
+#pragma unroll
+                    for (int s = 0; s < T; ++s) {
+                        const float Pn = P + wt[s];
+                        if (mine < 0 && Pn > r && wt[s] > 0.f) {
+                            mine = T * g.gl + s;
+                            lo = P;
+                            hi = Pn;
+                        }
+                        P = Pn;
+                    }
+                    const unsigned who = g.ballot(mine >= 0);
+                    if (who == 0u) {
+                        ok = false;
+                    } else {
+                        const int src = __ffs(who) - 1;
+                        sel = g.bcast(mine, src);
+                        lo = g.bcast(lo, src);
+                        hi = g.bcast(hi, src);
+                        if (!(r - lo > E) || !(hi - r > E)) ok = false;
+                        logS = __logf(S) - bmin;
+                    }
+                }
             }
-            lw += logS;
+
+            // ---- 5. FP64 re-decision of an ambiguous step -------------------
+            if (!ok) {
+                ++rechecks;
+                redecide<G, T, LJ>(a, w, g, chain, aw, i, nn, selw, logm, ehx, ehy, ehz, elx, ely,
+                                   elz, sel, logS, dead_at);
+                exact_upto = i - 1;
+            }
+            if (dead_at) break;
+
+            // ---- 6. commit ----------------------------------------------------
+            {
+                const int ss = sel % T;
+                float vx = 0.f, vy = 0.f, vz = 0.f;
+#pragma unroll
+                for (int s = 0; s < T; ++s)
+                    if (s == ss) {
+                        vx = ux[s];
+                        vy = uy[s];
+                        vz = uz[s];
+                    }
+                const int src = sel / T;
+                vx = 0.5f * g.bcast(vx, src);
+                vy = 0.5f * g.bcast(vy, src);
+                vz = 0.5f * g.bcast(vz, src);
+                ff_add(ehx, elx, vx);
+                ff_add(ehy, ely, vy);
+                ff_add(ehz, elz, vz);
+                if (g.gl == 0) {
+                    w.hi[i] = make_float4(ehx, ehy, ehz, 0.f);
+                    w.lo[i] = make_float4(elx, ely, elz, 0.f);
+                    w.tr[i] = (uint8_t)sel;
+                }
+                lw += logS;
+            }
+            __syncwarp(g.mask);
         }
+        if (!dead_at || att + 1 >= a.max_att) break;
+        ++att;
         __syncwarp(g.mask);
     }
 
+    if (a.attempts && g.gl == 0) a.attempts[c] = (uint16_t)(att + 1);
     if (a.counters && g.gl == 0) {
         if (rechecks) atomicAdd(&a.counters[0], (unsigned long long)rechecks);
         atomicAdd(&a.counters[1], 1ull);
@@ -851,6 +868,9 @@ int offlattice_validate(const rosen_offlattice_params *p, const rosen_offlattice
     if (G != 0 && (p->k + G - 1) / G > 4)
         return set_error(ROSEN_EINVAL,
                          "rosen_offlattice_grow: k = %d needs more than 4 trials per lane", p->k);
+    if (p->max_attempts < 0 || p->max_attempts > ROSEN_MAX_ATTEMPTS)
+        return set_error(ROSEN_EINVAL, "rosen_offlattice_grow: max_attempts = %d outside [0, %d]",
+                         p->max_attempts, ROSEN_MAX_ATTEMPTS);
     return ROSEN_OK;
 }
 
@@ -900,6 +920,8 @@ void offlattice_make_args(const rosen_offlattice_params *p, const rosen_offlatti
     a.trace = (p->flags & ROSEN_STORE_TRACE) ? o->trace : nullptr;
     a.coords = (p->flags & ROSEN_STORE_COORDS) ? o->coords : nullptr;
     a.counters = counters;
+    a.attempts = o->attempts;
+    a.max_att = p->max_attempts > 1 ? (uint32_t)p->max_attempts : 1u;
     memcpy(out, &a, sizeof a);
 }
 

@@ -27,7 +27,8 @@ struct Partial {
     double M;          // max log W in the tile (-inf: no live chain)
     double s[8];       // S0 S1 S2 Q0 Q1a Q2a Q1b Q2b, scaled by exp(-M) / exp(-2M)
     double alive;
-    double pad[2];
+    double n;          // growths in the tile: chains, or their attempts (restart mode)
+    double pad;
 };
 
 struct ReduceArgs {
@@ -39,6 +40,7 @@ struct ReduceArgs {
     const int64_t *n2rg2;
     const float *r2_f;
     const float *rg2_f;
+    const uint16_t *attempts;   // optional: growths per chain (restart mode)
     double logm[8];     // log(m) in FP64, m = 0..6
     double inv_n2;      // 1 / N^2
 };
@@ -94,16 +96,18 @@ __device__ __forceinline__ void merge(double &Ma, double *sa, double &na, double
 // Reduce tile `tile` of the ensemble a into *out (one block of kThreads).
 __device__ __forceinline__ void reduce_tile(const ReduceArgs &a, int64_t tile, Partial *out)
 {
-    __shared__ double red[kThreads / 32][10];
+    __shared__ double red[kThreads / 32][10];   // 9 sums + the growth count
     __shared__ double tileM;
     const int64_t c0 = tile * kTile;
     double lw[kPerThread], A1[kPerThread], A2[kPerThread];
     double m = -INFINITY;
+    double growths = 0.0;   // Eq. 9's sample size: chains, or attempts in restart mode
 #pragma unroll
     for (int q = 0; q < kPerThread; ++q) {
         const int64_t c = c0 + threadIdx.x + (int64_t)q * kThreads;
         if (c < a.C) {
             load_chain(a, c, lw[q], A1[q], A2[q]);
+            growths += a.attempts ? (double)a.attempts[c] : 1.0;
         } else {
             lw[q] = -INFINITY;
             A1[q] = A2[q] = 0.0;
@@ -146,10 +150,14 @@ __device__ __forceinline__ void reduce_tile(const ReduceArgs &a, int64_t tile, P
     for (int q = 0; q < 9; ++q)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) growths += __shfl_xor_sync(0xffffffffu, growths, off);
     __syncthreads();
-    if (lane == 0)
+    if (lane == 0) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) red[warp][q] = s[q];
+        red[warp][9] = growths;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         Partial P;
@@ -159,10 +167,14 @@ __device__ __forceinline__ void reduce_tile(const ReduceArgs &a, int64_t tile, P
             for (int w = 0; w < kThreads / 32; ++w) t += red[w][q];
             P.s[q] = t;
         }
-        double al = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) al += red[w][8];
+        double al = 0.0, ng = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            al += red[w][8];
+            ng += red[w][9];
+        }
         P.alive = al;
-        P.pad[0] = P.pad[1] = 0.0;
+        P.n = ng;
+        P.pad = 0.0;
         *out = P;
     }
 }
@@ -177,12 +189,16 @@ __device__ __forceinline__ void reduce_final(const Partial *part, int64_t ntiles
                                              const ReduceArgs &a, rosen_stats *out)
 {
     __shared__ double sM[kFinalThreads], sS[kFinalThreads][8], sN[kFinalThreads];
-    double M = -INFINITY, S[8] = {0, 0, 0, 0, 0, 0, 0, 0}, na = 0.0;
-    for (int64_t t = threadIdx.x; t < ntiles; t += kFinalThreads)
+    __shared__ double sG[kFinalThreads];
+    double M = -INFINITY, S[8] = {0, 0, 0, 0, 0, 0, 0, 0}, na = 0.0, ng = 0.0;
+    for (int64_t t = threadIdx.x; t < ntiles; t += kFinalThreads) {
         merge(M, S, na, part[t].M, part[t].s, part[t].alive);
+        ng += part[t].n;
+    }
     sM[threadIdx.x] = M;
     for (int q = 0; q < 8; ++q) sS[threadIdx.x][q] = S[q];
     sN[threadIdx.x] = na;
+    sG[threadIdx.x] = ng;
     __syncthreads();
     for (int half = kFinalThreads / 2; half > 0; half >>= 1) {
         if (threadIdx.x < half) {
@@ -194,12 +210,13 @@ __device__ __forceinline__ void reduce_final(const Partial *part, int64_t ntiles
             sM[threadIdx.x] = Ma;
             for (int q = 0; q < 8; ++q) sS[threadIdx.x][q] = Sa[q];
             sN[threadIdx.x] = nA;
+            sG[threadIdx.x] += sG[threadIdx.x + half];
         }
         __syncthreads();
     }
     if (threadIdx.x != 0) return;
     rosen_stats r;
-    r.n = (double)a.C;
+    r.n = sG[0];   // integer-valued partial sums: exact in FP64
     r.n_alive = sN[0];
     r.log_max = sM[0];
     r.S0 = sS[0][0];
@@ -216,7 +233,7 @@ __device__ __forceinline__ void reduce_final(const Partial *part, int64_t ntiles
         r.mean_r2 = r.se_r2 = r.mean_rg2 = r.se_rg2 = NAN;
         r.ess = 0.0;
     } else {
-        r.logZ = r.log_max + log(r.S0 / (double)a.C);
+        r.logZ = r.log_max + log(r.S0 / r.n);
         r.logZ_norm = a.k > 0 ? r.logZ - (double)(a.N - 1) * log((double)a.k) : r.logZ;
         const double m1 = r.S1 / r.S0, m2 = r.S2 / r.S0;
         const double v1 = r.Q2_r2 - 2.0 * m1 * r.Q1_r2 + m1 * m1 * r.Q0;
@@ -286,6 +303,7 @@ void reduce_make_args(const rosen_reduce_in *in, void *out)
     a.n2rg2 = in->n2rg2;
     a.r2_f = in->r2_f;
     a.rg2_f = in->rg2_f;
+    a.attempts = in->attempts;
     for (int q = 0; q < 8; ++q) a.logm[q] = q >= 1 ? log((double)q) : 0.0;
     a.inv_n2 = 1.0 / ((double)in->N * (double)in->N);
     memcpy(out, &a, sizeof a);
@@ -315,6 +333,7 @@ int reduce_launch(const rosen_reduce_in *in, rosen_stats *out, void *part_ws, cu
     a.n2rg2 = in->n2rg2;
     a.r2_f = in->r2_f;
     a.rg2_f = in->rg2_f;
+    a.attempts = in->attempts;
     for (int q = 0; q < 8; ++q) a.logm[q] = q >= 1 ? log((double)q) : 0.0;
     a.inv_n2 = 1.0 / ((double)in->N * (double)in->N);
     const int64_t tiles = reduce_tiles(in->C);

@@ -103,6 +103,7 @@ void request_bytes(const rosen_request &r, size_t *work, size_t *coords)
         b = align256(16 * C) + align256(4 * C) + align256(4 * C) + align256(8 * C);
     else
         b = 3 * align256(4 * C) + align256(C);
+    if (r.max_attempts > 1) b += align256(2 * C);   // attempts per chain (restart mode)
     b += align256(rosen_reduce_workspace_size(r.C)) + align256(sizeof(rosen_stats));
     *work = b;
     *coords = r.store_coords ? align256(12 * N * C) : 0;
@@ -121,6 +122,7 @@ int validate_request(const rosen_request &r)
         p.C = r.C;
         p.beta_eps = r.beta_eps;
         p.flags = r.store_coords ? ROSEN_STORE_COORDS : 0;
+        p.max_attempts = r.max_attempts;
         rosen_lattice_out o;
         memset(&o, 0, sizeof o);
         o.coords = r.store_coords ? reinterpret_cast<int32_t *>(16) : nullptr;
@@ -138,6 +140,7 @@ int validate_request(const rosen_request &r)
     p.cutoff = r.cutoff;
     p.beta_eps = r.beta_eps;
     p.flags = r.store_coords ? ROSEN_STORE_COORDS : 0;
+    p.max_attempts = r.max_attempts;
     rosen_offlattice_out o;
     memset(&o, 0, sizeof o);
     o.coords = r.store_coords ? reinterpret_cast<float *>(16) : nullptr;
@@ -188,6 +191,10 @@ void launch(rosen_server *s, Request *q)
         p += align256(4 * C);
         o.n2rg2 = reinterpret_cast<int64_t *>(p);
         p += align256(8 * C);
+        if (r.max_attempts > 1) {
+            o.attempts = reinterpret_cast<uint16_t *>(p);
+            p += align256(2 * C);
+        }
         o.coords = static_cast<int32_t *>(q->coords);
         rosen_lattice_params lp;
         memset(&lp, 0, sizeof lp);
@@ -197,7 +204,9 @@ void launch(rosen_server *s, Request *q)
         lp.C = r.C;
         lp.beta_eps = r.beta_eps;
         lp.flags = q->coords ? ROSEN_STORE_COORDS : 0;
+        lp.max_attempts = r.max_attempts;
         st = rosen_lattice_grow(&lp, &o, q->stream);
+        in.attempts = o.attempts;
         in.kind = ROSEN_REDUCE_LATTICE;
         in.use_counts = r.beta_eps == 0.0;
         in.logw = o.logw;
@@ -215,6 +224,10 @@ void launch(rosen_server *s, Request *q)
         p += align256(4 * C);
         o.alive = p;
         p += align256(C);
+        if (r.max_attempts > 1) {
+            o.attempts = reinterpret_cast<uint16_t *>(p);
+            p += align256(2 * C);
+        }
         o.coords = static_cast<float *>(q->coords);
         rosen_offlattice_params op;
         memset(&op, 0, sizeof op);
@@ -228,7 +241,9 @@ void launch(rosen_server *s, Request *q)
         op.cutoff = r.cutoff;
         op.beta_eps = r.beta_eps;
         op.flags = q->coords ? ROSEN_STORE_COORDS : 0;
+        op.max_attempts = r.max_attempts;
         st = rosen_offlattice_grow(&op, &o, q->stream);
+        in.attempts = o.attempts;
         in.kind = ROSEN_REDUCE_OFFLATTICE;
         in.k = r.k;
         in.logw = o.logw;

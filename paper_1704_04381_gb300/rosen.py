@@ -43,12 +43,12 @@ class rosen_lattice_params(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("ensemble", ctypes.c_uint32),
                 ("N", ctypes.c_int32), ("C", ctypes.c_int64), ("chain0", ctypes.c_int64),
                 ("beta_eps", ctypes.c_double), ("flags", ctypes.c_uint32),
-                ("lanes_per_chain", ctypes.c_int32)]
+                ("lanes_per_chain", ctypes.c_int32), ("max_attempts", ctypes.c_int32)]
 
 
 class rosen_lattice_out(ctypes.Structure):
     _fields_ = [("counts", _vp), ("logw", _vp), ("r2", _vp), ("n2rg2", _vp),
-                ("trace", _vp), ("coords", _vp)]
+                ("trace", _vp), ("coords", _vp), ("attempts", _vp)]
 
 
 class rosen_offlattice_params(ctypes.Structure):
@@ -56,19 +56,20 @@ class rosen_offlattice_params(ctypes.Structure):
                 ("N", ctypes.c_int32), ("C", ctypes.c_int64), ("chain0", ctypes.c_int64),
                 ("k", ctypes.c_int32), ("potential", ctypes.c_int32), ("sigma", ctypes.c_double),
                 ("cutoff", ctypes.c_double), ("beta_eps", ctypes.c_double),
-                ("flags", ctypes.c_uint32), ("lanes_per_chain", ctypes.c_int32)]
+                ("flags", ctypes.c_uint32), ("lanes_per_chain", ctypes.c_int32),
+                ("max_attempts", ctypes.c_int32)]
 
 
 class rosen_offlattice_out(ctypes.Structure):
     _fields_ = [("logw", _vp), ("r2", _vp), ("rg2", _vp), ("alive", _vp), ("trace", _vp),
-                ("coords", _vp), ("counters", _vp)]
+                ("coords", _vp), ("counters", _vp), ("attempts", _vp)]
 
 
 class rosen_reduce_in(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("N", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("use_counts", ctypes.c_int32), ("C", ctypes.c_int64), ("logw", _vp),
                 ("counts", _vp), ("r2_i", _vp), ("n2rg2", _vp), ("r2_f", _vp),
-                ("rg2_f", _vp)]
+                ("rg2_f", _vp), ("attempts", _vp)]
 
 
 ROSEN_MODEL_LATTICE = 0
@@ -78,7 +79,7 @@ ROSEN_MODEL_OFFLATTICE = 1
 class rosen_ensemble(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("N", ctypes.c_int32), ("C", ctypes.c_int64),
                 ("seed", ctypes.c_uint64), ("ensemble", ctypes.c_uint32), ("k", ctypes.c_int32),
-                ("potential", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("potential", ctypes.c_int32), ("max_attempts", ctypes.c_int32),
                 ("beta_eps", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("cutoff", ctypes.c_double)]
 
@@ -195,7 +196,8 @@ def rosen_lattice_grow(params, out, stream=None):
     """Grow lattice chains.  params: rosen_lattice_params; out: dict of tensors."""
     o = rosen_lattice_out(counts=_ptr(out.get("counts")), logw=_ptr(out.get("logw")),
                           r2=_ptr(out.get("r2")), n2rg2=_ptr(out.get("n2rg2")),
-                          trace=_ptr(out.get("trace")), coords=_ptr(out.get("coords")))
+                          trace=_ptr(out.get("trace")), coords=_ptr(out.get("coords")),
+                          attempts=_ptr(out.get("attempts")))
     _check(load().rosen_lattice_grow(ctypes.byref(params), ctypes.byref(o), _stream(stream)))
 
 
@@ -204,7 +206,8 @@ def rosen_offlattice_grow(params, out, stream=None):
     o = rosen_offlattice_out(logw=_ptr(out.get("logw")), r2=_ptr(out.get("r2")),
                              rg2=_ptr(out.get("rg2")), alive=_ptr(out.get("alive")),
                              trace=_ptr(out.get("trace")), coords=_ptr(out.get("coords")),
-                             counters=_ptr(out.get("counters")))
+                             counters=_ptr(out.get("counters")),
+                             attempts=_ptr(out.get("attempts")))
     _check(load().rosen_offlattice_grow(ctypes.byref(params), ctypes.byref(o), _stream(stream)))
 
 
@@ -234,13 +237,15 @@ def rosen_reduce_noalloc(inp, stats, stream=None):
 
 
 # ---- conveniences (allocation only) ---------------------------------------
-def lattice_params(seed, N, C, beta_eps=0.0, ensemble=0, chain0=0, flags=0, lanes_per_chain=0):
+def lattice_params(seed, N, C, beta_eps=0.0, ensemble=0, chain0=0, flags=0, lanes_per_chain=0,
+                   max_attempts=0):
     return rosen_lattice_params(seed=int(seed), ensemble=int(ensemble), N=int(N), C=int(C),
                                 chain0=int(chain0), beta_eps=float(beta_eps), flags=int(flags),
-                                lanes_per_chain=int(lanes_per_chain))
+                                lanes_per_chain=int(lanes_per_chain),
+                                max_attempts=int(max_attempts))
 
 
-def lattice_outputs(N, C, device="cuda", trace=False, coords=False):
+def lattice_outputs(N, C, device="cuda", trace=False, coords=False, attempts=False):
     """Allocate the per-chain output tensors of rosen_lattice_grow."""
     out = {
         "counts": torch.empty((C, 8), dtype=torch.int16, device=device),
@@ -248,6 +253,8 @@ def lattice_outputs(N, C, device="cuda", trace=False, coords=False):
         "r2": torch.empty(C, dtype=torch.int32, device=device),
         "n2rg2": torch.empty(C, dtype=torch.int64, device=device),
     }
+    if attempts:
+        out["attempts"] = torch.empty(C, dtype=torch.int16, device=device)
     if trace:
         out["trace"] = torch.empty((N - 1, C), dtype=torch.uint8, device=device)
     if coords:
@@ -256,15 +263,18 @@ def lattice_outputs(N, C, device="cuda", trace=False, coords=False):
 
 
 def offlattice_params(seed, N, C, k, potential=ROSEN_HARD_SPHERE, beta_eps=0.0, sigma=1.0,
-                      cutoff=2.5, ensemble=0, chain0=0, flags=0, lanes_per_chain=0):
+                      cutoff=2.5, ensemble=0, chain0=0, flags=0, lanes_per_chain=0,
+                      max_attempts=0):
     return rosen_offlattice_params(seed=int(seed), ensemble=int(ensemble), N=int(N), C=int(C),
                                    chain0=int(chain0), k=int(k), potential=int(potential),
                                    sigma=float(sigma), cutoff=float(cutoff),
                                    beta_eps=float(beta_eps), flags=int(flags),
-                                   lanes_per_chain=int(lanes_per_chain))
+                                   lanes_per_chain=int(lanes_per_chain),
+                                   max_attempts=int(max_attempts))
 
 
-def offlattice_outputs(N, C, device="cuda", trace=False, coords=False, counters=False):
+def offlattice_outputs(N, C, device="cuda", trace=False, coords=False, counters=False,
+                       attempts=False):
     """Allocate the per-chain output tensors of rosen_offlattice_grow."""
     out = {
         "logw": torch.empty(C, dtype=torch.float32, device=device),
@@ -272,6 +282,8 @@ def offlattice_outputs(N, C, device="cuda", trace=False, coords=False, counters=
         "rg2": torch.empty(C, dtype=torch.float32, device=device),
         "alive": torch.empty(C, dtype=torch.uint8, device=device),
     }
+    if attempts:
+        out["attempts"] = torch.empty(C, dtype=torch.int16, device=device)
     if trace:
         out["trace"] = torch.empty((N - 1, C), dtype=torch.uint8, device=device)
     if coords:
@@ -282,17 +294,21 @@ def offlattice_outputs(N, C, device="cuda", trace=False, coords=False, counters=
 
 
 def offlattice_reduce_in(out, N, k):
+    """Reduction inputs of real-space outputs (with their attempts, if any)."""
     C = out["logw"].numel()
     return rosen_reduce_in(kind=ROSEN_REDUCE_OFFLATTICE, N=int(N), k=int(k), use_counts=0, C=C,
                            logw=_ptr(out["logw"]), counts=None, r2_i=None, n2rg2=None,
-                           r2_f=_ptr(out["r2"]), rg2_f=_ptr(out["rg2"]))
+                           r2_f=_ptr(out["r2"]), rg2_f=_ptr(out["rg2"]),
+                           attempts=_ptr(out.get("attempts")))
 
 
 def lattice_reduce_in(out, N, use_counts):
+    """Reduction inputs of lattice outputs (with their attempts, if any)."""
     C = out["logw"].numel()
     return rosen_reduce_in(kind=ROSEN_REDUCE_LATTICE, N=int(N), k=0, use_counts=int(use_counts),
                            C=C, logw=_ptr(out["logw"]), counts=_ptr(out["counts"]),
-                           r2_i=_ptr(out["r2"]), n2rg2=_ptr(out["n2rg2"]), r2_f=None, rg2_f=None)
+                           r2_i=_ptr(out["r2"]), n2rg2=_ptr(out["n2rg2"]), r2_f=None, rg2_f=None,
+                           attempts=_ptr(out.get("attempts")))
 
 
 def stats_tensor(device="cuda"):
@@ -310,11 +326,11 @@ def reduce_workspace(C, device="cuda"):
 
 # ---- batched growth ----------------------------------------------------------
 def ensemble(model, N, C, seed, ensemble_id=0, k=0, potential=ROSEN_HARD_SPHERE, beta_eps=0.0,
-             sigma=1.0, cutoff=2.5):
+             sigma=1.0, cutoff=2.5, max_attempts=0):
     return rosen_ensemble(model=int(model), N=int(N), C=int(C), seed=int(seed),
                           ensemble=int(ensemble_id), k=int(k), potential=int(potential),
-                          reserved=0, beta_eps=float(beta_eps), sigma=float(sigma),
-                          cutoff=float(cutoff))
+                          max_attempts=int(max_attempts), beta_eps=float(beta_eps),
+                          sigma=float(sigma), cutoff=float(cutoff))
 
 
 class RosenBatch:
@@ -342,17 +358,19 @@ class RosenBatch:
 
     def lattice_outputs(self, e, stream=None):
         ens = self.ensembles[e]
-        out = lattice_outputs(ens.N, ens.C)
+        out = lattice_outputs(ens.N, ens.C, attempts=ens.max_attempts > 1)
         o = rosen_lattice_out(counts=_ptr(out["counts"]), logw=_ptr(out["logw"]),
-                              r2=_ptr(out["r2"]), n2rg2=_ptr(out["n2rg2"]))
+                              r2=_ptr(out["r2"]), n2rg2=_ptr(out["n2rg2"]),
+                              attempts=_ptr(out.get("attempts")))
         _check(load().rosen_batch_copy_lattice(self.handle, int(e), ctypes.byref(o), _stream(stream)))
         return out
 
     def offlattice_outputs(self, e, stream=None):
         ens = self.ensembles[e]
-        out = offlattice_outputs(ens.N, ens.C)
+        out = offlattice_outputs(ens.N, ens.C, attempts=ens.max_attempts > 1)
         o = rosen_offlattice_out(logw=_ptr(out["logw"]), r2=_ptr(out["r2"]),
-                                 rg2=_ptr(out["rg2"]), alive=_ptr(out["alive"]))
+                                 rg2=_ptr(out["rg2"]), alive=_ptr(out["alive"]),
+                                 attempts=_ptr(out.get("attempts")))
         _check(load().rosen_batch_copy_offlattice(self.handle, int(e), ctypes.byref(o),
                                                   _stream(stream)))
         return out
@@ -395,7 +413,8 @@ class rosen_request(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("ensemble", ctypes.c_uint32), ("k", ctypes.c_int32),
                 ("potential", ctypes.c_int32), ("store_coords", ctypes.c_int32),
                 ("beta_eps", ctypes.c_double), ("sigma", ctypes.c_double),
-                ("cutoff", ctypes.c_double)]
+                ("cutoff", ctypes.c_double), ("max_attempts", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class rosen_result(ctypes.Structure):
@@ -432,11 +451,12 @@ def _serve_lib():
 
 
 def request(model, N, C, seed, ensemble_id=0, k=0, potential=ROSEN_HARD_SPHERE, beta_eps=0.0,
-            sigma=1.0, cutoff=2.5, store_coords=False):
+            sigma=1.0, cutoff=2.5, store_coords=False, max_attempts=0):
     return rosen_request(model=int(model), N=int(N), C=int(C), seed=int(seed),
                          ensemble=int(ensemble_id), k=int(k), potential=int(potential),
                          store_coords=int(bool(store_coords)), beta_eps=float(beta_eps),
-                         sigma=float(sigma), cutoff=float(cutoff))
+                         sigma=float(sigma), cutoff=float(cutoff),
+                         max_attempts=int(max_attempts), reserved=0)
 
 
 def result_dict(r):

@@ -94,6 +94,7 @@ def _grow(rosen, **kw):
     dict(N=1), dict(N=513), dict(C=-1), dict(chain0=-5), dict(chain0=2 ** 32 - 5, C=10),
     dict(beta_eps=-0.1), dict(beta_eps=float("nan")), dict(beta_eps=float("inf")),
     dict(flags=8), dict(flags=1), dict(flags=2), dict(lanes_per_chain=3),
+    dict(max_attempts=-1), dict(max_attempts=65536),
 ])
 def test_lattice_rejects_bad_parameters(rosen, kw):
     assert _grow(rosen, **kw) == rosen.ROSEN_EINVAL
@@ -151,6 +152,7 @@ def _grow_off(rosen, **kw):
     dict(potential=1, cutoff=0.0), dict(potential=1, cutoff=9.0), dict(potential=1, sigma=0.0),
     dict(beta_eps=-1.0), dict(beta_eps=float("inf")), dict(flags=4), dict(flags=1),
     dict(lanes_per_chain=7), dict(lanes_per_chain=8, k=33),
+    dict(max_attempts=-1), dict(max_attempts=1 << 16),
 ])
 def test_offlattice_rejects_bad_parameters(rosen, kw):
     assert _grow_off(rosen, **kw) == rosen.ROSEN_EINVAL
@@ -163,7 +165,8 @@ def test_offlattice_empty_launch_is_a_no_op(rosen):
 
 @pytest.mark.parametrize("bad", [
     dict(model=2), dict(N=1), dict(C=0), dict(model=0, N=600), dict(model=1, k=0),
-    dict(model=1, potential=5), dict(beta_eps=-1.0),
+    dict(model=1, potential=5), dict(beta_eps=-1.0), dict(max_attempts=-2),
+    dict(model=0, max_attempts=70000),
 ])
 def test_batch_rejects_bad_ensembles(rosen, bad):
     good = dict(model=1, N=16, C=100, seed=1, k=16, potential=1, beta_eps=0.5)
