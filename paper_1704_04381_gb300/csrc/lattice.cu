@@ -31,6 +31,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.cuh"
 
@@ -139,14 +141,17 @@ __device__ __noinline__ int select_fp64(uint32_t freem, uint32_t acc, uint32_t x
     return sel;
 }
 
-// Grow chain c (local index) of the ensemble described by a, in this lane.
-// my points at the lane's column of the [monomer][lane] key array (stride B).
-// In restart mode a trapped growth is thrown away and the chain grown again
-// from the origin with the next attempt index in the step word.
+// Growth number att of chain c (local index) of the ensemble described by a,
+// in this lane.  my points at the lane's column of the [monomer][lane] key
+// array (stride B).  Returns true when the growth was trapped and another
+// attempt is allowed (restart mode): the caller grows the chain again with
+// att + 1 (the outputs then hold nothing final for it).  Otherwise the
+// chain's outputs are written and false is returned.
 template <bool kIsaw>
-__device__ __forceinline__ void lattice_chain(const LatticeArgs &a, int64_t c, uint32_t *my, int B,
-                                              const uint32_t *lut, const uint8_t *seltab,
-                                              const float *wt32, const double *wt64)
+__device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c, uint32_t att,
+                                                uint32_t *my, int B, const uint32_t *lut,
+                                                const uint8_t *seltab, const float *wt32,
+                                                const double *wt64)
 {
     const uint32_t chain = a.chain0 + (uint32_t)c;
     const int N = a.N;
@@ -158,13 +163,12 @@ __device__ __forceinline__ void lattice_chain(const LatticeArgs &a, int64_t c, u
     uint64_t cnt;      // 9-bit field m holds the number of steps with m free sites
     float lw;
     int dead_at;
-    if (a.coords) {
+    if (a.coords && att == 0) {
         a.coords[(0 * 3 + 0) * C + c] = 0;
         a.coords[(0 * 3 + 1) * C + c] = 0;
         a.coords[(0 * 3 + 2) * C + c] = 0;
     }
-    uint32_t att = 0;
-    for (;;) {
+    {
         key = kOriginKey;
         my[0] = key;
         sx = sy = sz = sq = 0;
@@ -240,9 +244,8 @@ __device__ __forceinline__ void lattice_chain(const LatticeArgs &a, int64_t c, u
                 a.coords[((int64_t)i * 3 + 2) * C + c] = ez;
             }
         }
-        if (!dead_at || att + 1 >= a.max_att) break;
-        ++att;
     }
+    if (dead_at && att + 1 < a.max_att) return true;
     if (a.attempts) a.attempts[c] = (uint16_t)(att + 1);
     if (dead_at) cnt += 1ull;   // counts[0] = 1 marks the dead end
     uint32_t cm[7];
@@ -264,7 +267,7 @@ __device__ __forceinline__ void lattice_chain(const LatticeArgs &a, int64_t c, u
         if (a.coords)
             for (int i = dead_at; i < N; ++i)
                 for (int q = 0; q < 3; ++q) a.coords[((int64_t)i * 3 + q) * C + c] = 0;
-        return;
+        return false;
     }
     if (!kIsaw) {
         lw = 0.f;
@@ -276,6 +279,17 @@ __device__ __forceinline__ void lattice_chain(const LatticeArgs &a, int64_t c, u
     if (a.n2rg2)
         a.n2rg2[c] = (int64_t)N * sq -
                      ((int64_t)sx * sx + (int64_t)sy * sy + (int64_t)sz * sz);
+    return false;
+}
+
+// Every growth of chain c in this lane (restart mode regrows in place).
+template <bool kIsaw>
+__device__ __forceinline__ void lattice_chain(const LatticeArgs &a, int64_t c, uint32_t *my, int B,
+                                              const uint32_t *lut, const uint8_t *seltab,
+                                              const float *wt32, const double *wt64)
+{
+    uint32_t att = 0;
+    while (lattice_attempt<kIsaw>(a, c, att, my, B, lut, seltab, wt32, wt64)) ++att;
 }
 
 
@@ -300,6 +314,64 @@ __global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a)
     const int64_t c = (int64_t)blockIdx.x * B + threadIdx.x;
     if (c >= a.C) return;
     lattice_chain<kIsaw>(a, c, keys + threadIdx.x, B, lut, seltab, wt32, wt64);
+}
+
+// Restart mode, single ensemble: a persistent kernel in which every warp owns
+// a contiguous range of chains and grows 32 of them per pass in lock-step.
+// A chain whose growth is trapped goes into the warp's retry queue (at most
+// 32 entries, in shared memory) and is grown again, with the next attempt
+// index, in the warp's next pass next to fresh chains.  No lane waits for a
+// regrowth while the others idle, and no block waits for one warp.
+template <bool kIsaw>
+__global__ void __launch_bounds__(256) lattice_retry_kernel(const LatticeArgs a, int64_t per_warp)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    uint32_t *lut = smem;
+    uint8_t *seltab = reinterpret_cast<uint8_t *>(smem + kLutWords);
+    float *wt32 = reinterpret_cast<float *>(smem + kLutWords + kSelBytes / 4);
+    double *wt64 = reinterpret_cast<double *>(smem + kLutWords + kSelBytes / 4 + 8);
+    const int wpb = blockDim.x / 32, wib = threadIdx.x / 32, lane = threadIdx.x & 31;
+    uint32_t *rq = smem + kLutWords + kSelBytes / 4 + 8 + 16 + (size_t)wib * 64;   // [2][32]
+    uint32_t *keys = smem + kLutWords + kSelBytes / 4 + 8 + 16 + (size_t)wpb * 64 +
+                     (size_t)wib * a.N * 32;
+
+    fill_tables(lut, seltab);
+    if (threadIdx.x < 8) {
+        wt32[threadIdx.x] = a.wt32[threadIdx.x];
+        wt64[threadIdx.x] = a.wt64[threadIdx.x];
+    }
+    __syncthreads();
+
+    const int64_t w = (int64_t)blockIdx.x * wpb + wib;
+    const int64_t hi = (w + 1) * per_warp < a.C ? (w + 1) * per_warp : a.C;
+    int64_t next = w * per_warp;
+    int queued = 0;          // warp-uniform
+    for (;;) {
+        const int take = queued;
+        const int64_t left = hi > next ? hi - next : 0;
+        const int fresh = left < 32 - take ? (int)left : 32 - take;
+        if (take + fresh == 0) break;
+        int64_t c = -1;
+        uint32_t att = 0;
+        if (lane < take) {
+            c = (int64_t)rq[lane];
+            att = rq[32 + lane];
+        } else if (lane < take + fresh) {
+            c = next + (lane - take);
+        }
+        next += fresh;
+        __syncwarp();
+        const bool retry =
+            c >= 0 && lattice_attempt<kIsaw>(a, c, att, keys + lane, 32, lut, seltab, wt32, wt64);
+        const unsigned m = __ballot_sync(0xffffffffu, retry);
+        if (retry) {
+            const int pos = __popc(m & ((1u << lane) - 1u));
+            rq[pos] = (uint32_t)c;
+            rq[32 + pos] = att + 1;
+        }
+        queued = __popc(m);
+        __syncwarp();
+    }
 }
 
 // Persistent batch kernel: blocks take (ensemble, chain range) items from a
@@ -440,6 +512,29 @@ void lattice_batch_launch(const void *dev_args, const BatchItem *items, int n_it
                                                items, n_items, head);
 }
 
+// Restart mode: as many warps as fit on the GPU at once (at most one per 32
+// chains), each with a contiguous range of chains.
+int lattice_retry_launch(const LatticeArgs &a, int N, int B, cudaStream_t s)
+{
+    const int wpb = B / 32;
+    const size_t smem = (size_t)(kLutWords + kSelBytes / 4 + 8 + 16) * 4 +
+                        (size_t)wpb * (64 * 4 + (size_t)N * 32 * 4);
+    auto kern = a.isaw ? lattice_retry_kernel<true> : lattice_retry_kernel<false>;
+    cudaError_t e = allow_max_smem(kern);
+    int bps = 0, dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, B, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return set_error(ROSEN_ECUDA, "rosen_lattice_grow: %s", cudaGetErrorString(e));
+    if (bps < 1) return set_error(ROSEN_ECUDA, "rosen_lattice_grow: kernel does not fit an SM");
+    const int64_t warps = std::min<int64_t>((int64_t)bps * sms * wpb, (a.C + 31) / 32);
+    const int64_t per_warp = (a.C + warps - 1) / warps;
+    const int64_t grid = ((a.C + per_warp - 1) / per_warp + wpb - 1) / wpb;
+    kern<<<(unsigned)grid, B, smem, s>>>(a, per_warp);
+    return check_launch("rosen_lattice_grow");
+}
+
 }  // namespace rosen
 
 using namespace rosen;
@@ -453,9 +548,10 @@ extern "C" int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lat
     LatticeArgs a;
     lattice_make_args(p, o, &a);
     const int B = lattice_block(p->N);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (a.max_att > 1) return lattice_retry_launch(a, p->N, B, s);
     const size_t smem = lattice_smem_bytes(p->N, B);
     const int64_t blocks = (p->C + B - 1) / B;
-    cudaStream_t s = (cudaStream_t)stream;
     if (p->beta_eps == 0.0) {
         allow_max_smem(lattice_lane_kernel<false>);
         lattice_lane_kernel<false><<<(unsigned)blocks, B, smem, s>>>(a);

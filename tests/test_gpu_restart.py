@@ -79,6 +79,20 @@ def test_lattice_restart_bit_exact(rosen, N, C, beta_eps, A):
     assert (err <= (N - 1) * (1e-6 + 6e-8 * np.abs(lw))).all()
 
 
+@pytest.mark.parametrize("C", [1, 31, 33, 1000])
+def test_lattice_restart_small_and_ragged(rosen, C):
+    # The persistent restart kernel splits the chains into per-warp ranges;
+    # tiny and ragged ensembles exercise its empty and partial ranges.  Wide
+    # dead-end odds (N = 300) make every pass carry retries.
+    N = 300
+    g = host(grow_lattice(rosen, 37, N, C, 0.1, 5, coords=True))
+    o = oracle.lattice_run(37, N, C, beta_eps=0.1, trace=True, coords=True, max_attempts=5)
+    np.testing.assert_array_equal(g["attempts"].astype(np.uint16), o["attempts"])
+    np.testing.assert_array_equal(g["counts"].astype(np.int64), o["counts"].astype(np.int64))
+    np.testing.assert_array_equal(g["trace"].T, o["trace"])
+    np.testing.assert_array_equal(g["n2rg2"], o["n2rg2"])
+
+
 def test_single_attempt_equals_plain_growth(rosen):
     N, C = 64, 20_000
     a = host(grow_lattice(rosen, 32, N, C, 0.2, 1))
