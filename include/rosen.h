@@ -56,6 +56,7 @@ extern "C" {
 
 /* ---- limits and flags ------------------------------------------------ */
 #define ROSEN_LATTICE_NMAX 512    /* packed 10-bit lattice coordinates      */
+#define ROSEN_LATTICE_LONG_NMAX 32768 /* rosen_lattice_grow_long            */
 #define ROSEN_OFFLATTICE_NMAX 1024
 #define ROSEN_KMAX 128            /* real-space trials per step             */
 
@@ -141,6 +142,27 @@ typedef struct rosen_lattice_out {
  */
 ROSEN_API int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lattice_out *o,
                        void *stream);
+
+/*
+ * Long chains (Section 4: chains that do not fit in shared memory keep
+ * their coordinates in global memory).  Same rule, draws, parameters and
+ * outputs as rosen_lattice_grow, bit for bit, for 2 <= N <= 32768.  Each
+ * chain's occupied sites live in an open-addressing hash table in
+ * `workspace`, so a step costs O(1) lookups, not a scan of the chain.  A
+ * lane owns one table of 8 * 2^ceil(log2(max(2N, 64))) bytes and grows its
+ * chains one after another.  The call grows min(C, workspace_bytes / table)
+ * chains at a time, so a smaller workspace means fewer chains in flight and
+ * no other change.
+ * workspace: caller-owned device memory, 8-byte aligned; the call zeroes the
+ * part it uses on the stream first, so its contents need not be kept between
+ * calls.  rosen_lattice_long_workspace_size gives the size for
+ * min(C, 131072) tables in flight.
+ * Errors: those of rosen_lattice_grow with N <= 32768; EINVAL for a NULL or
+ * misaligned workspace; ENOMEM if workspace_bytes is below one table.
+ */
+ROSEN_API size_t rosen_lattice_long_workspace_size(int32_t N, int64_t C);
+ROSEN_API int rosen_lattice_grow_long(const rosen_lattice_params *p, const rosen_lattice_out *o,
+                                      void *workspace, size_t workspace_bytes, void *stream);
 
 /* ---- real-space growth (Section 3.3.3, Algorithm 2) ------------------- */
 typedef struct rosen_offlattice_params {

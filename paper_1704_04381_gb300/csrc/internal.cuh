@@ -7,7 +7,8 @@
 namespace rosen {
 
 // ---- lattice.cu ------------------------------------------------------------
-int lattice_validate(const rosen_lattice_params *p, const rosen_lattice_out *o);
+int lattice_validate(const rosen_lattice_params *p, const rosen_lattice_out *o,
+                     int nmax = ROSEN_LATTICE_NMAX, const char *fn = "rosen_lattice_grow");
 size_t lattice_args_size();
 void lattice_make_args(const rosen_lattice_params *p, const rosen_lattice_out *o, void *out);
 size_t lattice_smem_bytes(int N, int B);

@@ -141,6 +141,44 @@ __device__ __noinline__ int select_fp64(uint32_t freem, uint32_t acc, uint32_t x
     return sel;
 }
 
+// The neighbour taken at one step, in slot order, from the free mask, the
+// contact fields of acc (bits 8+3d..10+3d: contacts of neighbour d) and the
+// step's draw x.  Athermal: the idx-th free neighbour, idx = floor(x m / 2^32).
+// Interacting: the smallest slot whose FP32 prefix sum of exp(beta_eps c_d)
+// exceeds r = u24(x) S, re-taken in FP64 when r lies within 2^-18 S of the
+// slot's bounds; log S is added to lw.
+template <bool kIsaw>
+__device__ __forceinline__ int choose(uint32_t freem, int m, uint32_t acc, uint32_t x,
+                                      const uint8_t *seltab, const float *wt32,
+                                      const double *wt64, float &lw)
+{
+    if (!kIsaw) return seltab[(freem << 3) | __umulhi(x, (uint32_t)m)];
+    float w[6], S = 0.f;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        const uint32_t cd = (acc >> (8 + 3 * d)) & 7u;
+        w[d] = ((freem >> d) & 1u) ? wt32[cd] : 0.f;
+        S += w[d];
+    }
+    const float r = u24f(x) * S;
+    float P = 0.f, lo = 0.f, hi = 0.f;
+    int sel = -1;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        const float Pn = P + w[d];
+        if (sel < 0 && Pn > r) {
+            sel = d;
+            lo = P;
+            hi = Pn;
+        }
+        P = Pn;
+    }
+    const float tol = S * 0x1p-18f;
+    if (sel < 0 || !(r - lo > tol) || !(hi - r > tol)) sel = select_fp64(freem, acc, x, wt64);
+    lw += logf(S);
+    return sel;
+}
+
 // Growth number att of chain c (local index) of the ensemble described by a,
 // in this lane.  my points at the lane's column of the [monomer][lane] key
 // array (stride B).  Returns true when the growth was trapped and another
@@ -198,34 +236,7 @@ __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c,
                 break;
             }
             const uint32_t x = philox(make_uint4(chain, a.ens, (uint32_t)i | (att << 16), 0u), a.key).x;
-            int sel;
-            if (!kIsaw) {
-                sel = seltab[(freem << 3) | __umulhi(x, (uint32_t)m)];
-            } else {
-                float w[6], S = 0.f;
-#pragma unroll
-                for (int d = 0; d < 6; ++d) {
-                    const uint32_t cd = (acc >> (8 + 3 * d)) & 7u;
-                    w[d] = ((freem >> d) & 1u) ? wt32[cd] : 0.f;
-                    S += w[d];
-                }
-                const float r = u24f(x) * S;
-                float P = 0.f, lo = 0.f, hi = 0.f;
-                sel = -1;
-#pragma unroll
-                for (int d = 0; d < 6; ++d) {
-                    const float Pn = P + w[d];
-                    if (sel < 0 && Pn > r) {
-                        sel = d;
-                        lo = P;
-                        hi = Pn;
-                    }
-                    P = Pn;
-                }
-                const float tol = S * 0x1p-18f;
-                if (sel < 0 || !(r - lo > tol) || !(hi - r > tol)) sel = select_fp64(freem, acc, x, wt64);
-                lw += logf(S);
-            }
+            const int sel = choose<kIsaw>(freem, m, acc, x, seltab, wt32, wt64, lw);
             cnt += 1ull << (9 * m);
             const uint32_t axis_step = 1u << (10 * (sel >> 1));
             key = (sel & 1) ? key - axis_step : key + axis_step;
@@ -419,6 +430,243 @@ __global__ void __launch_bounds__(256) lattice_batch_kernel(const LatticeArgs *_
     }
 }
 
+// ---- long chains: occupied sites in a per-chain hash table in HBM ---------
+//
+// Beyond a few hundred monomers the O(i) scan of the shared-memory kernel
+// dominates and the packed 10-bit keys run out.  Here every lane keeps its
+// chain's occupied sites in an open-addressing hash table (linear probing)
+// in device memory: a step looks up the six neighbours of the end (and, when
+// interacting, the 18 sites at lattice distance 2 that decide the contacts)
+// in O(1) each, whatever i is.  Site keys pack 17 bits per axis
+// (x + 2^16 | (y + 2^16) << 17 | (z + 2^16) << 34); bits 51..63 of an entry
+// hold the generation of the growth that wrote it, so a lane reuses its
+// table for the next chain without clearing it: entries of older generations
+// read as empty.  Tables hold at least 2N entries (load <= 1/2), so every
+// probe sequence ends at an empty slot.
+constexpr int kGenShift = 51;
+constexpr uint64_t kSiteMask = (1ull << kGenShift) - 1ull;
+constexpr uint32_t kGenMax = 8191;
+constexpr int64_t kAxisOff = 1 << 16;
+
+__device__ __forceinline__ uint64_t site_key(int x, int y, int z)
+{
+    return (uint64_t)(x + kAxisOff) | ((uint64_t)(y + kAxisOff) << 17) |
+           ((uint64_t)(z + kAxisOff) << 34);
+}
+
+// Key offset of neighbour d in slot order +x, -x, +y, -y, +z, -z.
+__device__ __forceinline__ uint64_t nb_off(int d)
+{
+    const uint64_t unit = 1ull << (17 * (d >> 1));
+    return (d & 1) ? (0ull - unit) : unit;
+}
+
+__device__ __forceinline__ uint32_t site_slot(uint64_t key, int logH)
+{
+    return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - logH));
+}
+
+// Continue the probe that read entry e at slot h: true if the site `want`
+// (key with this growth's tag) is in the table; otherwise h ends on the
+// empty slot where the site would be inserted.
+__device__ __forceinline__ bool probe_rest(const uint64_t *tab, uint32_t hmask, uint64_t want,
+                                           uint64_t tag, uint32_t &h, uint64_t e)
+{
+    while ((e & ~kSiteMask) == tag) {
+        if (e == want) return true;
+        h = (h + 1u) & hmask;
+        e = tab[h];
+    }
+    return false;
+}
+
+// Occupancy of six sites end + off(q): first probes issued together, then
+// resolved; bit q of the result is set for an occupied site.
+template <class Off>
+__device__ __forceinline__ uint32_t probe6(const uint64_t *tab, uint32_t hmask, int logH,
+                                           uint64_t end, uint64_t tag, Off off, uint32_t *hout)
+{
+    uint32_t h[6];
+    uint64_t e[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        h[q] = site_slot(end + off(q), logH);
+        e[q] = tab[h[q]];
+    }
+    uint32_t occ = 0u;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        if (probe_rest(tab, hmask, (end + off(q)) | tag, tag, h[q], e[q])) occ |= 1u << q;
+        if (hout) hout[q] = h[q];
+    }
+    return occ;
+}
+
+// The 12 sites at lattice distance 2 off the axes: pair p of axes (x,y),
+// (x,z), (y,z) with signs sa, sb: index 4p + 2sa + sb.
+__device__ __forceinline__ uint64_t diag_off(int q)
+{
+    const int p = q >> 2, sa = (q >> 1) & 1, sb = q & 1;
+    const int ax = p == 2 ? 1 : 0, bx = p == 0 ? 1 : 2;
+    return nb_off(2 * ax + sa) + nb_off(2 * bx + sb);
+}
+
+// Diagonal sites next to neighbour d (4 of the 12), as a 12-bit mask.
+__host__ __device__ constexpr uint32_t diag_mask(int d)
+{
+    uint32_t m = 0u;
+    for (int q = 0; q < 12; ++q) {
+        const int p = q >> 2, sa = (q >> 1) & 1, sb = q & 1;
+        const int ax = p == 2 ? 1 : 0, bx = p == 0 ? 1 : 2;
+        if ((2 * ax + sa) == d || (2 * bx + sb) == d) m |= 1u << q;
+    }
+    return m;
+}
+
+// Growth number att of chain c with the sites in the lane's table tab
+// (2^logH entries).  Same rule, draws and outputs as lattice_attempt.
+template <bool kIsaw>
+__device__ __forceinline__ bool long_attempt(const LatticeArgs &a, int64_t c, uint32_t att,
+                                             uint64_t *tab, int logH, uint32_t &gen,
+                                             const uint8_t *seltab, const float *wt32,
+                                             const double *wt64)
+{
+    const uint32_t chain = a.chain0 + (uint32_t)c;
+    const int N = a.N;
+    const int64_t C = a.C;
+    const uint32_t hmask = (1u << logH) - 1u;
+
+    if (++gen > kGenMax) {          // generation tags exhausted: clear the table
+        for (uint32_t h = 0; h <= hmask; ++h) tab[h] = 0ull;
+        gen = 1;
+    }
+    const uint64_t tag = (uint64_t)gen << kGenShift;
+    uint64_t end = site_key(0, 0, 0);
+    {
+        uint32_t h = site_slot(end, logH);
+        while ((tab[h] & ~kSiteMask) == tag) h = (h + 1u) & hmask;
+        tab[h] = end | tag;
+    }
+    if (a.coords && att == 0) {
+        a.coords[(0 * 3 + 0) * C + c] = 0;
+        a.coords[(0 * 3 + 1) * C + c] = 0;
+        a.coords[(0 * 3 + 2) * C + c] = 0;
+    }
+    int ex = 0, ey = 0, ez = 0;
+    int64_t sx = 0, sy = 0, sz = 0, sq = 0;
+    uint64_t cnt_lo = 0ull, cnt_hi = 0ull;   // 16-bit fields: m = 0..3 | 4..7
+    float lw = 0.f;
+    int dead_at = 0;
+
+    for (int i = 1; i < N; ++i) {
+        uint32_t hfree[6];
+        const uint32_t occ = probe6(tab, hmask, logH, end, tag, [](int q) { return nb_off(q); },
+                                    hfree);
+        uint32_t acc = occ;
+        if (kIsaw) {
+            const uint32_t far = probe6(tab, hmask, logH, end, tag,
+                                        [](int q) { return nb_off(q) + nb_off(q); }, nullptr);
+            const uint32_t dlo = probe6(tab, hmask, logH, end, tag,
+                                        [](int q) { return diag_off(q); }, nullptr);
+            const uint32_t dhi = probe6(tab, hmask, logH, end, tag,
+                                        [](int q) { return diag_off(q + 6); }, nullptr);
+            const uint32_t diag = dlo | (dhi << 6);
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                const uint32_t cd = ((far >> d) & 1u) + __popc(diag & diag_mask(d));
+                acc |= cd << (8 + 3 * d);
+            }
+        }
+        const uint32_t freem = ~occ & 63u;
+        const int m = __popc(freem);
+        if (m == 0) {
+            dead_at = i;
+            break;
+        }
+        const uint32_t x = philox(make_uint4(chain, a.ens, (uint32_t)i | (att << 16), 0u), a.key).x;
+        const int sel = choose<kIsaw>(freem, m, acc, x, seltab, wt32, wt64, lw);
+        if (m < 4) cnt_lo += 1ull << (16 * m);
+        else cnt_hi += 1ull << (16 * (m - 4));
+        uint32_t hs = 0u;
+#pragma unroll
+        for (int d = 0; d < 6; ++d)
+            if (d == sel) hs = hfree[d];
+        end += nb_off(sel);
+        tab[hs] = end | tag;
+        const int step = (sel & 1) ? -1 : 1;
+        if ((sel >> 1) == 0) ex += step;
+        else if ((sel >> 1) == 1) ey += step;
+        else ez += step;
+        sx += ex;
+        sy += ey;
+        sz += ez;
+        sq += (int64_t)ex * ex + (int64_t)ey * ey + (int64_t)ez * ez;
+        if (a.trace) a.trace[(int64_t)(i - 1) * C + c] = (uint8_t)((m << 3) | sel);
+        if (a.coords) {
+            a.coords[((int64_t)i * 3 + 0) * C + c] = ex;
+            a.coords[((int64_t)i * 3 + 1) * C + c] = ey;
+            a.coords[((int64_t)i * 3 + 2) * C + c] = ez;
+        }
+    }
+    if (dead_at && att + 1 < a.max_att) return true;
+    if (a.attempts) a.attempts[c] = (uint16_t)(att + 1);
+    if (dead_at) cnt_lo += 1ull;   // counts[0] = 1 marks the dead end
+    if (a.counts)
+        a.counts[c] = make_uint4((uint32_t)cnt_lo, (uint32_t)(cnt_lo >> 32), (uint32_t)cnt_hi,
+                                 (uint32_t)(cnt_hi >> 32));
+    if (dead_at) {
+        if (a.logw) a.logw[c] = -INFINITY;
+        if (a.r2) a.r2[c] = 0;
+        if (a.n2rg2) a.n2rg2[c] = 0;
+        if (a.trace) {
+            a.trace[(int64_t)(dead_at - 1) * C + c] = 7u;
+            for (int i = dead_at + 1; i < N; ++i) a.trace[(int64_t)(i - 1) * C + c] = 0xFFu;
+        }
+        if (a.coords)
+            for (int i = dead_at; i < N; ++i)
+                for (int q = 0; q < 3; ++q) a.coords[((int64_t)i * 3 + q) * C + c] = 0;
+        return false;
+    }
+    if (!kIsaw) {
+        lw = 0.f;
+#pragma unroll
+        for (int q = 2; q <= 6; ++q) {
+            const uint32_t cm = (uint32_t)(((q < 4 ? cnt_lo : cnt_hi) >> (16 * (q & 3))) & 0xFFFFu);
+            lw += (float)cm * a.logm[q];
+        }
+    }
+    if (a.logw) a.logw[c] = lw;
+    if (a.r2) a.r2[c] = ex * ex + ey * ey + ez * ez;
+    if (a.n2rg2) a.n2rg2[c] = (int64_t)N * sq - (sx * sx + sy * sy + sz * sz);
+    return false;
+}
+
+// One lane per chain at a time; lane l grows chains l, l + lanes, ... in its
+// own table (2^logH entries at ws + l 2^logH).
+template <bool kIsaw>
+__global__ void __launch_bounds__(256) lattice_long_kernel(const LatticeArgs a, uint64_t *ws,
+                                                           int64_t lanes, int logH)
+{
+    __shared__ uint8_t seltab[kSelBytes];
+    __shared__ float wt32[8];
+    __shared__ double wt64[8];
+    for (int q = threadIdx.x; q < kSelBytes; q += blockDim.x)
+        seltab[q] = nth_set_bit((uint32_t)q >> 3, (uint32_t)q & 7u);
+    if (threadIdx.x < 8) {
+        wt32[threadIdx.x] = a.wt32[threadIdx.x];
+        wt64[threadIdx.x] = a.wt64[threadIdx.x];
+    }
+    __syncthreads();
+    const int64_t lane = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (lane >= lanes) return;
+    uint64_t *tab = ws + (lane << logH);
+    uint32_t gen = 0;
+    for (int64_t c = lane; c < a.C; c += lanes) {
+        uint32_t att = 0;
+        while (long_attempt<kIsaw>(a, c, att, tab, logH, gen, seltab, wt32, wt64)) ++att;
+    }
+}
+
 }  // namespace
 
 size_t lattice_smem_bytes(int N, int B)
@@ -437,30 +685,31 @@ int lattice_block(int N)
     return B;
 }
 
-int lattice_validate(const rosen_lattice_params *p, const rosen_lattice_out *o)
+int lattice_validate(const rosen_lattice_params *p, const rosen_lattice_out *o, int nmax,
+                     const char *fn)
 {
-    if (!p || !o) return set_error(ROSEN_EINVAL, "rosen_lattice_grow: NULL params or outputs");
-    if (p->N < 2 || p->N > ROSEN_LATTICE_NMAX)
-        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: N = %d outside [2, %d]", p->N,
-                         ROSEN_LATTICE_NMAX);
+    if (!p || !o) return set_error(ROSEN_EINVAL, "%s: NULL params or outputs", fn);
+    if (p->N < 2 || p->N > nmax)
+        return set_error(ROSEN_EINVAL, "%s: N = %d outside [2, %d]", fn, p->N,
+                         nmax);
     if (p->C < 0 || p->chain0 < 0 || p->chain0 + p->C > (int64_t(1) << 32))
-        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: chains [%lld, %lld) outside [0, 2^32)",
+        return set_error(ROSEN_EINVAL, "%s: chains [%lld, %lld) outside [0, 2^32)", fn,
                          (long long)p->chain0, (long long)(p->chain0 + p->C));
     if (!(p->beta_eps >= 0.0) || !isfinite(p->beta_eps))
-        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: beta_eps must be finite and >= 0");
+        return set_error(ROSEN_EINVAL, "%s: beta_eps must be finite and >= 0", fn);
     if (p->flags & ~(ROSEN_STORE_TRACE | ROSEN_STORE_COORDS))
-        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: unknown flags 0x%x", p->flags);
+        return set_error(ROSEN_EINVAL, "%s: unknown flags 0x%x", fn, p->flags);
     if (p->lanes_per_chain != 0 && p->lanes_per_chain != 1)
-        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: lanes_per_chain must be 0 or 1");
+        return set_error(ROSEN_EINVAL, "%s: lanes_per_chain must be 0 or 1", fn);
     if (p->max_attempts < 0 || p->max_attempts > ROSEN_MAX_ATTEMPTS)
-        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: max_attempts = %d outside [0, %d]",
+        return set_error(ROSEN_EINVAL, "%s: max_attempts = %d outside [0, %d]", fn,
                          p->max_attempts, ROSEN_MAX_ATTEMPTS);
     if ((p->flags & ROSEN_STORE_TRACE) && !o->trace)
-        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: ROSEN_STORE_TRACE without trace");
+        return set_error(ROSEN_EINVAL, "%s: ROSEN_STORE_TRACE without trace", fn);
     if ((p->flags & ROSEN_STORE_COORDS) && !o->coords)
-        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: ROSEN_STORE_COORDS without coords");
+        return set_error(ROSEN_EINVAL, "%s: ROSEN_STORE_COORDS without coords", fn);
     if (o->counts && (reinterpret_cast<uintptr_t>(o->counts) & 15u))
-        return set_error(ROSEN_EINVAL, "rosen_lattice_grow: counts must be 16-byte aligned");
+        return set_error(ROSEN_EINVAL, "%s: counts must be 16-byte aligned", fn);
     return ROSEN_OK;
 }
 
@@ -561,3 +810,56 @@ extern "C" int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lat
     }
     return check_launch("rosen_lattice_grow");
 }
+
+// ---- long chains -------------------------------------------------------------
+namespace {
+
+constexpr int64_t kLongLanes = 1 << 17;   // tables the default workspace holds
+
+// log2 of the table entries per lane: >= 2N (load <= 1/2) and >= 64.
+int long_log_entries(int N)
+{
+    int lg = 6;
+    while ((int64_t(1) << lg) < 2 * (int64_t)N) ++lg;
+    return lg;
+}
+
+}  // namespace
+
+extern "C" size_t rosen_lattice_long_workspace_size(int32_t N, int64_t C)
+{
+    if (N < 2 || N > ROSEN_LATTICE_LONG_NMAX || C < 1) return 0;
+    const int64_t lanes = C < kLongLanes ? C : kLongLanes;
+    return (size_t)lanes * ((size_t)8 << long_log_entries(N));
+}
+
+extern "C" int rosen_lattice_grow_long(const rosen_lattice_params *p, const rosen_lattice_out *o,
+                                       void *workspace, size_t workspace_bytes, void *stream)
+{
+    const int st = lattice_validate(p, o, ROSEN_LATTICE_LONG_NMAX, "rosen_lattice_grow_long");
+    if (st != ROSEN_OK) return st;
+    if (p->C == 0) return ROSEN_OK;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 7u))
+        return set_error(ROSEN_EINVAL, "rosen_lattice_grow_long: workspace must be a non-NULL, "
+                                       "8-byte aligned device pointer");
+    const int logH = long_log_entries(p->N);
+    const size_t table = (size_t)8 << logH;
+    int64_t lanes = (int64_t)(workspace_bytes / table);
+    if (lanes > p->C) lanes = p->C;
+    if (lanes < 1)
+        return set_error(ROSEN_ENOMEM,
+                         "rosen_lattice_grow_long: workspace of %zu bytes holds no table of %zu "
+                         "bytes (N = %d)", workspace_bytes, table, p->N);
+    LatticeArgs a;
+    lattice_make_args(p, o, &a);
+    cudaStream_t s = (cudaStream_t)stream;
+    const cudaError_t e = cudaMemsetAsync(workspace, 0, (size_t)lanes * table, s);
+    if (e != cudaSuccess)
+        return set_error(ROSEN_ECUDA, "rosen_lattice_grow_long: %s", cudaGetErrorString(e));
+    const unsigned grid = (unsigned)((lanes + 255) / 256);
+    uint64_t *ws = static_cast<uint64_t *>(workspace);
+    if (a.isaw) lattice_long_kernel<true><<<grid, 256, 0, s>>>(a, ws, lanes, logH);
+    else lattice_long_kernel<false><<<grid, 256, 0, s>>>(a, ws, lanes, logH);
+    return check_launch("rosen_lattice_grow_long");
+}
+

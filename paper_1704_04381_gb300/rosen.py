@@ -16,6 +16,8 @@ from . import build as _build
 ROSEN_OK, ROSEN_EINVAL, ROSEN_ENOMEM, ROSEN_ECUDA = 0, 1, 2, 3
 ROSEN_ETIMEOUT, ROSEN_EBUSY, ROSEN_EAGAIN, ROSEN_ECLOSED, ROSEN_ENOTFOUND = 4, 5, 6, 7, 8
 ROSEN_LATTICE_NMAX = 512
+ROSEN_LATTICE_LONG_NMAX = 32768
+ROSEN_MAX_ATTEMPTS = 65535
 ROSEN_OFFLATTICE_NMAX = 1024
 ROSEN_KMAX = 128
 ROSEN_STORE_TRACE = 1
@@ -113,6 +115,12 @@ def load():
     L.rosen_lattice_grow.argtypes = [ctypes.POINTER(rosen_lattice_params),
                                      ctypes.POINTER(rosen_lattice_out), _vp]
     L.rosen_lattice_grow.restype = ctypes.c_int
+    L.rosen_lattice_long_workspace_size.argtypes = [ctypes.c_int32, ctypes.c_int64]
+    L.rosen_lattice_long_workspace_size.restype = ctypes.c_size_t
+    L.rosen_lattice_grow_long.argtypes = [ctypes.POINTER(rosen_lattice_params),
+                                          ctypes.POINTER(rosen_lattice_out), _vp, ctypes.c_size_t,
+                                          _vp]
+    L.rosen_lattice_grow_long.restype = ctypes.c_int
     L.rosen_offlattice_grow.argtypes = [ctypes.POINTER(rosen_offlattice_params),
                                         ctypes.POINTER(rosen_offlattice_out), _vp]
     L.rosen_offlattice_grow.restype = ctypes.c_int
@@ -199,6 +207,27 @@ def rosen_lattice_grow(params, out, stream=None):
                           trace=_ptr(out.get("trace")), coords=_ptr(out.get("coords")),
                           attempts=_ptr(out.get("attempts")))
     _check(load().rosen_lattice_grow(ctypes.byref(params), ctypes.byref(o), _stream(stream)))
+
+
+def rosen_lattice_long_workspace_size(N, C):
+    return int(load().rosen_lattice_long_workspace_size(int(N), int(C)))
+
+
+def lattice_long_workspace(N, C, device="cuda"):
+    """Allocate the hash-table workspace of rosen_lattice_grow_long."""
+    nbytes = rosen_lattice_long_workspace_size(N, C)
+    return torch.empty(max(nbytes, 8) // 8, dtype=torch.int64, device=device)
+
+
+def rosen_lattice_grow_long(params, out, workspace, stream=None):
+    """Grow long lattice chains (N <= 32768) with per-chain hash tables in workspace."""
+    o = rosen_lattice_out(counts=_ptr(out.get("counts")), logw=_ptr(out.get("logw")),
+                          r2=_ptr(out.get("r2")), n2rg2=_ptr(out.get("n2rg2")),
+                          trace=_ptr(out.get("trace")), coords=_ptr(out.get("coords")),
+                          attempts=_ptr(out.get("attempts")))
+    _check(load().rosen_lattice_grow_long(ctypes.byref(params), ctypes.byref(o), _ptr(workspace),
+                                          workspace.numel() * workspace.element_size(),
+                                          _stream(stream)))
 
 
 def rosen_offlattice_grow(params, out, stream=None):
