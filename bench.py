@@ -86,12 +86,17 @@ def offlattice_ops(N, k, chains, listed):
             (OFF_TRIAL_OPS * k + OFF_STEP_OPS) * (N - 1) * chains)
 
 
-def sm_max_mhz():
+def measured_peak(key, fallback):
+    """A figure of the measured peaks file (fallback when it is missing)."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
-            return float(json.load(f).get("sm_max_mhz", 2070.0))
-    return 2070.0
+            return float(json.load(f).get(key, fallback))
+    return fallback
+
+
+def sm_max_mhz():
+    return measured_peak("sm_max_mhz", 2070.0)
 
 
 class ClockSampler:
@@ -525,6 +530,73 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_long(args):
+    """Long lattice chains through rosen_lattice_grow_long (hash tables of
+    occupied sites in device memory), on the paper's global-memory workload:
+    10^6 chains at each N.  value = nominal insertions C (N - 1) per second;
+    grown = the steps the chains actually made before any dead end."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1704_04381_gb300 import rosen
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    Cl = args.chains or 1_000_000
+    Ns = [int(v) for v in args.long_n.split(",")]
+    parts, tot_ins, tot_ms, tot_grown, tot_lookups = {}, 0, 0.0, 0, 0
+    with ClockSampler(0) as clocks:
+        for Nl in Ns:
+            out = rosen.lattice_outputs(Nl, Cl)
+            ws = rosen.lattice_long_workspace(Nl, Cl)
+            p = rosen.lattice_params(11, Nl, Cl, beta_eps=args.long_beta_eps)
+            st = rosen.stats_tensor()
+            rws = rosen.reduce_workspace(Cl)
+            rin = rosen.lattice_reduce_in(out, Nl, use_counts=int(args.long_beta_eps == 0.0))
+            for _ in range(max(1, args.warmup)):
+                rosen.rosen_lattice_grow_long(p, out, ws, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                rosen.rosen_lattice_grow_long(p, out, ws, stream)
+                rosen.rosen_reduce(rin, st, rws, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            grown = int(out["counts"].to(torch.int64)[:, 1:7].sum())
+            sd = rosen.stats_dict(st)
+            ins = Cl * (Nl - 1)
+            lookups = 6 if args.long_beta_eps == 0.0 else 24
+            parts["N%d" % Nl] = {
+                "ms": ms, "insertions_per_s": ins / (ms / 1e3),
+                "grown_steps_per_s": grown / (ms / 1e3), "grown_steps": grown,
+                "alive_frac": sd["n_alive"] / Cl, "logZ": sd["logZ"], "mean_r2": sd["mean_r2"],
+                "workspace_gb": ws.numel() * 8 / 1e9}
+            tot_ins += ins
+            tot_ms += ms
+            tot_grown += grown
+            tot_lookups += grown * (lookups + 1)
+            del out, ws
+            torch.cuda.empty_cache()
+    # Each lookup and each insert touches one 32-byte sector of a table.
+    gbs = tot_lookups * 32 / (tot_ms / 1e3) / 1e9
+    peak = measured_peak("hbm_gbs", 6800.0)
+    line = {
+        "metric": "long-chain lattice insertions/s (hash tables in HBM)",
+        "value": tot_ins / (tot_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True,
+        "dtype": "int32+fp32", "data": "synthetic",
+        "config": {"workload": "lattice, beta*eps %g, N in %s, %d chains each"
+                               % (args.long_beta_eps, Ns, Cl)},
+        "parts": parts,
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                     "frac": gbs / peak, "traffic": None,
+                     "basis": "one 32 B sector per table lookup and per insert, grown steps"},
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_served(args):
     import random
     import torch
@@ -616,7 +688,7 @@ def main():
     ap.add_argument("--lattice-only", action="store_true")
     ap.add_argument("--chains", type=int, default=None,
                     help="chains per ensemble (default 10^7); smaller values are for profiling")
-    ap.add_argument("--workload", default="step", choices=["step", "batched", "served"])
+    ap.add_argument("--workload", default="step", choices=["step", "batched", "served", "long"])
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="scale of the chain counts in the batched/served modes")
     ap.add_argument("--rate", type=float, default=2000.0, help="served: arrivals per second")
@@ -625,7 +697,11 @@ def main():
     ap.add_argument("--max-queue", type=int, default=256)
     ap.add_argument("--max-attempts", type=int, default=0,
                     help="step: restart mode, growths per chain (0/1: dead ends keep W = 0)")
+    ap.add_argument("--long-n", default="1000,10000", help="long: chain lengths")
+    ap.add_argument("--long-beta-eps", type=float, default=0.0)
     args = ap.parse_args()
+    if args.workload == "long":
+        return run_long(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "served":

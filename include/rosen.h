@@ -58,6 +58,7 @@ extern "C" {
 #define ROSEN_LATTICE_NMAX 512    /* packed 10-bit lattice coordinates      */
 #define ROSEN_LATTICE_LONG_NMAX 32768 /* rosen_lattice_grow_long            */
 #define ROSEN_OFFLATTICE_NMAX 1024
+#define ROSEN_OFFLATTICE_LONG_NMAX 16384 /* rosen_offlattice_grow_long      */
 #define ROSEN_KMAX 128            /* real-space trials per step             */
 
 #define ROSEN_MAX_ATTEMPTS 65535  /* restart mode: growths per chain        */
@@ -223,6 +224,31 @@ typedef struct rosen_offlattice_out {
  */
 ROSEN_API int rosen_offlattice_grow(const rosen_offlattice_params *p,
                                     const rosen_offlattice_out *o, void *stream);
+
+/*
+ * Long real-space chains (Section 4: chains that do not fit in shared memory
+ * keep their coordinates in global memory).  Same rule, draws, parameters,
+ * exactness and outputs as rosen_offlattice_grow, for 2 <= N <= 16384 and
+ * lanes_per_chain 0, 16 or 32.  Each chain slot keeps its positions, trace
+ * and near list in `workspace`, and files its beads in a hash table of
+ * spatial cells (side just above the list radius).  A step visits the 27
+ * cells around the end instead of every earlier bead.  The near list is put
+ * in bead order, so a chain's arithmetic is that of rosen_offlattice_grow
+ * with the same lanes per chain, and its outputs are identical.
+ * As many chains are grown at once as the workspace holds slots of
+ * (rosen_offlattice_long_workspace_size(N, 1)) bytes, at most as many as are
+ * resident on the GPU.
+ * workspace: caller-owned device memory, 16-byte aligned; the call zeroes
+ * the part it uses on the stream first.  rosen_offlattice_long_workspace_size
+ * gives the size for min(C, 9728) slots.
+ * Errors: those of rosen_offlattice_grow with N <= 16384; EINVAL for
+ * lanes_per_chain 8 or a NULL or misaligned workspace; ENOMEM if the
+ * workspace holds no slot.
+ */
+ROSEN_API size_t rosen_offlattice_long_workspace_size(int32_t N, int64_t C);
+ROSEN_API int rosen_offlattice_grow_long(const rosen_offlattice_params *p,
+                                         const rosen_offlattice_out *o, void *workspace,
+                                         size_t workspace_bytes, void *stream);
 
 /*
  * The FP32 unit vectors the real-space kernels use as trial directions

@@ -17,7 +17,9 @@ void lattice_batch_launch(const void *dev_args, const BatchItem *items, int n_it
                           int B, size_t smem, int grid, cudaStream_t s);
 
 // ---- offlattice.cu ---------------------------------------------------------
-int offlattice_validate(const rosen_offlattice_params *p, const rosen_offlattice_out *o);
+int offlattice_validate(const rosen_offlattice_params *p, const rosen_offlattice_out *o,
+                        int nmax = ROSEN_OFFLATTICE_NMAX,
+                        const char *fn = "rosen_offlattice_grow");
 size_t offlattice_args_size();
 void offlattice_make_args(const rosen_offlattice_params *p, const rosen_offlattice_out *o,
                           unsigned long long *counters, void *out);

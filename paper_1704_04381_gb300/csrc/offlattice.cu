@@ -28,686 +28,11 @@
 
 #include "common.cuh"
 #include "internal.cuh"
+#include "offlattice_chain.cuh"
 
 namespace rosen {
 namespace {
 
-constexpr double kPi = 3.14159265358979323846;
-
-struct OffArgs {
-    PhiloxKeys key;
-    uint32_t ens, chain0;
-    int32_t N, k;
-    int64_t C;
-    float sig2, rc2, rf2, rf;  // sigma^2, cutoff^2, list radius^2 (with margin), list radius
-    float beta4;               // 4 beta eps (LJ)
-    float dband;               // HS: sigma (the distance at which decisions flip); LJ: cutoff
-    float ucut2;               // 2 |s^6 (s^6 - 1)| at the cutoff: energy jump (doubled)
-    double sig2d, rc2d, beta_eps;
-    float *logw, *r2, *rg2;
-    uint8_t *alive, *trace;
-    float *coords;
-    unsigned long long *counters;   // optional [3]: steps re-decided, chains, listed beads
-    uint16_t *attempts;             // optional [C]
-    uint32_t max_att;               // growths per chain (1: no restart)
-};
-
-// Per-chain shared memory: float-float positions, the near list, the trace.
-// Rounded up to 16 bytes so that every chain's float4 arrays stay aligned.
-// (The per-bead band array exists only for Lennard-Jones chains.)
-__host__ __device__ inline size_t chain_smem_bytes(int N, bool lj)
-{
-    const size_t n = (size_t)N;
-    const size_t b = 3 * n * sizeof(float4) + n * sizeof(int) + (lj ? n * sizeof(float) : 0) + n;
-    return (b + 15) & ~size_t(15);
-}
-
-struct ChainSmem {
-    float4 *hi, *lo;   // positions (x, y, z, -)
-    float4 *nl;        // near list: g.x, g.y, g.z, 1 + |g|^2
-    int *nj;           // near list: bead index
-    float *nb;         // near list: bound on |d^2 (FP32) - d^2 (FP64)| for this bead
-    uint8_t *tr;       // chosen trial of each step
-};
-
-__device__ inline ChainSmem carve(unsigned char *base, int N, bool lj)
-{
-    ChainSmem w;
-    w.hi = reinterpret_cast<float4 *>(base);
-    w.lo = w.hi + N;
-    w.nl = w.lo + N;
-    w.nj = reinterpret_cast<int *>(w.nl + N);
-    w.nb = reinterpret_cast<float *>(w.nj + N);
-    w.tr = reinterpret_cast<uint8_t *>(lj ? w.nb + N : w.nb);
-    return w;
-}
-
-// Bound on |d^2 (FP32) - d^2 (FP64)| for a trial against a listed bead with
-// displacement g (|g| = gn, 1 + |g|^2 = c) whose position drifted for D steps
-// since it was last exact.  d^2 = c + 2 u.g differs from the exact value by
-// 2 (g + u).dg + 2 g.du + rounding, with |du| <= 4e-7 per direction (the
-// exhaustively measured component error is 2.7e-7; z is exact), |dg| <=
-// D 4e-7 + 2.1e-7 |g| (drift plus the rounding of g), |g + u| <= dmax (sigma
-// at the hard-sphere decision, min(1 + |g|, cutoff) for LJ), and three FMA
-// roundings of values up to 2c.  Doubled for safety.
-__device__ __forceinline__ float pair_band(float gn, float c, int D, float dmax)
-{
-    const float dg = (float)D * 4e-7f + 2.1e-7f * gn;
-    return 2.f * (2.f * dmax * dg + 2.f * gn * 4e-7f + 3.6e-7f * c);
-}
-
-// sin and cos of 2 pi V / 2^24 for a 24-bit integer V.  The quarter-turn
-// reduction is exact integer arithmetic: V = q 2^22 + r with r in
-// [-2^21, 2^21), so the angle is q (pi/2) + pi y with y = r / 2^23 exact in
-// FP32 and |y| <= 1/4.  sin(pi y) and cos(pi y) are their Taylor series
-// truncated after y^9 and y^10 (remainders below 2e-9), evaluated by Horner's
-// rule in FP32; the quadrant q only swaps and negates.
-__device__ __forceinline__ void sincos_turn24(uint32_t V, float &sn, float &cs)
-{
-    constexpr float S1 = (float)kPi;
-    constexpr float S3 = (float)(-kPi * kPi * kPi / 6.0);
-    constexpr float S5 = (float)(kPi * kPi * kPi * kPi * kPi / 120.0);
-    constexpr float S7 = (float)(-kPi * kPi * kPi * kPi * kPi * kPi * kPi / 5040.0);
-    constexpr float S9 = (float)(kPi * kPi * kPi * kPi * kPi * kPi * kPi * kPi * kPi / 362880.0);
-    constexpr float C2 = (float)(-kPi * kPi / 2.0);
-    constexpr float C4 = (float)(kPi * kPi * kPi * kPi / 24.0);
-    constexpr float C6 = (float)(-kPi * kPi * kPi * kPi * kPi * kPi / 720.0);
-    constexpr float C8 = (float)(kPi * kPi * kPi * kPi * kPi * kPi * kPi * kPi / 40320.0);
-    constexpr float C10 =
-        (float)(-kPi * kPi * kPi * kPi * kPi * kPi * kPi * kPi * kPi * kPi / 3628800.0);
-    const uint32_t qn = (V + (1u << 21)) >> 22;
-    const int32_t r = (int32_t)V - (int32_t)(qn << 22);
-    const float y = (float)r * 0x1p-23f;
-    const float y2 = y * y;
-    const float ps = fmaf(fmaf(fmaf(fmaf(S9, y2, S7), y2, S5), y2, S3), y2, S1) * y;
-    const float pc = fmaf(fmaf(fmaf(fmaf(fmaf(C10, y2, C8), y2, C6), y2, C4), y2, C2), y2, 1.f);
-    const uint32_t q = qn & 3u;
-    const float a = (q & 1u) ? pc : ps;
-    const float b = (q & 1u) ? ps : pc;
-    sn = (q & 2u) ? -a : a;
-    cs = ((q + 1u) & 2u) ? -b : b;
-}
-
-// Trial direction from two words (the reading of "rngonsphere"):
-// z = 1 - 2 u24(a), phi = 2 pi u24(b), s = sqrt((1-z)(1+z)).  (1-z), (1+z) are
-// exact in FP32; sqrtf is correctly rounded.
-__device__ __forceinline__ float3 dir32(uint32_t a, uint32_t b)
-{
-    const float z = 1.f - 2.f * u24f(a);
-    const float s = sqrtf((1.f - z) * (1.f + z));
-    float sn, cs;
-    sincos_turn24(b >> 8, sn, cs);
-    return make_float3(s * cs, s * sn, z);
-}
-
-__device__ __forceinline__ void dir64(uint32_t a, uint32_t b, double &x, double &y, double &z)
-{
-    z = 1.0 - 2.0 * u24d(a);
-    const double s = sqrt((1.0 - z) * (1.0 + z));
-    double sn, cs;
-    sincospi(2.0 * u24d(b), &sn, &cs);
-    x = s * cs;
-    y = s * sn;
-}
-
-// Words of trial t inside its draw: slot 1 + t/2, pair (0,1) or (2,3).
-__device__ __forceinline__ void trial_words(const uint4 &x, int t, uint32_t &a, uint32_t &b)
-{
-    a = (t & 1) ? x.z : x.x;
-    b = (t & 1) ? x.w : x.y;
-}
-
-// Error-free sum of a float into a float-float value (Knuth's TwoSum).
-__device__ __forceinline__ void ff_add(float &hi, float &lo, float v)
-{
-    const float s = hi + v;
-    const float bp = s - hi;
-    const float e = (hi - (s - bp)) + (v - bp);
-    const float t = lo + e;
-    hi = s + t;
-    lo = t - (hi - s);
-}
-
-template <int G>
-struct Group {
-    unsigned mask;   // the group's lanes in the warp
-    int gl;          // lane within the group
-    int base;        // first lane of the group in the warp
-
-    __device__ Group()
-    {
-        const int lane = threadIdx.x & 31;
-        gl = lane & (G - 1);
-        base = lane - gl;
-        mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << base);
-    }
-    __device__ unsigned ballot(bool p) const
-    {
-        const unsigned b = __ballot_sync(mask, p);
-        return (G == 32) ? b : (b >> base) & ((1u << G) - 1u);
-    }
-    template <class V>
-    __device__ V bcast(V v, int src) const
-    {
-        return __shfl_sync(mask, v, src, G);
-    }
-    __device__ float min(float v) const
-    {
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(mask, v, o, G));
-        return v;
-    }
-    __device__ double min(double v) const
-    {
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(mask, v, o, G));
-        return v;
-    }
-    __device__ float max(float v) const
-    {
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o, G));
-        return v;
-    }
-    __device__ float sum(float v) const
-    {
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
-        return v;
-    }
-    template <class V>
-    __device__ V scan(V v) const   // inclusive prefix sum over the group
-    {
-#pragma unroll
-        for (int o = 1; o < G; o <<= 1) {
-            const V u = __shfl_up_sync(mask, v, o, G);
-            if (gl >= o) v += u;
-        }
-        return v;
-    }
-};
-
-// FP64 replay of r_1 .. r_{i-1} from the chosen trials; the exact positions
-// are stored back into the float-float arrays and the end returned.
-template <int G>
-__device__ __noinline__ void replay_positions(const OffArgs &a, const ChainSmem &w,
-                                              const Group<G> &g, uint32_t chain, uint32_t aw,
-                                              int i, double &ex, double &ey, double &ez)
-{
-    double cx = 0.0, cy = 0.0, cz = 0.0;
-    for (int b0 = 1; b0 <= i - 1; b0 += G) {
-        const int s = b0 + g.gl;
-        double x = 0.0, y = 0.0, z = 0.0;
-        if (s <= i - 1) {
-            const int t = w.tr[s];
-            const uint4 q =
-                philox(make_uint4(chain, a.ens, (uint32_t)s | aw, 1u + (uint32_t)(t >> 1)), a.key);
-            uint32_t wa, wb;
-            trial_words(q, t, wa, wb);
-            dir64(wa, wb, x, y, z);
-        }
-        x = g.scan(x) + cx;
-        y = g.scan(y) + cy;
-        z = g.scan(z) + cz;
-        if (s <= i - 1) {
-            const float hx = (float)x, hy = (float)y, hz = (float)z;
-            w.hi[s] = make_float4(hx, hy, hz, 0.f);
-            w.lo[s] = make_float4((float)(x - hx), (float)(y - hy), (float)(z - hz), 0.f);
-        }
-        cx = g.bcast(x, G - 1);
-        cy = g.bcast(y, G - 1);
-        cz = g.bcast(z, G - 1);
-    }
-    __syncwarp(g.mask);
-    ex = cx;
-    ey = cy;
-    ez = cz;
-}
-
-// FP64 re-decision of step i: replay the exact positions, recompute every
-// trial's free flag or energy in FP64 from the listed beads, and select with
-// the sequential FP64 arithmetic of the definition.
-template <int G, int T, bool LJ>
-__device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, const Group<G> &g,
-                                      uint32_t chain, uint32_t aw, int i, int nn, uint32_t selw,
-                                      const float *logm, float &ehx, float &ehy, float &ehz,
-                                      float &elx, float &ely, float &elz, int &sel, float &logS,
-                                      int &dead_at)
-{
-    const int k = a.k;
-    double ex, ey, ez;
-    replay_positions<G>(a, w, g, chain, aw, i, ex, ey, ez);
-    // The exact end, back into the float-float registers.
-    ehx = (float)ex;
-    elx = (float)(ex - ehx);
-    ehy = (float)ey;
-    ely = (float)(ey - ehy);
-    ehz = (float)ez;
-    elz = (float)(ez - ehz);
-    double val[T];
-#pragma unroll
-    for (int s = 0; s < T; ++s) {
-        const int t = T * g.gl + s;
-        const uint4 xx =
-            philox(make_uint4(chain, a.ens, (uint32_t)i | aw, 1u + (uint32_t)(t >> 1)), a.key);
-        uint32_t wa, wb;
-        trial_words(xx, t, wa, wb);
-        double dx, dy, dz;
-        dir64(wa, wb, dx, dy, dz);
-        const double tx = ex + dx, ty = ey + dy, tz = ez + dz;
-        double acc = 0.0;
-        bool fr = true;
-        for (int q = 0; q < nn; ++q) {
-            const int j = w.nj[q];
-            const float4 h = w.hi[j], l = w.lo[j];
-            const double rx = tx - ((double)h.x + (double)l.x);
-            const double ry = ty - ((double)h.y + (double)l.y);
-            const double rz = tz - ((double)h.z + (double)l.z);
-            const double d2 = rx * rx + ry * ry + rz * rz;
-            if (!LJ) {
-                if (d2 < a.sig2d) fr = false;
-            } else if (d2 < a.rc2d) {
-                // sigma^2 / d^2 by two Newton steps from the FP32 reciprocal
-                // (FP64 division is a long instruction sequence on this part).
-                double rcp = (double)__frcp_rn((float)d2);
-                rcp = rcp * fma(-d2, rcp, 2.0);
-                rcp = rcp * fma(-d2, rcp, 2.0);
-                const double sr = a.sig2d * rcp;
-                const double s3 = sr * sr * sr;
-                acc += 4.0 * s3 * (s3 - 1.0);
-            }
-        }
-        const bool valid = t < k;
-        if (!valid) val[s] = LJ ? INFINITY : 0.0;
-        else if (!LJ) val[s] = fr ? 1.0 : 0.0;
-        else val[s] = (a.beta_eps == 0.0) ? 0.0 : a.beta_eps * acc;
-    }
-    if (!LJ) {
-        int cnt = 0;
-#pragma unroll
-        for (int s = 0; s < T; ++s) cnt += val[s] > 0.0;
-        const int incl = g.scan(cnt);
-        const int m = g.bcast(incl, G - 1);
-        if (m == 0) {
-            dead_at = i;
-        } else {
-            const int idx = (int)__umulhi(selw, (uint32_t)m);
-            int mine = -1, seen = incl - cnt;
-#pragma unroll
-            for (int s = 0; s < T; ++s)
-                if (val[s] > 0.0) {
-                    if (seen == idx) mine = T * g.gl + s;
-                    ++seen;
-                }
-            const unsigned who = g.ballot(mine >= 0);
-            sel = g.bcast(mine, __ffs(who) - 1);
-            logS = logm[m];
-        }
-    } else {
-        double bmin = INFINITY;
-#pragma unroll
-        for (int s = 0; s < T; ++s) bmin = fmin(bmin, val[s]);
-        bmin = g.min(bmin);
-        if (bmin == INFINITY) {
-            dead_at = i;
-        } else {
-            double wv[T];
-#pragma unroll
-            for (int s = 0; s < T; ++s) wv[s] = exp(-(val[s] - bmin));
-            // Sequential FP64 sum and prefix in trial order, as the
-            // definition states them; every lane walks the trials.
-            double S = 0.0, r = 0.0, P = 0.0;
-            int pick = -1, lastpos = -1;
-            for (int pass = 0; pass < 2; ++pass) {
-                for (int t = 0; t < k; ++t) {
-                    double v = 0.0;
-#pragma unroll
-                    for (int s = 0; s < T; ++s)
-                        if (s == t % T) v = wv[s];
-                    v = g.bcast(v, t / T);
-                    if (pass == 0) {
-                        S += v;
-                        if (v > 0.0) lastpos = t;
-                    } else if (pick < 0) {
-                        P += v;
-                        if (P > r) pick = t;
-                    }
-                }
-                if (pass == 0) r = u24d(selw) * S;
-            }
-            sel = pick >= 0 ? pick : lastpos;
-            logS = (float)(log(S) - bmin);
-        }
-    }
-}
-
-// Grow chain c (local index) of the ensemble a with the G lanes of group g,
-// in the per-chain shared memory w.  In restart mode a growth that reaches a
-// dead end is thrown away and the chain grown again from bead 0, with the
-// attempt index in the high half of the step word.
-template <int G, int T, bool LJ>
-__device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const ChainSmem &w,
-                                          const Group<G> &g, const float *logm)
-{
-    const int N = a.N, k = a.k;
-    const uint32_t chain = a.chain0 + (uint32_t)c;
-
-    if (g.gl == 0) {
-        w.hi[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        w.lo[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    float ehx, ehy, ehz, elx, ely, elz;
-    float lw;
-    int dead_at;
-    int exact_upto;   // beads 0..exact_upto are exact (r_0; after a replay at step i: all < i)
-    unsigned rechecks = 0;
-    unsigned long long listed = 0;
-    uint32_t att = 0;
-    for (;;) {
-        const uint32_t aw = att << 16;
-        ehx = ehy = ehz = elx = ely = elz = 0.f;
-        lw = 0.f;
-        dead_at = 0;
-        exact_upto = 0;
-
-        for (int i = 1; i < N; ++i) {
-            // ---- 1. near list (ascending bead index) --------------------------
-            int nn = 0;
-            float band = 0.f;    // largest bead band of the step (hard spheres)
-            for (int b0 = 0; b0 <= i - 2; b0 += G) {
-                const int j = b0 + g.gl;
-                float4 L = make_float4(0.f, 0.f, 0.f, 0.f);
-                bool near = false;
-                if (j <= i - 2) {
-                    const float4 h = w.hi[j], l = w.lo[j];
-                    const float gx = (ehx - h.x) + (elx - l.x);
-                    const float gy = (ehy - h.y) + (ely - l.y);
-                    const float gz = (ehz - h.z) + (elz - l.z);
-                    const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-                    L = make_float4(gx, gy, gz, 1.f + g2);
-                    near = g2 < a.rf2;
-                }
-                const unsigned m = g.ballot(near);
-                if (near) {
-                    const int slot = nn + __popc(m & ((1u << g.gl) - 1u));
-                    w.nl[slot] = L;
-                    w.nj[slot] = j;
-                    if (LJ) {
-                        const float gn = sqrtf(L.w - 1.f) * 1.001f + 1e-6f;
-                        w.nb[slot] =
-                            pair_band(gn, L.w, i - 1 - max(j, exact_upto), fminf(1.f + gn, a.dband));
-                    }
-                }
-                nn += __popc(m);
-            }
-            listed += (unsigned)nn;
-            __syncwarp(g.mask);
-            if (!LJ && nn > 0) {
-                // One band for the step: the oldest listed bead drifted longest, and
-                // |g| <= sqrt(rf2), c <= 1 + rf2 for every listed bead.
-                const int D = i - 1 - max(w.nj[0], exact_upto);
-                band = pair_band(a.rf, 1.f + a.rf2, D, a.dband);
-            }
-
-            // ---- 2. trials ----------------------------------------------------
-            float ux[T], uy[T], uz[T];
-            bool valid[T];
-            uint32_t selw = 0;
-            uint4 x = make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-            for (int s = 0; s < T; ++s) {
-                const int t = T * g.gl + s;
-                valid[s] = t < k;
-                if (T == 1 || (s & 1) == 0)
-                    x = philox(make_uint4(chain, a.ens, (uint32_t)i | aw, 1u + (uint32_t)(t >> 1)),
-                               a.key);
-                if (s == 0)
-                    selw = (x.x & 0xFFu) | ((x.y & 0xFFu) << 8) | ((x.z & 0xFFu) << 16) |
-                           ((x.w & 0xFFu) << 24);
-                uint32_t wa, wb;
-                trial_words(x, t, wa, wb);
-                const float3 u = dir32(wa, wb);
-                ux[s] = 2.f * u.x;   // 2u: d^2 = c + (2u).g
-                uy[s] = 2.f * u.y;
-                uz[s] = 2.f * u.z;
-            }
-            selw = g.bcast(selw, 0);
-
-            // ---- 3. pair loop -----------------------------------------------
-            float mind[T], U[T], Ub[T], Ua[T];
-            int ncut[T];
-#pragma unroll
-            for (int s = 0; s < T; ++s) {
-                mind[s] = INFINITY;
-                U[s] = 0.f;
-                Ub[s] = 0.f;
-                Ua[s] = 0.f;
-                ncut[s] = 0;
-            }
-#pragma unroll 2
-            for (int q = 0; q < nn; ++q) {
-                const float4 L = w.nl[q];
-                const float bq = LJ ? w.nb[q] : 0.f;
-#pragma unroll
-                for (int s = 0; s < T; ++s) {
-                    const float d2 = fmaf(ux[s], L.x, fmaf(uy[s], L.y, fmaf(uz[s], L.z, L.w)));
-                    if (!LJ) {
-                        mind[s] = fminf(mind[s], d2);
-                    } else {
-                        if (d2 < a.rc2) {
-                            const float sr = __fdividef(a.sig2, d2);
-                            const float s3 = sr * sr * sr;
-                            const float e = s3 * (s3 - 1.f);
-                            U[s] += e;
-                            Ua[s] += fabsf(e);
-                            Ub[s] = fmaf(sr * s3, fabsf(2.f * s3 - 1.f) * bq, Ub[s]);
-                        }
-                        ncut[s] += fabsf(d2 - a.rc2) < bq;
-                    }
-                }
-            }
-
-            // ---- 4. weights, selection, error bounds ---------------------------
-            int sel = -1;
-            float logS = 0.f;
-            bool ok = true;
-            if (!LJ) {
-                bool fr[T], flag = false;
-                int cnt = 0;
-#pragma unroll
-                for (int s = 0; s < T; ++s) {
-                    fr[s] = valid[s] && mind[s] >= a.sig2;
-                    flag |= valid[s] && fabsf(mind[s] - a.sig2) < band;
-                    cnt += fr[s];
-                }
-                if (g.ballot(flag)) {
-                    ok = false;
-                } else {
-                    const int incl = g.scan(cnt);
-                    const int m = g.bcast(incl, G - 1);
-                    if (m == 0) {
-                        dead_at = i;
-                    } else {
-                        const int idx = (int)__umulhi(selw, (uint32_t)m);
-                        int mine = -1, seen = incl - cnt;
-#pragma unroll
-                        for (int s = 0; s < T; ++s)
-                            if (fr[s]) {
-                                if (seen == idx) mine = T * g.gl + s;
-                                ++seen;
-                            }
-                        const unsigned who = g.ballot(mine >= 0);
-                        sel = g.bcast(mine, __ffs(who) - 1);
-                        logS = logm[m];
-                    }
-                }
-            } else {
-                float bu[T], bmin = INFINITY;
-#pragma unroll
-                for (int s = 0; s < T; ++s) {
-                    bu[s] = valid[s] ? (a.beta4 == 0.f ? 0.f : a.beta4 * U[s]) : INFINITY;
-                    bmin = fminf(bmin, bu[s]);
-                }
-                bmin = g.min(bmin);
-                if (bmin == INFINITY) {
-                    dead_at = i;
-                } else {
-                    float wt[T], own = 0.f, err = 0.f;
-#pragma unroll
-                    for (int s = 0; s < T; ++s) {
-                        wt[s] = exp2f(-(bu[s] - bmin) * 1.4426950408889634f);
-                        own += wt[s];
-                        // |d(bu)/d(d^2)| = 4 beta eps (3 / sigma^2) s^4 |2 s^6 - 1| per
-                        // pair, the FP32 rounding of the pair terms, and the jump of
-                        // pairs within the band of the cutoff; doubled.
-                        // (Ub already carries each bead's own band.)  Trials of
-                        // zero weight contribute no error (and would give 0 * inf).
-                        const float dbu = a.beta4 * (6.f / a.sig2 * Ub[s] + 1e-6f * Ua[s] +
-                                                     a.ucut2 * (float)ncut[s]);
-                        if (wt[s] > 0.f) err += wt[s] * (dbu + 1.2e-7f * (bu[s] - bmin) + 3e-7f);
-                    }
-                    const float incl = g.scan(own);
-                    const float S = g.bcast(incl, G - 1);
-                    const float E = g.sum(err) + S * 6e-8f * (float)(k + 2);
-                    const float r = u24f(selw) * S;
-                    float P = incl - own;
-                    int mine = -1;
-                    float lo = 0.f, hi = 0.f;
-#pragma unroll
-                    for (int s = 0; s < T; ++s) {
-                        const float Pn = P + wt[s];
-                        if (mine < 0 && Pn > r && wt[s] > 0.f) {
-                            mine = T * g.gl + s;
-                            lo = P;
-                            hi = Pn;
-                        }
-                        P = Pn;
-                    }
-                    const unsigned who = g.ballot(mine >= 0);
-                    if (who == 0u) {
-                        ok = false;
-                    } else {
-                        const int src = __ffs(who) - 1;
-                        sel = g.bcast(mine, src);
-                        lo = g.bcast(lo, src);
-                        hi = g.bcast(hi, src);
-                        if (!(r - lo > E) || !(hi - r > E)) ok = false;
-                        logS = __logf(S) - bmin;
-                    }
-                }
-            }
-
-            // ---- 5. FP64 re-decision of an ambiguous step -------------------
-            if (!ok) {
-                ++rechecks;
-                redecide<G, T, LJ>(a, w, g, chain, aw, i, nn, selw, logm, ehx, ehy, ehz, elx, ely,
-                                   elz, sel, logS, dead_at);
-                exact_upto = i - 1;
-            }
-            if (dead_at) break;
-
-            // ---- 6. commit ----------------------------------------------------
-            {
-                const int ss = sel % T;
-                float vx = 0.f, vy = 0.f, vz = 0.f;
-#pragma unroll
-                for (int s = 0; s < T; ++s)
-                    if (s == ss) {
-                        vx = ux[s];
-                        vy = uy[s];
-                        vz = uz[s];
-                    }
-                const int src = sel / T;
-                vx = 0.5f * g.bcast(vx, src);
-                vy = 0.5f * g.bcast(vy, src);
-                vz = 0.5f * g.bcast(vz, src);
-                ff_add(ehx, elx, vx);
-                ff_add(ehy, ely, vy);
-                ff_add(ehz, elz, vz);
-                if (g.gl == 0) {
-                    w.hi[i] = make_float4(ehx, ehy, ehz, 0.f);
-                    w.lo[i] = make_float4(elx, ely, elz, 0.f);
-                    w.tr[i] = (uint8_t)sel;
-                }
-                lw += logS;
-            }
-            __syncwarp(g.mask);
-        }
-        if (!dead_at || att + 1 >= a.max_att) break;
-        ++att;
-        __syncwarp(g.mask);
-    }
-
-    if (a.attempts && g.gl == 0) a.attempts[c] = (uint16_t)(att + 1);
-    if (a.counters && g.gl == 0) {
-        if (rechecks) atomicAdd(&a.counters[0], (unsigned long long)rechecks);
-        atomicAdd(&a.counters[1], 1ull);
-        atomicAdd(&a.counters[2], listed);
-    }
-    const int64_t C = a.C;
-    if (dead_at) {
-        if (g.gl == 0) {
-            if (a.logw) a.logw[c] = -INFINITY;
-            if (a.r2) a.r2[c] = 0.f;
-            if (a.rg2) a.rg2[c] = 0.f;
-            if (a.alive) a.alive[c] = 0;
-        }
-        if (a.trace)
-            for (int s = 1 + g.gl; s < N; s += G)
-                a.trace[(int64_t)(s - 1) * C + c] =
-                    s < dead_at ? w.tr[s] : (s == dead_at ? 0xFEu : 0xFFu);
-        if (a.coords)
-            for (int s = g.gl; s < N; s += G) {
-                const bool keep = s < dead_at;
-                const float4 h = w.hi[s], l = w.lo[s];
-                a.coords[((int64_t)s * 3 + 0) * C + c] = keep ? h.x + l.x : 0.f;
-                a.coords[((int64_t)s * 3 + 1) * C + c] = keep ? h.y + l.y : 0.f;
-                a.coords[((int64_t)s * 3 + 2) * C + c] = keep ? h.z + l.z : 0.f;
-            }
-        return;
-    }
-    // Observables: R_ee^2 and R_g^2 about the centre of mass.
-    float sx = 0.f, sy = 0.f, sz = 0.f;
-    for (int s = g.gl; s < N; s += G) {
-        const float4 h = w.hi[s], l = w.lo[s];
-        sx += h.x + l.x;
-        sy += h.y + l.y;
-        sz += h.z + l.z;
-    }
-    const float inv = 1.f / (float)N;
-    const float mx = g.sum(sx) * inv, my = g.sum(sy) * inv, mz = g.sum(sz) * inv;
-    float gg = 0.f;
-    for (int s = g.gl; s < N; s += G) {
-        const float4 h = w.hi[s], l = w.lo[s];
-        const float dx = (h.x - mx) + l.x, dy = (h.y - my) + l.y, dz = (h.z - mz) + l.z;
-        gg += dx * dx + dy * dy + dz * dz;
-    }
-    gg = g.sum(gg) * inv;
-    if (g.gl == 0) {
-        const float xe = ehx + elx, ye = ehy + ely, ze = ehz + elz;
-        if (a.logw) a.logw[c] = lw;
-        if (a.r2) a.r2[c] = xe * xe + ye * ye + ze * ze;
-        if (a.rg2) a.rg2[c] = gg;
-        if (a.alive) a.alive[c] = 1;
-    }
-    if (a.trace)
-        for (int s = 1 + g.gl; s < N; s += G) a.trace[(int64_t)(s - 1) * C + c] = w.tr[s];
-    if (a.coords)
-        for (int s = g.gl; s < N; s += G) {
-            const float4 h = w.hi[s], l = w.lo[s];
-            a.coords[((int64_t)s * 3 + 0) * C + c] = h.x + l.x;
-            a.coords[((int64_t)s * 3 + 1) * C + c] = h.y + l.y;
-            a.coords[((int64_t)s * 3 + 2) * C + c] = h.z + l.z;
-        }
-}
-
-
-constexpr int kTable = 132;   // log m, m = 0..131: 528 bytes keep per-chain areas aligned
-
-__device__ __forceinline__ void fill_log_table(float *logm)
-{
-    for (int q = threadIdx.x; q < kTable; q += blockDim.x) logm[q] = q ? logf((float)q) : 0.f;
-}
 
 template <int G, int T, bool LJ>
 __global__ void __launch_bounds__(256, 4) offlattice_group_kernel(const OffArgs a, int chains_per_block)
@@ -832,44 +157,45 @@ BatchFn pick_batch(int G, int T, bool lj)
 
 }  // namespace
 
-int offlattice_validate(const rosen_offlattice_params *p, const rosen_offlattice_out *o)
+int offlattice_validate(const rosen_offlattice_params *p, const rosen_offlattice_out *o, int nmax,
+                        const char *fn)
 {
-    if (!p || !o) return set_error(ROSEN_EINVAL, "rosen_offlattice_grow: NULL params or outputs");
-    if (p->N < 2 || p->N > ROSEN_OFFLATTICE_NMAX)
-        return set_error(ROSEN_EINVAL, "rosen_offlattice_grow: N = %d outside [2, %d]", p->N,
-                         ROSEN_OFFLATTICE_NMAX);
+    if (!p || !o) return set_error(ROSEN_EINVAL, "%s: NULL params or outputs", fn);
+    if (p->N < 2 || p->N > nmax)
+        return set_error(ROSEN_EINVAL, "%s: N = %d outside [2, %d]", fn, p->N,
+                         nmax);
     if (p->k < 1 || p->k > ROSEN_KMAX)
-        return set_error(ROSEN_EINVAL, "rosen_offlattice_grow: k = %d outside [1, %d]", p->k,
+        return set_error(ROSEN_EINVAL, "%s: k = %d outside [1, %d]", fn, p->k,
                          ROSEN_KMAX);
     if (p->C < 0 || p->chain0 < 0 || p->chain0 + p->C > (int64_t(1) << 32))
         return set_error(ROSEN_EINVAL,
-                         "rosen_offlattice_grow: chains [%lld, %lld) outside [0, 2^32)",
+                         "%s: chains [%lld, %lld) outside [0, 2^32)", fn,
                          (long long)p->chain0, (long long)(p->chain0 + p->C));
     if (p->potential != ROSEN_HARD_SPHERE && p->potential != ROSEN_LJ)
-        return set_error(ROSEN_EINVAL, "rosen_offlattice_grow: unknown potential %d", p->potential);
+        return set_error(ROSEN_EINVAL, "%s: unknown potential %d", fn, p->potential);
     if (!(p->sigma >= 0.0) || !isfinite(p->sigma) || p->sigma > 4.0)
-        return set_error(ROSEN_EINVAL, "rosen_offlattice_grow: sigma must lie in [0, 4]");
+        return set_error(ROSEN_EINVAL, "%s: sigma must lie in [0, 4]", fn);
     if (p->potential == ROSEN_LJ &&
         (!(p->cutoff > 0.0) || !isfinite(p->cutoff) || p->cutoff > 8.0 || p->sigma <= 0.0))
         return set_error(ROSEN_EINVAL,
-                         "rosen_offlattice_grow: LJ needs sigma > 0 and 0 < cutoff <= 8");
+                         "%s: LJ needs sigma > 0 and 0 < cutoff <= 8", fn);
     if (!(p->beta_eps >= 0.0) || !isfinite(p->beta_eps))
-        return set_error(ROSEN_EINVAL, "rosen_offlattice_grow: beta_eps must be finite and >= 0");
+        return set_error(ROSEN_EINVAL, "%s: beta_eps must be finite and >= 0", fn);
     if (p->flags & ~(ROSEN_STORE_TRACE | ROSEN_STORE_COORDS))
-        return set_error(ROSEN_EINVAL, "rosen_offlattice_grow: unknown flags 0x%x", p->flags);
+        return set_error(ROSEN_EINVAL, "%s: unknown flags 0x%x", fn, p->flags);
     if ((p->flags & ROSEN_STORE_TRACE) && !o->trace)
-        return set_error(ROSEN_EINVAL, "rosen_offlattice_grow: ROSEN_STORE_TRACE without trace");
+        return set_error(ROSEN_EINVAL, "%s: ROSEN_STORE_TRACE without trace", fn);
     if ((p->flags & ROSEN_STORE_COORDS) && !o->coords)
-        return set_error(ROSEN_EINVAL, "rosen_offlattice_grow: ROSEN_STORE_COORDS without coords");
+        return set_error(ROSEN_EINVAL, "%s: ROSEN_STORE_COORDS without coords", fn);
     const int G = p->lanes_per_chain;
     if (G != 0 && G != 8 && G != 16 && G != 32)
         return set_error(ROSEN_EINVAL,
-                         "rosen_offlattice_grow: lanes_per_chain must be 0, 8, 16 or 32");
+                         "%s: lanes_per_chain must be 0, 8, 16 or 32", fn);
     if (G != 0 && (p->k + G - 1) / G > 4)
         return set_error(ROSEN_EINVAL,
-                         "rosen_offlattice_grow: k = %d needs more than 4 trials per lane", p->k);
+                         "%s: k = %d needs more than 4 trials per lane", fn, p->k);
     if (p->max_attempts < 0 || p->max_attempts > ROSEN_MAX_ATTEMPTS)
-        return set_error(ROSEN_EINVAL, "rosen_offlattice_grow: max_attempts = %d outside [0, %d]",
+        return set_error(ROSEN_EINVAL, "%s: max_attempts = %d outside [0, %d]", fn,
                          p->max_attempts, ROSEN_MAX_ATTEMPTS);
     return ROSEN_OK;
 }

@@ -19,6 +19,7 @@ ROSEN_LATTICE_NMAX = 512
 ROSEN_LATTICE_LONG_NMAX = 32768
 ROSEN_MAX_ATTEMPTS = 65535
 ROSEN_OFFLATTICE_NMAX = 1024
+ROSEN_OFFLATTICE_LONG_NMAX = 16384
 ROSEN_KMAX = 128
 ROSEN_STORE_TRACE = 1
 ROSEN_STORE_COORDS = 2
@@ -121,6 +122,12 @@ def load():
                                           ctypes.POINTER(rosen_lattice_out), _vp, ctypes.c_size_t,
                                           _vp]
     L.rosen_lattice_grow_long.restype = ctypes.c_int
+    L.rosen_offlattice_long_workspace_size.argtypes = [ctypes.c_int32, ctypes.c_int64]
+    L.rosen_offlattice_long_workspace_size.restype = ctypes.c_size_t
+    L.rosen_offlattice_grow_long.argtypes = [ctypes.POINTER(rosen_offlattice_params),
+                                             ctypes.POINTER(rosen_offlattice_out), _vp,
+                                             ctypes.c_size_t, _vp]
+    L.rosen_offlattice_grow_long.restype = ctypes.c_int
     L.rosen_offlattice_grow.argtypes = [ctypes.POINTER(rosen_offlattice_params),
                                         ctypes.POINTER(rosen_offlattice_out), _vp]
     L.rosen_offlattice_grow.restype = ctypes.c_int
@@ -238,6 +245,29 @@ def rosen_offlattice_grow(params, out, stream=None):
                              counters=_ptr(out.get("counters")),
                              attempts=_ptr(out.get("attempts")))
     _check(load().rosen_offlattice_grow(ctypes.byref(params), ctypes.byref(o), _stream(stream)))
+
+
+def rosen_offlattice_long_workspace_size(N, C):
+    return int(load().rosen_offlattice_long_workspace_size(int(N), int(C)))
+
+
+def offlattice_long_workspace(N, C, device="cuda"):
+    """Allocate the per-chain-slot workspace of rosen_offlattice_grow_long."""
+    nbytes = rosen_offlattice_long_workspace_size(N, C)
+    return torch.empty(max(nbytes, 16) // 16 * 2, dtype=torch.int64, device=device)
+
+
+def rosen_offlattice_grow_long(params, out, workspace, stream=None):
+    """Grow long real-space chains (N <= 16384) with cell grids in workspace."""
+    o = rosen_offlattice_out(logw=_ptr(out.get("logw")), r2=_ptr(out.get("r2")),
+                             rg2=_ptr(out.get("rg2")), alive=_ptr(out.get("alive")),
+                             trace=_ptr(out.get("trace")), coords=_ptr(out.get("coords")),
+                             counters=_ptr(out.get("counters")),
+                             attempts=_ptr(out.get("attempts")))
+    _check(load().rosen_offlattice_grow_long(ctypes.byref(params), ctypes.byref(o),
+                                             _ptr(workspace),
+                                             workspace.numel() * workspace.element_size(),
+                                             _stream(stream)))
 
 
 def rosen_sphere_points(words, out, stream=None):
