@@ -580,19 +580,55 @@ def run_long(args):
             torch.cuda.empty_cache()
     # Each lookup and each insert touches one 32-byte sector of a table.
     gbs = tot_lookups * 32 / (tot_ms / 1e3) / 1e9
+    lat_ms = tot_ms
+    # Real space: hard spheres, k = 32, through rosen_offlattice_grow_long.
+    Cr = args.long_real_chains
+    Nr = [int(v) for v in args.long_real_n.split(",") if v]
+    with ClockSampler(0) as clocks_r:
+        for Nl in Nr:
+            out = rosen.offlattice_outputs(Nl, Cr, counters=True)
+            ws = rosen.offlattice_long_workspace(Nl, Cr)
+            p = rosen.offlattice_params(12, Nl, Cr, K_TRIALS)
+            st = rosen.stats_tensor()
+            rws = rosen.reduce_workspace(Cr)
+            rin = rosen.offlattice_reduce_in(out, Nl, K_TRIALS)
+            for _ in range(max(1, args.warmup)):
+                rosen.rosen_offlattice_grow_long(p, out, ws, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                rosen.rosen_offlattice_grow_long(p, out, ws, stream)
+                rosen.rosen_reduce(rin, st, rws, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            sd = rosen.stats_dict(st)
+            ins = Cr * (Nl - 1)
+            parts["hard_sphere_k32_N%d" % Nl] = {
+                "ms": ms, "insertions_per_s": ins / (ms / 1e3), "chains": Cr,
+                "alive_frac": sd["n_alive"] / Cr, "logZ_norm": sd["logZ_norm"],
+                "mean_r2": sd["mean_r2"], "workspace_gb": ws.numel() * 8 / 1e9}
+            tot_ins += ins
+            tot_ms += ms
+            del out, ws
+            torch.cuda.empty_cache()
     peak = measured_peak("hbm_gbs", 6800.0)
     line = {
-        "metric": "long-chain lattice insertions/s (hash tables in HBM)",
+        "metric": "long-chain insertions/s (lattice hash tables, real-space cell grids in HBM)",
         "value": tot_ins / (tot_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms, "higher_is_better": True,
         "dtype": "int32+fp32", "data": "synthetic",
-        "config": {"workload": "lattice, beta*eps %g, N in %s, %d chains each"
-                               % (args.long_beta_eps, Ns, Cl)},
+        "config": {"workload": "lattice beta*eps %g, N in %s, %d chains each; hard spheres "
+                               "k=32, N in %s, %d chains each"
+                               % (args.long_beta_eps, Ns, Cl, Nr, Cr)},
         "parts": parts,
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                      "frac": gbs / peak, "traffic": None,
+                     "kernel": "lattice_long_kernel (lattice parts, %.1f ms)" % lat_ms,
                      "basis": "one 32 B sector per table lookup and per insert, grown steps"},
         "clocks": clocks.summary(),
+        "clocks_real_space": clocks_r.summary(),
     }
     print(json.dumps(line), flush=True)
 
@@ -699,6 +735,8 @@ def main():
                     help="step: restart mode, growths per chain (0/1: dead ends keep W = 0)")
     ap.add_argument("--long-n", default="1000,10000", help="long: chain lengths")
     ap.add_argument("--long-beta-eps", type=float, default=0.0)
+    ap.add_argument("--long-real-n", default="1000,10000", help="long: real-space lengths")
+    ap.add_argument("--long-real-chains", type=int, default=100_000)
     args = ap.parse_args()
     if args.workload == "long":
         return run_long(args)

@@ -125,6 +125,31 @@ def test_long_lattice_validation(rosen):
     assert grow_long(4096, 1 << 20, C=0) == rosen.ROSEN_OK
 
 
+def test_long_offlattice_validation(rosen):
+    L = rosen.load()
+    assert rosen.rosen_offlattice_long_workspace_size(1, 10) == 0
+    assert rosen.rosen_offlattice_long_workspace_size(16385, 10) == 0
+    assert rosen.rosen_offlattice_long_workspace_size(1000, 0) == 0
+    one = rosen.rosen_offlattice_long_workspace_size(1000, 1)
+    assert one % 16 == 0 and one > 1000 * 4 * 16
+    assert rosen.rosen_offlattice_long_workspace_size(1000, 10) == 10 * one
+    assert rosen.rosen_offlattice_long_workspace_size(1000, 10 ** 9) == 9728 * one
+
+    def grow_long(ws, nbytes, **kw):
+        p = rosen.offlattice_params(**{**dict(seed=1, N=1000, C=10, k=32), **kw})
+        o = rosen.rosen_offlattice_out()
+        return L.rosen_offlattice_grow_long(ctypes.byref(p), ctypes.byref(o), ws, nbytes, None)
+
+    assert grow_long(4096, 1 << 30, N=1) == rosen.ROSEN_EINVAL
+    assert grow_long(4096, 1 << 30, N=16385) == rosen.ROSEN_EINVAL
+    assert grow_long(4096, 1 << 30, k=0) == rosen.ROSEN_EINVAL
+    assert grow_long(4096, 1 << 30, lanes_per_chain=8, k=8) == rosen.ROSEN_EINVAL
+    assert "16 or 32" in rosen.last_error()
+    assert grow_long(None, 1 << 30) == rosen.ROSEN_EINVAL
+    assert grow_long(4104, 1 << 30) == rosen.ROSEN_EINVAL
+    assert grow_long(4096, 1 << 30, C=0) == rosen.ROSEN_OK
+
+
 def test_lattice_empty_launch_is_a_no_op(rosen):
     assert _grow(rosen, C=0) == rosen.ROSEN_OK
 
