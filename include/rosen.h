@@ -149,12 +149,13 @@ ROSEN_API int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_latt
  * their coordinates in global memory).  Same rule, draws, parameters and
  * outputs as rosen_lattice_grow, bit for bit, for 2 <= N <= 32768.  Each
  * chain's occupied sites live in an open-addressing hash table in
- * `workspace`, so a step costs O(1) lookups, not a scan of the chain.  A
- * lane owns one table of 8 * 2^ceil(log2(max(2N, 64))) bytes and grows its
- * chains one after another.  The call grows min(C, workspace_bytes / table)
- * chains at a time, so a smaller workspace means fewer chains in flight and
- * no other change.
- * workspace: caller-owned device memory, 8-byte aligned; the call zeroes the
+ * `workspace`, one 16-byte entry (key and occupancy bitmap) per 4x4x4 block
+ * of sites, so a step costs a few block lookups, not a scan of the chain.  A
+ * lane owns one table of 16 * 2^ceil(log2(max(N + 1, 64))) bytes and grows
+ * its chains one after another.  The call grows min(C, workspace_bytes /
+ * table) chains at a time, so a smaller workspace means fewer chains in
+ * flight and no other change.
+ * workspace: caller-owned device memory, 16-byte aligned; the call zeroes the
  * part it uses on the stream first, so its contents need not be kept between
  * calls.  rosen_lattice_long_workspace_size gives the size for
  * min(C, 131072) tables in flight.

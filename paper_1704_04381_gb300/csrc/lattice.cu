@@ -430,104 +430,75 @@ __global__ void __launch_bounds__(256) lattice_batch_kernel(const LatticeArgs *_
     }
 }
 
-// ---- long chains: occupied sites in a per-chain hash table in HBM ---------
+// ---- long chains: occupancy bitmaps in a per-chain hash table in HBM -------
 //
 // Beyond a few hundred monomers the O(i) scan of the shared-memory kernel
 // dominates and the packed 10-bit keys run out.  Here every lane keeps its
 // chain's occupied sites in an open-addressing hash table (linear probing)
-// in device memory: a step looks up the six neighbours of the end (and, when
-// interacting, the 18 sites at lattice distance 2 that decide the contacts)
-// in O(1) each, whatever i is.  Site keys pack 17 bits per axis
-// (x + 2^16 | (y + 2^16) << 17 | (z + 2^16) << 34); bits 51..63 of an entry
-// hold the generation of the growth that wrote it, so a lane reuses its
-// table for the next chain without clearing it: entries of older generations
-// read as empty.  Tables hold at least 2N entries (load <= 1/2), so every
-// probe sequence ends at an empty slot.
-constexpr int kGenShift = 51;
-constexpr uint64_t kSiteMask = (1ull << kGenShift) - 1ull;
-constexpr uint32_t kGenMax = 8191;
-constexpr int64_t kAxisOff = 1 << 16;
+// in device memory, one 16-byte entry per 4x4x4 block of sites: the block's
+// key and a 64-bit occupancy bitmap (bit (x & 3) | (y & 3) << 2 | (z & 3) << 4).
+// A step reads only the blocks its neighbourhood touches: the end's block
+// and, per axis, the neighbouring block the neighbours (athermal, about 2.5
+// blocks per step on average) or the sites at lattice distance <= 2
+// (interacting, about 4.75) cross into -- one 16-byte load each.  Block keys
+// pack 16 bits per axis; bits 48..63 of the key word hold the generation of
+// the growth that wrote it, so a lane reuses its table for the next chain
+// without clearing it (older generations read as empty).  A chain occupies at
+// most N blocks and a table holds more than N entries, so every probe
+// sequence ends at an empty slot.
+constexpr int kGenShift = 48;
+constexpr uint64_t kBlockMask = (1ull << kGenShift) - 1ull;
+constexpr uint32_t kGenMax = 65535;
 
-__device__ __forceinline__ uint64_t site_key(int x, int y, int z)
+__device__ __forceinline__ uint64_t block_key(int bx, int by, int bz)
 {
-    return (uint64_t)(x + kAxisOff) | ((uint64_t)(y + kAxisOff) << 17) |
-           ((uint64_t)(z + kAxisOff) << 34);
+    return (uint64_t)(uint32_t)(bx + 32768) | ((uint64_t)(uint32_t)(by + 32768) << 16) |
+           ((uint64_t)(uint32_t)(bz + 32768) << 32);
 }
 
-// Key offset of neighbour d in slot order +x, -x, +y, -y, +z, -z.
-__device__ __forceinline__ uint64_t nb_off(int d)
-{
-    const uint64_t unit = 1ull << (17 * (d >> 1));
-    return (d & 1) ? (0ull - unit) : unit;
-}
-
-__device__ __forceinline__ uint32_t site_slot(uint64_t key, int logH)
+__device__ __forceinline__ uint32_t block_slot(uint64_t key, int logH)
 {
     return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - logH));
 }
 
-// Continue the probe that read entry e at slot h: true if the site `want`
-// (key with this growth's tag) is in the table; otherwise h ends on the
-// empty slot where the site would be inserted.
-__device__ __forceinline__ bool probe_rest(const uint64_t *tab, uint32_t hmask, uint64_t want,
-                                           uint64_t tag, uint32_t &h, uint64_t e)
+// A block found (or not) in the table: its bitmap, the slot holding it (or
+// the empty slot where it would go) and whether it exists.
+struct BlockRef {
+    uint64_t bits;
+    uint32_t h;
+    bool found;
+};
+
+// Continue the probe for tagged key `want` that read entry e at slot h.
+__device__ __forceinline__ BlockRef block_rest(const ulonglong2 *tab, uint32_t hmask, uint64_t want,
+                                               uint64_t tag, uint32_t h, ulonglong2 e)
 {
-    while ((e & ~kSiteMask) == tag) {
-        if (e == want) return true;
+    while ((e.x & ~kBlockMask) == tag) {
+        if (e.x == want) return BlockRef{e.y, h, true};
         h = (h + 1u) & hmask;
         e = tab[h];
     }
-    return false;
+    return BlockRef{0ull, h, false};
 }
 
-// Occupancy of six sites end + off(q): first probes issued together, then
-// resolved; bit q of the result is set for an occupied site.
-template <class Off>
-__device__ __forceinline__ uint32_t probe6(const uint64_t *tab, uint32_t hmask, int logH,
-                                           uint64_t end, uint64_t tag, Off off, uint32_t *hout)
+// Bit of the site at offset (dx, dy, dz) from the end, whose position in its
+// block is (qx, qy, qz); the block offset along an axis is 0 or the axis's
+// side s (the neighbouring block the neighbourhood reaches on that axis).
+__device__ __forceinline__ uint32_t site_bit(int qx, int qy, int qz, int dx, int dy, int dz,
+                                             uint64_t b0, uint64_t bx, uint64_t by, uint64_t bz,
+                                             uint64_t bxy, uint64_t bxz, uint64_t byz)
 {
-    uint32_t h[6];
-    uint64_t e[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        h[q] = site_slot(end + off(q), logH);
-        e[q] = tab[h[q]];
-    }
-    uint32_t occ = 0u;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        if (probe_rest(tab, hmask, (end + off(q)) | tag, tag, h[q], e[q])) occ |= 1u << q;
-        if (hout) hout[q] = h[q];
-    }
-    return occ;
-}
-
-// The 12 sites at lattice distance 2 off the axes: pair p of axes (x,y),
-// (x,z), (y,z) with signs sa, sb: index 4p + 2sa + sb.
-__device__ __forceinline__ uint64_t diag_off(int q)
-{
-    const int p = q >> 2, sa = (q >> 1) & 1, sb = q & 1;
-    const int ax = p == 2 ? 1 : 0, bx = p == 0 ? 1 : 2;
-    return nb_off(2 * ax + sa) + nb_off(2 * bx + sb);
-}
-
-// Diagonal sites next to neighbour d (4 of the 12), as a 12-bit mask.
-__host__ __device__ constexpr uint32_t diag_mask(int d)
-{
-    uint32_t m = 0u;
-    for (int q = 0; q < 12; ++q) {
-        const int p = q >> 2, sa = (q >> 1) & 1, sb = q & 1;
-        const int ax = p == 2 ? 1 : 0, bx = p == 0 ? 1 : 2;
-        if ((2 * ax + sa) == d || (2 * bx + sb) == d) m |= 1u << q;
-    }
-    return m;
+    const int px = qx + dx, py = qy + dy, pz = qz + dz;
+    const bool ox = (unsigned)px > 3u, oy = (unsigned)py > 3u, oz = (unsigned)pz > 3u;
+    const uint64_t m = ox ? (oy ? bxy : (oz ? bxz : bx)) : (oy ? (oz ? byz : by) : (oz ? bz : b0));
+    return (uint32_t)(m >> ((px & 3) | ((py & 3) << 2) | ((pz & 3) << 4))) & 1u;
 }
 
 // Growth number att of chain c with the sites in the lane's table tab
 // (2^logH entries).  Same rule, draws and outputs as lattice_attempt.
 template <bool kIsaw>
 __device__ __forceinline__ bool long_attempt(const LatticeArgs &a, int64_t c, uint32_t att,
-                                             uint64_t *tab, int logH, uint32_t &gen,
+                                             ulonglong2 *tab, int logH, uint32_t &gen,
                                              const uint8_t *seltab, const float *wt32,
                                              const double *wt64)
 {
@@ -537,15 +508,15 @@ __device__ __forceinline__ bool long_attempt(const LatticeArgs &a, int64_t c, ui
     const uint32_t hmask = (1u << logH) - 1u;
 
     if (++gen > kGenMax) {          // generation tags exhausted: clear the table
-        for (uint32_t h = 0; h <= hmask; ++h) tab[h] = 0ull;
+        for (uint32_t h = 0; h <= hmask; ++h) tab[h] = make_ulonglong2(0ull, 0ull);
         gen = 1;
     }
     const uint64_t tag = (uint64_t)gen << kGenShift;
-    uint64_t end = site_key(0, 0, 0);
     {
-        uint32_t h = site_slot(end, logH);
-        while ((tab[h] & ~kSiteMask) == tag) h = (h + 1u) & hmask;
-        tab[h] = end | tag;
+        const uint64_t want = block_key(0, 0, 0) | tag;
+        uint32_t h = block_slot(want & kBlockMask, logH);
+        while ((tab[h].x & ~kBlockMask) == tag) h = (h + 1u) & hmask;
+        tab[h] = make_ulonglong2(want, 1ull);     // site (0,0,0): bit 0
     }
     if (a.coords && att == 0) {
         a.coords[(0 * 3 + 0) * C + c] = 0;
@@ -559,21 +530,78 @@ __device__ __forceinline__ bool long_attempt(const LatticeArgs &a, int64_t c, ui
     int dead_at = 0;
 
     for (int i = 1; i < N; ++i) {
-        uint32_t hfree[6];
-        const uint32_t occ = probe6(tab, hmask, logH, end, tag, [](int q) { return nb_off(q); },
-                                    hfree);
-        uint32_t acc = occ;
+        const int bx0 = ex >> 2, by0 = ey >> 2, bz0 = ez >> 2;
+        const int qx = ex & 3, qy = ey & 3, qz = ez & 3;
+        // The neighbouring block per axis: athermal steps need it only when
+        // the end sits on a face of its block, interacting steps always.
+        const int sx_ = qx <= 1 ? -1 : 1, sy_ = qy <= 1 ? -1 : 1, sz_ = qz <= 1 ? -1 : 1;
+        const bool need_x = kIsaw || qx == 0 || qx == 3;
+        const bool need_y = kIsaw || qy == 0 || qy == 3;
+        const bool need_z = kIsaw || qz == 0 || qz == 3;
+        const bool fx = qx == 0 || qx == 3, fy = qy == 0 || qy == 3, fz = qz == 0 || qz == 3;
+        const bool need_xy = kIsaw && fx && fy, need_xz = kIsaw && fx && fz,
+                   need_yz = kIsaw && fy && fz;
+        uint64_t want[7];
+        bool need[7];
+        want[0] = block_key(bx0, by0, bz0) | tag;
+        want[1] = block_key(bx0 + sx_, by0, bz0) | tag;
+        want[2] = block_key(bx0, by0 + sy_, bz0) | tag;
+        want[3] = block_key(bx0, by0, bz0 + sz_) | tag;
+        want[4] = block_key(bx0 + sx_, by0 + sy_, bz0) | tag;
+        want[5] = block_key(bx0 + sx_, by0, bz0 + sz_) | tag;
+        want[6] = block_key(bx0, by0 + sy_, bz0 + sz_) | tag;
+        need[0] = true;
+        need[1] = need_x;
+        need[2] = need_y;
+        need[3] = need_z;
+        need[4] = need_xy;
+        need[5] = need_xz;
+        need[6] = need_yz;
+        uint32_t h[7];
+        ulonglong2 e[7];
+        constexpr int kB = kIsaw ? 7 : 4;
+#pragma unroll
+        for (int q = 0; q < kB; ++q) {
+            h[q] = block_slot(want[q] & kBlockMask, logH);
+            e[q] = need[q] ? tab[h[q]] : make_ulonglong2(0ull, 0ull);
+        }
+        BlockRef ref[kB];
+#pragma unroll
+        for (int q = 0; q < kB; ++q)
+            ref[q] = need[q] ? block_rest(tab, hmask, want[q], tag, h[q], e[q])
+                             : BlockRef{0ull, 0u, false};
+        const uint64_t b0 = ref[0].bits, bxm = ref[1].bits, bym = ref[2].bits, bzm = ref[3].bits;
+        const uint64_t bxy = kIsaw ? ref[4 < kB ? 4 : 0].bits : 0ull;
+        const uint64_t bxz = kIsaw ? ref[5 < kB ? 5 : 0].bits : 0ull;
+        const uint64_t byz = kIsaw ? ref[6 < kB ? 6 : 0].bits : 0ull;
+
+        uint32_t occ = 0u, acc;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            const int ux = d == 0 ? 1 : (d == 1 ? -1 : 0);
+            const int uy = d == 2 ? 1 : (d == 3 ? -1 : 0);
+            const int uz = d == 4 ? 1 : (d == 5 ? -1 : 0);
+            occ |= site_bit(qx, qy, qz, ux, uy, uz, b0, bxm, bym, bzm, bxy, bxz, byz) << d;
+        }
+        acc = occ;
         if (kIsaw) {
-            const uint32_t far = probe6(tab, hmask, logH, end, tag,
-                                        [](int q) { return nb_off(q) + nb_off(q); }, nullptr);
-            const uint32_t dlo = probe6(tab, hmask, logH, end, tag,
-                                        [](int q) { return diag_off(q); }, nullptr);
-            const uint32_t dhi = probe6(tab, hmask, logH, end, tag,
-                                        [](int q) { return diag_off(q + 6); }, nullptr);
-            const uint32_t diag = dlo | (dhi << 6);
+            // Contacts of neighbour d: occupied sites next to it other than
+            // the end (its far site and the four beside it).
 #pragma unroll
             for (int d = 0; d < 6; ++d) {
-                const uint32_t cd = ((far >> d) & 1u) + __popc(diag & diag_mask(d));
+                const int ux = d == 0 ? 1 : (d == 1 ? -1 : 0);
+                const int uy = d == 2 ? 1 : (d == 3 ? -1 : 0);
+                const int uz = d == 4 ? 1 : (d == 5 ? -1 : 0);
+                uint32_t cd = 0u;
+#pragma unroll
+                for (int f = 0; f < 6; ++f) {
+                    if (f == (d ^ 1)) continue;    // back to the end
+                    const int vx = f == 0 ? 1 : (f == 1 ? -1 : 0);
+                    const int vy = f == 2 ? 1 : (f == 3 ? -1 : 0);
+                    const int vz = f == 4 ? 1 : (f == 5 ? -1 : 0);
+                    cd += site_bit(qx, qy, qz, ux + vx, uy + vy, uz + vz, b0, bxm, bym, bzm, bxy,
+                                   bxz, byz);
+                }
                 acc |= cd << (8 + 3 * d);
             }
         }
@@ -587,16 +615,24 @@ __device__ __forceinline__ bool long_attempt(const LatticeArgs &a, int64_t c, ui
         const int sel = choose<kIsaw>(freem, m, acc, x, seltab, wt32, wt64, lw);
         if (m < 4) cnt_lo += 1ull << (16 * m);
         else cnt_hi += 1ull << (16 * (m - 4));
-        uint32_t hs = 0u;
-#pragma unroll
-        for (int d = 0; d < 6; ++d)
-            if (d == sel) hs = hfree[d];
-        end += nb_off(sel);
-        tab[hs] = end | tag;
         const int step = (sel & 1) ? -1 : 1;
         if ((sel >> 1) == 0) ex += step;
         else if ((sel >> 1) == 1) ey += step;
         else ez += step;
+        // Set the new site's bit in its block (the end's block or the
+        // neighbouring block of the axis moved along).
+        const int ax = sel >> 1;
+        const bool out = ax == 0 ? (unsigned)(qx + step) > 3u
+                                 : (ax == 1 ? (unsigned)(qy + step) > 3u : (unsigned)(qz + step) > 3u);
+        BlockRef r = ref[0];
+        uint64_t key = want[0];
+        if (out) {
+            r = ax == 0 ? ref[1] : (ax == 1 ? ref[2] : ref[3]);
+            key = ax == 0 ? want[1] : (ax == 1 ? want[2] : want[3]);
+        }
+        const uint64_t bit = 1ull << ((ex & 3) | ((ey & 3) << 2) | ((ez & 3) << 4));
+        if (r.found) tab[r.h].y = r.bits | bit;
+        else tab[r.h] = make_ulonglong2(key, bit);
         sx += ex;
         sy += ey;
         sz += ez;
@@ -644,7 +680,7 @@ __device__ __forceinline__ bool long_attempt(const LatticeArgs &a, int64_t c, ui
 // One lane per chain at a time; lane l grows chains l, l + lanes, ... in its
 // own table (2^logH entries at ws + l 2^logH).
 template <bool kIsaw>
-__global__ void __launch_bounds__(256) lattice_long_kernel(const LatticeArgs a, uint64_t *ws,
+__global__ void __launch_bounds__(256) lattice_long_kernel(const LatticeArgs a, ulonglong2 *ws,
                                                            int64_t lanes, int logH)
 {
     __shared__ uint8_t seltab[kSelBytes];
@@ -659,7 +695,7 @@ __global__ void __launch_bounds__(256) lattice_long_kernel(const LatticeArgs a, 
     __syncthreads();
     const int64_t lane = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (lane >= lanes) return;
-    uint64_t *tab = ws + (lane << logH);
+    ulonglong2 *tab = ws + (lane << logH);
     uint32_t gen = 0;
     for (int64_t c = lane; c < a.C; c += lanes) {
         uint32_t att = 0;
@@ -816,11 +852,12 @@ namespace {
 
 constexpr int64_t kLongLanes = 1 << 17;   // tables the default workspace holds
 
-// log2 of the table entries per lane: >= 2N (load <= 1/2) and >= 64.
+// log2 of the table entries per lane: more than N (a chain fills at most N
+// blocks) and at least 64.
 int long_log_entries(int N)
 {
     int lg = 6;
-    while ((int64_t(1) << lg) < 2 * (int64_t)N) ++lg;
+    while ((int64_t(1) << lg) < (int64_t)N + 1) ++lg;
     return lg;
 }
 
@@ -830,7 +867,7 @@ extern "C" size_t rosen_lattice_long_workspace_size(int32_t N, int64_t C)
 {
     if (N < 2 || N > ROSEN_LATTICE_LONG_NMAX || C < 1) return 0;
     const int64_t lanes = C < kLongLanes ? C : kLongLanes;
-    return (size_t)lanes * ((size_t)8 << long_log_entries(N));
+    return (size_t)lanes * (sizeof(ulonglong2) << long_log_entries(N));
 }
 
 extern "C" int rosen_lattice_grow_long(const rosen_lattice_params *p, const rosen_lattice_out *o,
@@ -839,11 +876,11 @@ extern "C" int rosen_lattice_grow_long(const rosen_lattice_params *p, const rose
     const int st = lattice_validate(p, o, ROSEN_LATTICE_LONG_NMAX, "rosen_lattice_grow_long");
     if (st != ROSEN_OK) return st;
     if (p->C == 0) return ROSEN_OK;
-    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 7u))
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 15u))
         return set_error(ROSEN_EINVAL, "rosen_lattice_grow_long: workspace must be a non-NULL, "
-                                       "8-byte aligned device pointer");
+                                       "16-byte aligned device pointer");
     const int logH = long_log_entries(p->N);
-    const size_t table = (size_t)8 << logH;
+    const size_t table = sizeof(ulonglong2) << logH;
     int64_t lanes = (int64_t)(workspace_bytes / table);
     if (lanes > p->C) lanes = p->C;
     if (lanes < 1)
@@ -857,7 +894,7 @@ extern "C" int rosen_lattice_grow_long(const rosen_lattice_params *p, const rose
     if (e != cudaSuccess)
         return set_error(ROSEN_ECUDA, "rosen_lattice_grow_long: %s", cudaGetErrorString(e));
     const unsigned grid = (unsigned)((lanes + 255) / 256);
-    uint64_t *ws = static_cast<uint64_t *>(workspace);
+    ulonglong2 *ws = static_cast<ulonglong2 *>(workspace);
     if (a.isaw) lattice_long_kernel<true><<<grid, 256, 0, s>>>(a, ws, lanes, logH);
     else lattice_long_kernel<false><<<grid, 256, 0, s>>>(a, ws, lanes, logH);
     return check_launch("rosen_lattice_grow_long");

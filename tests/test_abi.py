@@ -106,9 +106,9 @@ def test_long_lattice_validation(rosen):
     assert rosen.rosen_lattice_long_workspace_size(1, 10) == 0
     assert rosen.rosen_lattice_long_workspace_size(32769, 10) == 0
     assert rosen.rosen_lattice_long_workspace_size(1000, 0) == 0
-    # 2N = 2000 -> 2048 entries of 8 bytes per table; min(C, 131072) tables.
-    assert rosen.rosen_lattice_long_workspace_size(1000, 10) == 10 * 2048 * 8
-    assert rosen.rosen_lattice_long_workspace_size(2, 10 ** 9) == (1 << 17) * 64 * 8
+    # N + 1 = 1001 -> 1024 entries of 16 bytes per table; min(C, 131072) tables.
+    assert rosen.rosen_lattice_long_workspace_size(1000, 10) == 10 * 1024 * 16
+    assert rosen.rosen_lattice_long_workspace_size(2, 10 ** 9) == (1 << 17) * 64 * 16
 
     def grow_long(ws, nbytes, **kw):
         p = rosen.lattice_params(**{**dict(seed=1, N=1000, C=10), **kw})
@@ -120,7 +120,8 @@ def test_long_lattice_validation(rosen):
     assert grow_long(4096, 1 << 20, beta_eps=-1.0) == rosen.ROSEN_EINVAL
     assert grow_long(None, 1 << 20) == rosen.ROSEN_EINVAL
     assert grow_long(4100, 1 << 20) == rosen.ROSEN_EINVAL
-    assert grow_long(4096, 2048 * 8 - 1) == rosen.ROSEN_ENOMEM
+    assert grow_long(4104, 1 << 20) == rosen.ROSEN_EINVAL
+    assert grow_long(4096, 1024 * 16 - 1) == rosen.ROSEN_ENOMEM
     assert "rosen_lattice_grow_long" in rosen.last_error()
     assert grow_long(4096, 1 << 20, C=0) == rosen.ROSEN_OK
 

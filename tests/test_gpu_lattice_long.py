@@ -7,7 +7,7 @@ What is checked:
 - Beyond that the FP64 oracle decides, bit for bit, up to the maximum
   N = 32768.
 - Results must not depend on how many tables the workspace holds.
-- A lane that outlives the 8191 generation tags clears its table and goes
+- A lane that outlives the 65535 generation tags clears its table and goes
   on unchanged.
 """
 import numpy as np
@@ -109,9 +109,9 @@ def test_results_do_not_depend_on_the_workspace(rosen):
 
 
 def test_generation_wrap_clears_the_table(rosen):
-    # One table grows all 8300 chains: the 8192nd growth clears and restarts
-    # the generation tags.
-    N, C = 16, 8300
+    # One table grows all 66000 chains: growth 65536 clears the table and
+    # restarts the generation tags.
+    N, C = 8, 66_000
     a = grow(rosen, 46, N, C, 0.3, ws_tables=1)
     b = grow(rosen, 46, N, C, 0.3, long=False)
     same(a, b)
