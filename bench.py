@@ -542,7 +542,7 @@ def run_long(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     Cl = args.chains or 1_000_000
-    Ns = [int(v) for v in args.long_n.split(",")]
+    Ns = [int(v) for v in args.long_n.split(",") if v]
     parts, tot_ins, tot_ms, tot_grown, tot_lookups = {}, 0, 0.0, 0, 0
     with ClockSampler(0) as clocks:
         for Nl in Ns:
@@ -566,7 +566,11 @@ def run_long(args):
             grown = int(out["counts"].to(torch.int64)[:, 1:7].sum())
             sd = rosen.stats_dict(st)
             ins = Cl * (Nl - 1)
-            lookups = 6 if args.long_beta_eps == 0.0 else 24
+            # Expected 4x4x4-block reads per step: the end's block, plus per
+            # axis the neighbouring block when the end sits on a face
+            # (probability 1/2); interacting steps read it on every axis,
+            # and a diagonal block when two axes sit on faces (3 x 1/4).
+            lookups = 2.5 if args.long_beta_eps == 0.0 else 4.75
             parts["N%d" % Nl] = {
                 "ms": ms, "insertions_per_s": ins / (ms / 1e3),
                 "grown_steps_per_s": grown / (ms / 1e3), "grown_steps": grown,
@@ -575,11 +579,12 @@ def run_long(args):
             tot_ins += ins
             tot_ms += ms
             tot_grown += grown
-            tot_lookups += grown * (lookups + 1)
+            tot_lookups += grown * lookups
             del out, ws
             torch.cuda.empty_cache()
-    # Each lookup and each insert touches one 32-byte sector of a table.
-    gbs = tot_lookups * 32 / (tot_ms / 1e3) / 1e9
+    # Algorithmic bytes: a 16-byte entry per block read and an 8-byte bitmap
+    # write per grown step.
+    gbs = (tot_lookups * 16 + tot_grown * 8) / (tot_ms / 1e3) / 1e9
     lat_ms = tot_ms
     # Real space: hard spheres, k = 32, through rosen_offlattice_grow_long.
     Cr = args.long_real_chains
@@ -626,7 +631,8 @@ def run_long(args):
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                      "frac": gbs / peak, "traffic": None,
                      "kernel": "lattice_long_kernel (lattice parts, %.1f ms)" % lat_ms,
-                     "basis": "one 32 B sector per table lookup and per insert, grown steps"},
+                     "basis": "16 B per 4x4x4-block entry read (2.5 athermal, 4.75 interacting, "
+                              "expected per step) + 8 B bitmap write, per grown step"},
         "clocks": clocks.summary(),
         "clocks_real_space": clocks_r.summary(),
     }
