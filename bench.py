@@ -584,7 +584,7 @@ def run_long(args):
             torch.cuda.empty_cache()
     # Algorithmic bytes: a 16-byte entry per block read and an 8-byte bitmap
     # write per grown step.
-    gbs = (tot_lookups * 16 + tot_grown * 8) / (tot_ms / 1e3) / 1e9
+    gbs = (tot_lookups * 16 + tot_grown * 8) / (tot_ms / 1e3) / 1e9 if tot_ms > 0 else 0.0
     lat_ms = tot_ms
     # Real space: hard spheres, k = 32, through rosen_offlattice_grow_long.
     Cr = args.long_real_chains
