@@ -54,16 +54,17 @@ struct ChainSmem {
 
 // A long chain's storage (all in device memory): the arrays above, the near
 // list as gathered (before it is put in bead order), and the cell grid -- a
-// hash table of the cells that hold beads, each heading a list of its beads
-// linked through next.
+// hash table of the cells that hold beads, each heading a list of its beads.
+// The list link of bead j is kept in hi[j].w (its bits), so one 16-byte load
+// gives a bead's position and the next bead of its cell.
 struct ChainLong : ChainSmem {
     float4 *nls;
     int *njs;
     float *nbs;
-    int *next;
     uint4 *cells;      // {key with generation (2 words), head bead, -}
     int logH;          // log2 of the cell-table entries
     float inv_cell;    // 1 / cell side
+    float pre2;        // coarse test: beads with hi-only |g|^2 >= pre2 are not near
 };
 
 __device__ inline ChainSmem carve(unsigned char *base, int N, bool lj)
@@ -117,9 +118,10 @@ __device__ __forceinline__ int cell_head(const uint4 *cells, int logH, uint64_t 
     }
 }
 
-// Put bead j at the head of the list of its cell (key `want`).
-__device__ __forceinline__ void cell_insert(uint4 *cells, int *next, int logH, uint64_t want,
-                                            uint64_t tag, int j)
+// Put bead j at the head of the list of its cell (key `want`); returns the
+// bead it now links to (-1: the cell was empty).
+__device__ __forceinline__ int cell_push(uint4 *cells, int logH, uint64_t want, uint64_t tag,
+                                         int j)
 {
     const uint32_t hmask = (1u << logH) - 1u;
     uint32_t h = cell_slot(want & kCellKeyMask, logH);
@@ -127,14 +129,12 @@ __device__ __forceinline__ void cell_insert(uint4 *cells, int *next, int logH, u
         const uint4 e = cells[h];
         const uint64_t k = (uint64_t)e.x | ((uint64_t)e.y << 32);
         if ((k & ~kCellKeyMask) != tag) {
-            next[j] = -1;
             cells[h] = make_uint4((uint32_t)want, (uint32_t)(want >> 32), (uint32_t)j, 0u);
-            return;
+            return -1;
         }
         if (k == want) {
-            next[j] = (int)e.z;
             reinterpret_cast<int *>(&cells[h])[2] = j;
-            return;
+            return (int)e.z;
         }
         h = (h + 1u) & hmask;
     }
@@ -309,7 +309,7 @@ __device__ __noinline__ void replay_positions(const OffArgs &a, const ChainSmem 
         z = g.scan(z) + cz;
         if (s <= i - 1) {
             const float hx = (float)x, hy = (float)y, hz = (float)z;
-            w.hi[s] = make_float4(hx, hy, hz, 0.f);
+            w.hi[s] = make_float4(hx, hy, hz, w.hi[s].w);   // .w: a long chain's cell link
             w.lo[s] = make_float4((float)(x - hx), (float)(y - hy), (float)(z - hz), 0.f);
         }
         cx = g.bcast(x, G - 1);
@@ -468,14 +468,21 @@ __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong 
         if (!g.ballot(has)) break;
         float4 L = make_float4(0.f, 0.f, 0.f, 0.f);
         bool near = false;
+        float4 h = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+        if (has) h = w.hi[j];
         if (has && j <= i - 2) {
-            const float4 h = w.hi[j], l = w.lo[j];
-            const float gx = (ehx - h.x) + (elx - l.x);
-            const float gy = (ehy - h.y) + (ely - l.y);
-            const float gz = (ehz - h.z) + (elz - l.z);
-            const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-            L = make_float4(gx, gy, gz, 1.f + g2);
-            near = g2 < a.rf2;
+            // Coarse test on hi alone (the lo words are below 6e-8 |x|; pre2
+            // covers them), then the exact test of the full scan.
+            const float px = (ehx - h.x) + elx, py = (ehy - h.y) + ely, pz = (ehz - h.z) + elz;
+            if (fmaf(px, px, fmaf(py, py, pz * pz)) < w.pre2) {
+                const float4 l = w.lo[j];
+                const float gx = (ehx - h.x) + (elx - l.x);
+                const float gy = (ehy - h.y) + (ely - l.y);
+                const float gz = (ehz - h.z) + (elz - l.z);
+                const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+                L = make_float4(gx, gy, gz, 1.f + g2);
+                near = g2 < a.rf2;
+            }
         }
         const unsigned m = g.ballot(near);
         if (near) {
@@ -489,7 +496,7 @@ __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong 
             }
         }
         nn += __popc(m);
-        if (has) j = w.next[j];
+        if (has) j = __float_as_int(h.w);
     }
     __syncwarp(g.mask);
     for (int p = g.gl; p < nn; p += G) {
@@ -544,7 +551,10 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                 __syncwarp(g.mask);
             }
             tag = (uint64_t)*genp << kCellGenShift;
-            if (g.gl == 0) cell_insert(w.cells, w.next, w.logH, cell_key(0, 0, 0) | tag, tag, 0);
+            if (g.gl == 0) {
+                const int link = cell_push(w.cells, w.logH, cell_key(0, 0, 0) | tag, tag, 0);
+                w.hi[0] = make_float4(0.f, 0.f, 0.f, __int_as_float(link));
+            }
             __syncwarp(g.mask);
         }
 
@@ -766,14 +776,16 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                 ff_add(ehy, ely, vy);
                 ff_add(ehz, elz, vz);
                 if (g.gl == 0) {
-                    w.hi[i] = make_float4(ehx, ehy, ehz, 0.f);
+                    float link = 0.f;
+                    if constexpr (kLong)
+                        link = __int_as_float(cell_push(
+                            w.cells, w.logH,
+                            cell_key(cell_coord(ehx, w.inv_cell), cell_coord(ehy, w.inv_cell),
+                                     cell_coord(ehz, w.inv_cell)) | tag,
+                            tag, i));
+                    w.hi[i] = make_float4(ehx, ehy, ehz, link);
                     w.lo[i] = make_float4(elx, ely, elz, 0.f);
                     w.tr[i] = (uint8_t)sel;
-                    if constexpr (kLong)
-                        cell_insert(w.cells, w.next, w.logH,
-                                    cell_key(cell_coord(ehx, w.inv_cell), cell_coord(ehy, w.inv_cell),
-                                             cell_coord(ehz, w.inv_cell)) | tag,
-                                    tag, i);
                 }
                 lw += logS;
             }

@@ -34,15 +34,15 @@ int long_log_cells(int N)
 }
 
 // Device memory of one slot: hi, lo, nl, nls (N float4 each), the cell table
-// (2^logH uint4), nj, njs, next (N int each), nb, nbs (N float each), the
-// trace (N bytes); every piece starts on a 16-byte boundary.
+// (2^logH uint4), nj, njs (N int each), nb, nbs (N float each), the trace
+// (N bytes); every piece starts on a 16-byte boundary.
 size_t long_slot_bytes(int N, int logH)
 {
     const size_t n = (size_t)N;
-    return 4 * n * sizeof(float4) + ((size_t)sizeof(uint4) << logH) + 5 * r16(4 * n) + r16(n);
+    return 4 * n * sizeof(float4) + ((size_t)sizeof(uint4) << logH) + 4 * r16(4 * n) + r16(n);
 }
 
-__device__ ChainLong carve_long(unsigned char *base, int N, int logH, float inv_cell)
+__device__ ChainLong carve_long(unsigned char *base, int N, int logH, float inv_cell, float pre2)
 {
     ChainLong w;
     w.hi = reinterpret_cast<float4 *>(base);
@@ -54,19 +54,19 @@ __device__ ChainLong carve_long(unsigned char *base, int N, int logH, float inv_
     const size_t q = r16(4 * (size_t)N);
     w.nj = reinterpret_cast<int *>(p);
     w.njs = reinterpret_cast<int *>(p + q);
-    w.next = reinterpret_cast<int *>(p + 2 * q);
-    w.nb = reinterpret_cast<float *>(p + 3 * q);
-    w.nbs = reinterpret_cast<float *>(p + 4 * q);
-    w.tr = p + 5 * q;
+    w.nb = reinterpret_cast<float *>(p + 2 * q);
+    w.nbs = reinterpret_cast<float *>(p + 3 * q);
+    w.tr = p + 4 * q;
     w.logH = logH;
     w.inv_cell = inv_cell;
+    w.pre2 = pre2;
     return w;
 }
 
 template <int G, int T, bool LJ>
 __global__ void __launch_bounds__(256, 4) offlattice_long_kernel(const OffArgs a, unsigned char *ws,
                                                                  int64_t slots, size_t slot_bytes,
-                                                                 int logH, float inv_cell)
+                                                                 int logH, float inv_cell, float pre2)
 {
     __shared__ float logm[kTable];
     fill_log_table(logm);
@@ -74,14 +74,14 @@ __global__ void __launch_bounds__(256, 4) offlattice_long_kernel(const OffArgs a
     const Group<G> g;
     const int64_t slot = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
     if (slot >= slots) return;     // whole groups leave together
-    const ChainLong w = carve_long(ws + slot * slot_bytes, a.N, logH, inv_cell);
+    const ChainLong w = carve_long(ws + slot * slot_bytes, a.N, logH, inv_cell, pre2);
     uint32_t gen = 0;
     for (int64_t c = slot; c < a.C; c += slots) off_chain<G, T, LJ>(a, c, w, g, logm, &gen);
 }
 
 template <int G, int T, bool LJ>
 int launch_long(const OffArgs &a, unsigned char *ws, size_t bytes, int logH, float inv_cell,
-                cudaStream_t s)
+                float pre2, cudaStream_t s)
 {
     auto kern = offlattice_long_kernel<G, T, LJ>;
     int bps = 0, dev = 0, sms = 0;
@@ -103,18 +103,18 @@ int launch_long(const OffArgs &a, unsigned char *ws, size_t bytes, int logH, flo
     if (e != cudaSuccess)
         return set_error(ROSEN_ECUDA, "rosen_offlattice_grow_long: %s", cudaGetErrorString(e));
     const int64_t grid = (slots * G + 255) / 256;
-    kern<<<(unsigned)grid, 256, 0, s>>>(a, ws, slots, slot_bytes, logH, inv_cell);
+    kern<<<(unsigned)grid, 256, 0, s>>>(a, ws, slots, slot_bytes, logH, inv_cell, pre2);
     return check_launch("rosen_offlattice_grow_long");
 }
 
 template <int G, bool LJ>
 int launch_long_g(const OffArgs &a, unsigned char *ws, size_t bytes, int logH, float inv_cell,
-                  cudaStream_t s)
+                  float pre2, cudaStream_t s)
 {
     const int T = (a.k + G - 1) / G;
-    if (T <= 1) return launch_long<G, 1, LJ>(a, ws, bytes, logH, inv_cell, s);
-    if (T <= 2) return launch_long<G, 2, LJ>(a, ws, bytes, logH, inv_cell, s);
-    return launch_long<G, 4, LJ>(a, ws, bytes, logH, inv_cell, s);
+    if (T <= 1) return launch_long<G, 1, LJ>(a, ws, bytes, logH, inv_cell, pre2, s);
+    if (T <= 2) return launch_long<G, 2, LJ>(a, ws, bytes, logH, inv_cell, pre2, s);
+    return launch_long<G, 4, LJ>(a, ws, bytes, logH, inv_cell, pre2, s);
 }
 
 }  // namespace
@@ -152,12 +152,20 @@ extern "C" int rosen_offlattice_grow_long(const rosen_offlattice_params *p,
     // position from its exact value (4e-7 per step), plus a margin.
     const double side = sqrt((double)a.rf2) * (1.0 + 1e-6) + 2e-6 * p->N + 1e-3;
     const float inv_cell = (float)(1.0 / side);
+    // Coarse-test threshold: |g|^2 from the hi words alone differs from the
+    // float-float value by the lo words (<= 6e-8 |x| <= 6e-8 N per axis) and
+    // FP32 rounding (< 1e-6): with d = 6e-8 N + 1e-6 and |g| <= rf + 1 the
+    // difference is below 3.5 (rf + 1) d + 3 d^2 + 4e-6 rf^2; doubled.
+    const double rf = sqrt((double)a.rf2);
+    const double d = 6e-8 * p->N + 1e-6;
+    const float pre2 =
+        (float)((double)a.rf2 + 2.0 * (3.5 * (rf + 1.0) * d + 3.0 * d * d + 4e-6 * a.rf2) + 1e-6);
     const int logH = long_log_cells(p->N);
     unsigned char *ws = static_cast<unsigned char *>(workspace);
     cudaStream_t s = (cudaStream_t)stream;
     if (G == 16)
-        return lj ? launch_long_g<16, true>(a, ws, workspace_bytes, logH, inv_cell, s)
-                  : launch_long_g<16, false>(a, ws, workspace_bytes, logH, inv_cell, s);
-    return lj ? launch_long_g<32, true>(a, ws, workspace_bytes, logH, inv_cell, s)
-              : launch_long_g<32, false>(a, ws, workspace_bytes, logH, inv_cell, s);
+        return lj ? launch_long_g<16, true>(a, ws, workspace_bytes, logH, inv_cell, pre2, s)
+                  : launch_long_g<16, false>(a, ws, workspace_bytes, logH, inv_cell, pre2, s);
+    return lj ? launch_long_g<32, true>(a, ws, workspace_bytes, logH, inv_cell, pre2, s)
+              : launch_long_g<32, false>(a, ws, workspace_bytes, logH, inv_cell, pre2, s);
 }
