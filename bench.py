@@ -401,9 +401,12 @@ def cpu_baseline(with_hs):
     import oracle
     threads = oracle.default_threads()
     value, rates, note = oracle_rates(with_hs, threads, budget_s=15.0)
+    # One core as well (the paper's CPU timings are single-core).
+    v1, r1, n1 = oracle_rates(with_hs, 1, budget_s=4.0)
     return {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": note + "; value = the full step's insertions over the summed time "
-                             "at these rates", "parts": rates}
+                             "at these rates", "parts": rates,
+            "single_core": {"value": v1, "cores": 1, "parts": r1, "sample": n1}}
 
 
 def run_reference(args):
