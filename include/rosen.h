@@ -321,7 +321,9 @@ ROSEN_API int rosen_reduce(const rosen_reduce_in *in, rosen_stats *out, void *wo
 
 typedef struct rosen_ensemble {
     int32_t model;       /* ROSEN_MODEL_LATTICE or ROSEN_MODEL_OFFLATTICE        */
-    int32_t N;           /* monomers per chain (lattice <= 512, real <= 1024)    */
+    int32_t N;           /* monomers per chain: lattice <= 32768, real space
+                            <= 16384; chains longer than 512 / 1024 are grown
+                            by the long-chain kernels (their own classes)     */
     int64_t C;           /* chains, >= 1; chain indices 0 .. C-1                 */
     uint64_t seed;
     uint32_t ensemble;   /* ensemble id, part of the Philox counter              */
@@ -390,7 +392,9 @@ typedef struct rosen_serve_config {
 
 typedef struct rosen_request {
     int32_t model;       /* ROSEN_MODEL_LATTICE or ROSEN_MODEL_OFFLATTICE        */
-    int32_t N;
+    int32_t N;           /* lattice <= 32768, real space <= 16384; longer than
+                            512 / 1024: grown by the long-chain entry points,
+                            with a workspace of at most 1 GiB from the budget */
     int64_t C;
     uint64_t seed;
     uint32_t ensemble;

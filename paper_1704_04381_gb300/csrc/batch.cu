@@ -38,6 +38,10 @@ namespace {
 struct ClassPlan {
     bool lattice;
     bool lj;
+    bool longc = false; // long chains: members grown one after another by the
+                        // hash-table / cell-grid kernels in one class workspace
+    void *d_ws = nullptr;
+    size_t ws_bytes = 0;
     int k;            // real space: trials per step (max over the class)
     int Nmax;
     std::vector<int> members;   // ensemble indices
@@ -195,6 +199,7 @@ int upload_args(rosen_batch *b, ClassPlan &c)
 
 int shape_class(rosen_batch *b, ClassPlan &c)
 {
+    if (c.longc) return ROSEN_OK;
     int bps = 0;
     int st;
     if (c.lattice) {
@@ -222,14 +227,29 @@ int upload_items(ClassPlan &c, const std::vector<BatchItem> &items)
     return ROSEN_OK;
 }
 
-void launch_class(const ClassPlan &c, cudaStream_t s)
+int launch_class(const rosen_batch *b, const ClassPlan &c, cudaStream_t s)
 {
-    if (c.n_items == 0) return;
+    if (c.longc) {
+        for (int e : c.members) {
+            int st;
+            if (c.lattice) {
+                const rosen_lattice_params p = lat_params(b->ens[e]);
+                st = rosen_lattice_grow_long(&p, &b->lat_out[e], c.d_ws, c.ws_bytes, s);
+            } else {
+                const rosen_offlattice_params p = off_params(b->ens[e], 0);
+                st = rosen_offlattice_grow_long(&p, &b->off_out[e], c.d_ws, c.ws_bytes, s);
+            }
+            if (st != ROSEN_OK) return st;
+        }
+        return ROSEN_OK;
+    }
+    if (c.n_items == 0) return ROSEN_OK;
     if (c.lattice)
         lattice_batch_launch(c.d_args, c.d_items, c.n_items, c.d_head, c.B, c.smem, c.grid, s);
     else
         offlattice_batch_launch(c.G, c.T, c.lj, c.d_args, c.d_items, c.n_items, c.d_head, c.cpb,
                                 c.Nmax, c.smem, c.grid, s);
+    return ROSEN_OK;
 }
 
 // Time every candidate shape of a class on a sample of its chains and keep
@@ -264,7 +284,7 @@ int tune_class(rosen_batch *b, ClassPlan &c)
         for (int rep = 0; rep < 2; ++rep) {
             CK(cudaMemsetAsync(c.d_head, 0, sizeof(int), b->s0));
             CK(cudaEventRecord(e0, b->s0));
-            launch_class(c, b->s0);
+            launch_class(b, c, b->s0);
             CK(cudaEventRecord(e1, b->s0));
             CK(cudaStreamSynchronize(b->s0));
             CK(cudaGetLastError());
@@ -307,7 +327,10 @@ int capture(rosen_batch *b)
     note(cudaEventRecord(b->forked, b->s0), "fork");
     for (ClassPlan &c : b->classes) {
         note(cudaStreamWaitEvent(c.stream, b->forked, 0), "wait fork");
-        launch_class(c, c.stream);
+        if (launch_class(b, c, c.stream) != ROSEN_OK && first == cudaSuccess) {
+            first = cudaErrorLaunchFailure;
+            what = "long-chain class launch";
+        }
         note(cudaGetLastError(), c.lattice ? "lattice class launch" : "real-space class launch");
         note(cudaEventRecord(c.done, c.stream), "record join");
         note(cudaStreamWaitEvent(b->s0, c.done, 0), "join");
@@ -327,19 +350,25 @@ int capture(rosen_batch *b)
     return ROSEN_OK;
 }
 
+// Members longer than the shared-memory kernels take go to long classes.
+bool is_long(const rosen_ensemble &e)
+{
+    return e.model == ROSEN_MODEL_LATTICE ? e.N > ROSEN_LATTICE_NMAX : e.N > ROSEN_OFFLATTICE_NMAX;
+}
+
 int validate_ensemble(const rosen_ensemble &e, int idx)
 {
     if (e.model == ROSEN_MODEL_LATTICE) {
         const rosen_lattice_params p = lat_params(e);
         rosen_lattice_out o;
         memset(&o, 0, sizeof o);
-        const int st = lattice_validate(&p, &o);
+        const int st = lattice_validate(&p, &o, ROSEN_LATTICE_LONG_NMAX);
         if (st != ROSEN_OK) return set_error(st, "ensemble %d: %s", idx, rosen_last_error());
     } else if (e.model == ROSEN_MODEL_OFFLATTICE) {
         const rosen_offlattice_params p = off_params(e, 0);
         rosen_offlattice_out o;
         memset(&o, 0, sizeof o);
-        const int st = offlattice_validate(&p, &o);
+        const int st = offlattice_validate(&p, &o, ROSEN_OFFLATTICE_LONG_NMAX);
         if (st != ROSEN_OK) return set_error(st, "ensemble %d: %s", idx, rosen_last_error());
     } else {
         return set_error(ROSEN_EINVAL, "ensemble %d: unknown model %d", idx, e.model);
@@ -354,6 +383,7 @@ void free_batch(rosen_batch *b)
         if (c.d_items) cudaFree(c.d_items);
         if (c.d_args) cudaFree(c.d_args);
         if (c.d_head) cudaFree(c.d_head);
+        if (c.d_ws) cudaFree(c.d_ws);
         if (c.stream) cudaStreamDestroy(c.stream);
         if (c.done) cudaEventDestroy(c.done);
     }
@@ -460,16 +490,19 @@ int create(rosen_batch *b, const rosen_ensemble *ens, int n)
         const rosen_ensemble &x = ens[e];
         const bool lat = x.model == ROSEN_MODEL_LATTICE;
         const bool lj = !lat && x.potential == ROSEN_LJ;
-        const int bk = bucket_of(x.N);
+        const bool lg = is_long(x);
+        const int bk = lg ? -1 : bucket_of(x.N);
         ClassPlan *found = nullptr;
         for (ClassPlan &c : b->classes)
-            if (c.lattice == lat && c.lj == lj && (lat || c.k == x.k) && bucket_of(c.Nmax) == bk)
+            if (c.lattice == lat && c.lj == lj && (lat || c.k == x.k) && c.longc == lg &&
+                (lg || bucket_of(c.Nmax) == bk))
                 found = &c;
         if (!found) {
             b->classes.push_back(ClassPlan());
             found = &b->classes.back();
             found->lattice = lat;
             found->lj = lj;
+            found->longc = lg;
             found->k = lat ? 0 : x.k;
             found->Nmax = 0;
         }
@@ -480,6 +513,24 @@ int create(rosen_batch *b, const rosen_ensemble *ens, int n)
         CK(cudaMalloc(&c.d_head, sizeof(int)));
         CK(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming));
+        if (c.longc) {
+            // One workspace for the members in turn: the largest default size
+            // among them, at most 8 GiB (fewer chains in flight, same results),
+            // at least one table or chain slot of the longest member.
+            size_t want = 0, least = 0;
+            for (int e : c.members) {
+                const rosen_ensemble &x = b->ens[e];
+                const size_t w = c.lattice ? rosen_lattice_long_workspace_size(x.N, x.C)
+                                           : rosen_offlattice_long_workspace_size(x.N, x.C);
+                const size_t one = c.lattice ? rosen_lattice_long_workspace_size(x.N, 1)
+                                             : rosen_offlattice_long_workspace_size(x.N, 1);
+                want = std::max(want, w);
+                least = std::max(least, one);
+            }
+            c.ws_bytes = std::max(least, std::min(want, (size_t)8 << 30));
+            CK(cudaMalloc(&c.d_ws, c.ws_bytes));
+            continue;
+        }
         // Untuned default shape: 128 chains per block (fewer if the keys of
         // the longest chain would not fit), or the default lanes per chain.
         if (c.lattice) {
@@ -520,6 +571,7 @@ extern "C" int rosen_batch_tune(rosen_batch *b, void *stream)
     (void)stream;
     if (!b) return set_error(ROSEN_EINVAL, "rosen_batch_tune: NULL batch");
     for (ClassPlan &c : b->classes) {
+        if (c.longc) continue;       // nothing to choose: fixed kernels
         const int st = tune_class(b, c);
         if (st != ROSEN_OK) return st;
     }
@@ -569,14 +621,15 @@ extern "C" int rosen_batch_describe(rosen_batch *b, char *buf, size_t len)
     std::string s = "[";
     for (size_t q = 0; q < b->classes.size(); ++q) {
         const ClassPlan &c = b->classes[q];
-        char line[320];
+        char line[448];
         snprintf(line, sizeof line,
                  "%s{\"model\":\"%s\",\"k\":%d,\"Nmax\":%d,\"ensembles\":%zu,\"items\":%d,"
                  "\"threads\":%d,\"lanes_per_chain\":%d,\"chains_per_block\":%d,\"grid\":%d,"
-                 "\"smem\":%zu,\"tuned\":%s,\"members\":[",
+                 "\"smem\":%zu,\"long\":%s,\"workspace\":%zu,\"tuned\":%s,\"members\":[",
                  q ? "," : "", c.lattice ? "lattice" : (c.lj ? "lj" : "hard_sphere"), c.k, c.Nmax,
                  c.members.size(), c.n_items, c.lattice ? c.B : c.cpb * c.G, c.lattice ? 1 : c.G,
-                 c.cpb, c.grid, c.smem, b->tuned ? "true" : "false");
+                 c.cpb, c.grid, c.smem, c.longc ? "true" : "false", c.ws_bytes,
+                 b->tuned ? "true" : "false");
         s += line;
         for (size_t m = 0; m < c.members.size(); ++m)
             s += (m ? "," : "") + std::to_string(c.members[m]);

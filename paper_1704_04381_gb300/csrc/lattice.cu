@@ -892,11 +892,12 @@ extern "C" int rosen_lattice_grow_long(const rosen_lattice_params *p, const rose
     cudaStream_t s = (cudaStream_t)stream;
     const cudaError_t e = cudaMemsetAsync(workspace, 0, (size_t)lanes * table, s);
     if (e != cudaSuccess)
-        return set_error(ROSEN_ECUDA, "rosen_lattice_grow_long: %s", cudaGetErrorString(e));
+        return set_error(ROSEN_ECUDA, "rosen_lattice_grow_long: clearing %lld tables of %zu bytes: %s",
+                         (long long)lanes, table, cudaGetErrorString(e));
     const unsigned grid = (unsigned)((lanes + 255) / 256);
     ulonglong2 *ws = static_cast<ulonglong2 *>(workspace);
     if (a.isaw) lattice_long_kernel<true><<<grid, 256, 0, s>>>(a, ws, lanes, logH);
     else lattice_long_kernel<false><<<grid, 256, 0, s>>>(a, ws, lanes, logH);
-    return check_launch("rosen_lattice_grow_long");
+    return check_launch("rosen_lattice_grow_long (kernel launch)");
 }
 

@@ -89,7 +89,8 @@ int launch_long(const OffArgs &a, unsigned char *ws, size_t bytes, int logH, flo
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess)
-        return set_error(ROSEN_ECUDA, "rosen_offlattice_grow_long: %s", cudaGetErrorString(e));
+        return set_error(ROSEN_ECUDA, "rosen_offlattice_grow_long: device query: %s",
+                         cudaGetErrorString(e));
     const size_t slot_bytes = long_slot_bytes(a.N, logH);
     int64_t slots = (int64_t)(bytes / slot_bytes);
     const int64_t resident = (int64_t)(bps > 0 ? bps : 1) * sms * (256 / G);
@@ -101,10 +102,11 @@ int launch_long(const OffArgs &a, unsigned char *ws, size_t bytes, int logH, flo
                          "of %zu bytes (N = %d)", bytes, slot_bytes, a.N);
     e = cudaMemsetAsync(ws, 0, (size_t)slots * slot_bytes, s);
     if (e != cudaSuccess)
-        return set_error(ROSEN_ECUDA, "rosen_offlattice_grow_long: %s", cudaGetErrorString(e));
+        return set_error(ROSEN_ECUDA, "rosen_offlattice_grow_long: clearing %lld slots of %zu bytes: %s",
+                         (long long)slots, slot_bytes, cudaGetErrorString(e));
     const int64_t grid = (slots * G + 255) / 256;
     kern<<<(unsigned)grid, 256, 0, s>>>(a, ws, slots, slot_bytes, logH, inv_cell, pre2);
-    return check_launch("rosen_offlattice_grow_long");
+    return check_launch("rosen_offlattice_grow_long (kernel launch)");
 }
 
 template <int G, bool LJ>

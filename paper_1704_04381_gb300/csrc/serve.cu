@@ -16,6 +16,7 @@
 #include <string.h>
 #include <time.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -93,16 +94,36 @@ bool valid_model(const rosen_request &r)
     return r.model == ROSEN_MODEL_LATTICE || r.model == ROSEN_MODEL_OFFLATTICE;
 }
 
+constexpr size_t kLongWorkspaceCap = size_t(1) << 30;
+
+bool long_request(const rosen_request &r)
+{
+    return r.model == ROSEN_MODEL_LATTICE ? r.N > ROSEN_LATTICE_NMAX : r.N > ROSEN_OFFLATTICE_NMAX;
+}
+
+// Workspace of a long-chain request: the default size, at most 1 GiB (fewer
+// chains in flight), at least one table or chain slot.
+size_t long_workspace_bytes(const rosen_request &r)
+{
+    if (!long_request(r)) return 0;
+    const bool lat = r.model == ROSEN_MODEL_LATTICE;
+    const size_t want = lat ? rosen_lattice_long_workspace_size(r.N, r.C)
+                            : rosen_offlattice_long_workspace_size(r.N, r.C);
+    const size_t one = lat ? rosen_lattice_long_workspace_size(r.N, 1)
+                           : rosen_offlattice_long_workspace_size(r.N, 1);
+    return align256(std::max(one, std::min(want, kLongWorkspaceCap)));
+}
+
 // Device bytes a request holds while it runs, and what stored conformations
 // keep after it finishes.
 void request_bytes(const rosen_request &r, size_t *work, size_t *coords)
 {
     const size_t C = (size_t)r.C, N = (size_t)r.N;
-    size_t b = 0;
+    size_t b = long_workspace_bytes(r);
     if (r.model == ROSEN_MODEL_LATTICE)
-        b = align256(16 * C) + align256(4 * C) + align256(4 * C) + align256(8 * C);
+        b += align256(16 * C) + align256(4 * C) + align256(4 * C) + align256(8 * C);
     else
-        b = 3 * align256(4 * C) + align256(C);
+        b += 3 * align256(4 * C) + align256(C);
     if (r.max_attempts > 1) b += align256(2 * C);   // attempts per chain (restart mode)
     b += align256(rosen_reduce_workspace_size(r.C)) + align256(sizeof(rosen_stats));
     *work = b;
@@ -126,7 +147,7 @@ int validate_request(const rosen_request &r)
         rosen_lattice_out o;
         memset(&o, 0, sizeof o);
         o.coords = r.store_coords ? reinterpret_cast<int32_t *>(16) : nullptr;
-        return lattice_validate(&p, &o);
+        return lattice_validate(&p, &o, ROSEN_LATTICE_LONG_NMAX, "rosen_serve_submit");
     }
     rosen_offlattice_params p;
     memset(&p, 0, sizeof p);
@@ -144,7 +165,7 @@ int validate_request(const rosen_request &r)
     rosen_offlattice_out o;
     memset(&o, 0, sizeof o);
     o.coords = r.store_coords ? reinterpret_cast<float *>(16) : nullptr;
-    return offlattice_validate(&p, &o);
+    return offlattice_validate(&p, &o, ROSEN_OFFLATTICE_LONG_NMAX, "rosen_serve_submit");
 }
 
 void fail(Request *q, int status, const char *msg)
@@ -175,6 +196,9 @@ void launch(rosen_server *s, Request *q)
         return;
     }
     unsigned char *p = static_cast<unsigned char *>(q->work);
+    const size_t long_bytes = long_workspace_bytes(r);
+    void *long_ws = long_bytes ? p : nullptr;   // long chains: their workspace first
+    p += long_bytes;
     rosen_reduce_in in;
     memset(&in, 0, sizeof in);
     in.N = r.N;
@@ -205,7 +229,8 @@ void launch(rosen_server *s, Request *q)
         lp.beta_eps = r.beta_eps;
         lp.flags = q->coords ? ROSEN_STORE_COORDS : 0;
         lp.max_attempts = r.max_attempts;
-        st = rosen_lattice_grow(&lp, &o, q->stream);
+        st = long_ws ? rosen_lattice_grow_long(&lp, &o, long_ws, long_bytes, q->stream)
+                     : rosen_lattice_grow(&lp, &o, q->stream);
         in.attempts = o.attempts;
         in.kind = ROSEN_REDUCE_LATTICE;
         in.use_counts = r.beta_eps == 0.0;
@@ -242,7 +267,8 @@ void launch(rosen_server *s, Request *q)
         op.beta_eps = r.beta_eps;
         op.flags = q->coords ? ROSEN_STORE_COORDS : 0;
         op.max_attempts = r.max_attempts;
-        st = rosen_offlattice_grow(&op, &o, q->stream);
+        st = long_ws ? rosen_offlattice_grow_long(&op, &o, long_ws, long_bytes, q->stream)
+                     : rosen_offlattice_grow(&op, &o, q->stream);
         in.attempts = o.attempts;
         in.kind = ROSEN_REDUCE_OFFLATTICE;
         in.k = r.k;

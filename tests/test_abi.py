@@ -214,7 +214,8 @@ def test_offlattice_empty_launch_is_a_no_op(rosen):
 
 
 @pytest.mark.parametrize("bad", [
-    dict(model=2), dict(N=1), dict(C=0), dict(model=0, N=600), dict(model=1, k=0),
+    dict(model=2), dict(N=1), dict(C=0), dict(model=0, N=40000), dict(model=1, N=20000),
+    dict(model=1, k=0),
     dict(model=1, potential=5), dict(beta_eps=-1.0), dict(max_attempts=-2),
     dict(model=0, max_attempts=70000),
 ])
