@@ -292,9 +292,14 @@ def run_ours(args):
             kname = "offlattice_group_kernel<16,2,hard sphere>"
         part["ops_per_chain"] = ops / C
         part["brute_ops_per_chain"] = sops / C
+        # Brute-force pair tests per second (every earlier monomer against
+        # every trial; the lattice scores six neighbours with one test).
+        pairs = (N - 1) * (N - 2) // 2 * (1 if it["kind"] == "lattice" else K_TRIALS)
+        part["pair_tests_per_s"] = pairs * C / (kms / 1e3)
         parts[it["name"]] = part
         rooflines.append((kms, sops, ops, kname))
     kms, sops, ops, kname = max(rooflines)
+    launches = ens.launches_per_step() * args.steps
     achieved = sops / (kms / 1e3)
     executed = ops / (kms / 1e3)
 
@@ -303,6 +308,12 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank != 0:
         return
+    # The metric's latency half: a short served run (one GPU only).
+    served = None
+    if not args.no_served and world == 1:
+        del ens
+        torch.cuda.empty_cache()
+        served = served_run(rosen, 40.0, 5.0, 40.0, 256, 1.0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -322,7 +333,8 @@ def run_ours(args):
                      "peak_basis": "%d SMs x 128 lanes x %.0f MHz (max SM clock)" % (sms, mhz)},
         "clocks": clocks.summary(),
         "e2e": e2e,
-        "gpu_launches": ens.launches_per_step() * args.steps,
+        "gpu_launches": launches,
+        "served": served,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(not args.lattice_only)
@@ -642,19 +654,17 @@ def run_long(args):
     print(json.dumps(line), flush=True)
 
 
-def run_served(args):
+def served_run(rosen, rate, duration, budget_gb, max_queue, scale):
+    """Poisson arrivals at `rate` per second for `duration` seconds, drawn from
+    the batched configuration's distribution (x scale), 20% storing their
+    conformations; returns the completed chains/s, latency percentiles and
+    admission counts."""
     import random
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_1704_04381_gb300 import rosen
-    torch.cuda.set_device(0)
-    # Request mix: the batched configuration's distribution, 20% with stored
-    # conformations; Poisson arrivals at args.rate per second.
-    pool = batch_config(rosen, n_ens=4096, seed=5, scale=args.batch_scale)
+    import numpy as np
+    pool = batch_config(rosen, n_ens=4096, seed=5, scale=scale)
     rng = random.Random(5)
-    srv = rosen.RosenServer(mem_budget_bytes=int(args.budget_gb * (1 << 30)), max_slots=64,
-                            max_queue=args.max_queue)
+    srv = rosen.RosenServer(mem_budget_bytes=int(budget_gb * (1 << 30)), max_slots=64,
+                            max_queue=max_queue)
     done, rejected, tickets = [], 0, []
     lock = threading.Lock()
     stop = threading.Event()
@@ -679,8 +689,8 @@ def run_served(args):
     n = 0
     chains_offered = 0
     while True:
-        t_next += rng.expovariate(args.rate)
-        if t_next - t0 > args.duration:
+        t_next += rng.expovariate(rate)
+        if t_next - t0 > duration:
             break
         now = time.perf_counter()
         if t_next > now:
@@ -698,26 +708,39 @@ def run_served(args):
         else:
             rejected += 1
     stop.set()
-    th.join(timeout=args.duration * 4 + 120)
+    th.join(timeout=duration * 4 + 120)
     wall = time.perf_counter() - t0
     srv.close()
-    import numpy as np
     ok = [r for r in done if r["status"] == rosen.ROSEN_OK]
     lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in ok]) if ok else np.zeros(1)
     chains = sum(int(r["stats"]["n"]) for r in ok)
+    return {"chains_per_s": chains / wall, "offered_requests": n, "rejected_busy": rejected,
+            "completed": len(ok), "offered_chains_per_s": chains_offered / duration,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+            "wall_s": wall, "rate_per_s": rate, "duration_s": duration}
+
+
+def run_served(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1704_04381_gb300 import rosen
+    torch.cuda.set_device(0)
+    r = served_run(rosen, args.rate, args.duration, args.budget_gb, args.max_queue,
+                   args.batch_scale)
     line = {
         "metric": "served chains/s with p50/p99 latency (Poisson arrivals)",
-        "value": chains / wall, "unit": "chains/s", "n_gpus": 1,
+        "value": r["chains_per_s"], "unit": "chains/s", "n_gpus": 1,
         "higher_is_better": True, "data": "synthetic",
         "config": {"workload": "requests from the batched distribution x %g, 20%% store "
                                "conformations" % args.batch_scale, "rate_per_s": args.rate,
                    "duration_s": args.duration, "budget_gb": args.budget_gb,
                    "max_queue": args.max_queue},
-        "offered_requests": n, "rejected_busy": rejected, "completed": len(ok),
-        "offered_chains_per_s": chains_offered / args.duration,
-        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "max": float(lat.max())},
-        "wall_s": wall,
+        "offered_requests": r["offered_requests"], "rejected_busy": r["rejected_busy"],
+        "completed": r["completed"], "offered_chains_per_s": r["offered_chains_per_s"],
+        "latency_ms": r["latency_ms"],
+        "wall_s": r["wall_s"],
     }
     print(json.dumps(line), flush=True)
 
@@ -730,6 +753,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-served", action="store_true",
+                    help="step: skip the short served run (40 requests/s for 5 s)")
     ap.add_argument("--lattice-only", action="store_true")
     ap.add_argument("--chains", type=int, default=None,
                     help="chains per ensemble (default 10^7); smaller values are for profiling")
