@@ -261,6 +261,15 @@ ROSEN_API int rosen_offlattice_grow_long(const rosen_offlattice_params *p,
  */
 ROSEN_API int rosen_sphere_points(const uint32_t *words, int64_t n, float *out, void *stream);
 
+/*
+ * The same unit vectors as float-float components, as the Lennard-Jones
+ * kernels add them to the chain's position (no paper counterpart: it keeps
+ * positions within ~1e-12 per step of exact).  out: device, 5n floats per
+ * pair: x hi, x lo, y hi, y lo, z.  Each component is within 1.5e-12 of the
+ * exact value; exposed so that bound can be checked exhaustively.
+ */
+ROSEN_API int rosen_sphere_points_ff(const uint32_t *words, int64_t n, float *out, void *stream);
+
 /* ---- ensemble reduction (Eq. 2 with W as weight, Eq. 9) --------------- */
 #define ROSEN_REDUCE_LATTICE 0    /* inputs: counts or logw, r2 (int32), n2rg2 */
 #define ROSEN_REDUCE_OFFLATTICE 1 /* inputs: logw, r2 (float), rg2 (float)     */

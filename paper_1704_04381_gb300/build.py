@@ -42,9 +42,48 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _ff(x):
+    """A double as a float-float pair (hi = nearest float, lo = nearest float
+    to the remainder), as C hex-float literals."""
+    import struct
+    f32 = lambda v: struct.unpack("<f", struct.pack("<f", v))[0]
+    hi = f32(x)
+    lo = f32(x - hi)
+    return float(hi).hex() + "f", float(lo).hex() + "f"
+
+
+def write_turn_table():
+    """Generate csrc/turn_table.cuh: cos and sin of 2 pi m / 256 (m = 0..255)
+    and the constant 2 pi / 2^24 as float-float pairs, from the host's
+    double-precision cos and sin.  Written only when its text changes."""
+    import math
+    lines = ["// turn_table.cuh -- generated by build.py (write_turn_table); do not edit.",
+             "// Float-float values from double-precision cos and sin on the host:",
+             "// kTurn[m] = {cos hi, sin hi, cos lo, sin lo} of 2 pi m / 256, and",
+             "// 2 pi / 2^24 (the angle of one unit of a 24-bit turn fraction).",
+             "#pragma once", "",
+             "namespace rosen {", ""]
+    kh, kl = _ff(2.0 * math.pi / 2.0 ** 24)
+    lines.append("constexpr float kTurnUnitHi = %s, kTurnUnitLo = %s;" % (kh, kl))
+    lines.append("")
+    lines.append("__constant__ float4 kTurn[256] = {")
+    for m in range(256):
+        ch, cl = _ff(math.cos(2.0 * math.pi * m / 256.0))
+        sh, sl = _ff(math.sin(2.0 * math.pi * m / 256.0))
+        lines.append("    {%s, %s, %s, %s}," % (ch, sh, cl, sl))
+    lines += ["};", "", "}  // namespace rosen", ""]
+    text = "\n".join(lines)
+    path = os.path.join(CSRC, "turn_table.cuh")
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as f:
+            f.write(text)
+    return path
+
+
 def build(force=False, verbose=False, extra_flags=()):
     """Compile and link librosen.so if any source changed; return its path."""
     os.makedirs(OUT, exist_ok=True)
+    write_turn_table()
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     hdrs = _headers()
     exe = nvcc()

@@ -96,6 +96,21 @@ __global__ void sphere_points_kernel(const uint2 *words, int64_t n, float *out)
     out[3 * q + 2] = u.z;
 }
 
+// Float-float directions as the Lennard-Jones kernels commit them.
+__global__ void sphere_points_ff_kernel(const uint2 *words, int64_t n, float *out)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const uint2 v = words[q];
+    float xh, xl, yh, yl, z;
+    dir_ff(v.x, v.y, xh, xl, yh, yl, z);
+    out[5 * q + 0] = xh;
+    out[5 * q + 1] = xl;
+    out[5 * q + 2] = yh;
+    out[5 * q + 3] = yl;
+    out[5 * q + 4] = z;
+}
+
 // Chains per block: 256 threads, fewer if the chains' shared memory would
 // exceed 96 KB (at least one warp).
 int chains_per_block_for(int G, int N, bool lj)
@@ -245,6 +260,11 @@ void offlattice_make_args(const rosen_offlattice_params *p, const rosen_offlatti
     a.alive = o->alive;
     a.trace = (p->flags & ROSEN_STORE_TRACE) ? o->trace : nullptr;
     a.coords = (p->flags & ROSEN_STORE_COORDS) ? o->coords : nullptr;
+    // Position drift from exact per step for chains that commit float-float
+    // directions (1.5e-12 per component) with float-float adds whose rounding
+    // grows with |r| <= N (7e-15 N), both with margin; kernels that commit
+    // FP32 directions use 4e-7 instead.
+    a.drift = (float)(4e-12 + 1e-14 * p->N);
     a.counters = counters;
     a.attempts = o->attempts;
     a.max_att = p->max_attempts > 1 ? (uint32_t)p->max_attempts : 1u;
@@ -311,4 +331,18 @@ extern "C" int rosen_sphere_points(const uint32_t *words, int64_t n, float *out,
     sphere_points_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0,
                            (cudaStream_t)stream>>>(reinterpret_cast<const uint2 *>(words), n, out);
     return check_launch("rosen_sphere_points");
+}
+
+extern "C" int rosen_sphere_points_ff(const uint32_t *words, int64_t n, float *out, void *stream)
+{
+    if (n < 0) return set_error(ROSEN_EINVAL, "rosen_sphere_points_ff: n < 0");
+    if (n > 0 && (!words || !out)) return set_error(ROSEN_EINVAL, "rosen_sphere_points_ff: NULL");
+    if (reinterpret_cast<uintptr_t>(words) & 7u)
+        return set_error(ROSEN_EINVAL, "rosen_sphere_points_ff: words must be 8-byte aligned");
+    if (n == 0) return ROSEN_OK;
+    const int threads = 256;
+    sphere_points_ff_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0,
+                              (cudaStream_t)stream>>>(reinterpret_cast<const uint2 *>(words), n,
+                                                      out);
+    return check_launch("rosen_sphere_points_ff");
 }

@@ -10,6 +10,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "turn_table.cuh"
 
 namespace rosen {
 namespace {
@@ -29,6 +30,7 @@ struct OffArgs {
     float *logw, *r2, *rg2;
     uint8_t *alive, *trace;
     float *coords;
+    float drift;                    // bound on a position's drift from exact, per step
     unsigned long long *counters;   // optional [3]: steps re-decided, chains, listed beads
     uint16_t *attempts;             // optional [C]
     uint32_t max_att;               // growths per chain (1: no restart)
@@ -145,12 +147,14 @@ __device__ __forceinline__ int cell_push(uint4 *cells, int logH, uint64_t want, 
 // since it was last exact.  d^2 = c + 2 u.g differs from the exact value by
 // 2 (g + u).dg + 2 g.du + rounding, with |du| <= 4e-7 per direction (the
 // exhaustively measured component error is 2.7e-7; z is exact), |dg| <=
-// D 4e-7 + 2.1e-7 |g| (drift plus the rounding of g), |g + u| <= dmax (sigma
+// D drift + 2.1e-7 |g| (drift plus the rounding of g), |g + u| <= dmax (sigma
 // at the hard-sphere decision, min(1 + |g|, cutoff) for LJ), and three FMA
-// roundings of values up to 2c.  Doubled for safety.
-__device__ __forceinline__ float pair_band(float gn, float c, int D, float dmax)
+// roundings of values up to 2c.  Doubled for safety.  The drift per step is
+// 4e-7 when positions sum the FP32 directions and about 1e-12 when they sum
+// float-float directions (dir_ff; Lennard-Jones with k > 32).
+__device__ __forceinline__ float pair_band(float gn, float c, int D, float dmax, float drift)
 {
-    const float dg = (float)D * 4e-7f + 2.1e-7f * gn;
+    const float dg = (float)D * drift + 2.1e-7f * gn;
     return 2.f * (2.f * dmax * dg + 2.f * gn * 4e-7f + 3.6e-7f * c);
 }
 
@@ -224,6 +228,92 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float v)
     const float t = lo + e;
     hi = s + t;
     lo = t - (hi - s);
+}
+
+// ---- float-float arithmetic (Knuth's TwoSum, Dekker's product with FMA) ----
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bp = s - a;
+    e = (a - (s - bp)) + (b - bp);
+}
+
+// Renormalise s + e with |e| small against s.
+__device__ __forceinline__ void quick_sum(float &s, float &e)
+{
+    const float t = s + e;
+    e = e - (t - s);
+    s = t;
+}
+
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float &ph, float &pl)
+{
+    ph = ah * bh;
+    pl = fmaf(ah, bh, -ph);            // exact error of the leading product
+    pl = fmaf(ah, bl, fmaf(al, bh, pl));
+    quick_sum(ph, pl);
+}
+
+__device__ __forceinline__ void ff_sum(float ah, float al, float bh, float bl, float &sh, float &sl)
+{
+    two_sum(ah, bh, sh, sl);
+    sl += al + bl;
+    quick_sum(sh, sl);
+}
+
+// The unit vector of words (a, b) as float-float components (z is exact).
+// With the turn fraction V = b >> 8 = 2^16 m + v, the angle 2 pi V / 2^24 is
+// 2 pi m / 256 (cos and sin from the float-float table kTurn) plus
+// t = 2 pi v / 2^24 < 0.0246, whose sin and cos come from their Taylor series:
+// sin t = t + d with d = -t^3/6 (1 - t^2/20 (1 - t^2/42)) in FP32 (|d| <
+// 2.5e-6, so its FP32 rounding is below 1e-12), cos t = 1 + e with
+// e = -q/2 + q^2/24 (1 - q/30), q = t^2 float-float.  The rotation and the
+// scaling by s = sqrt((1 - z)(1 + z)) are float-float products.  Each
+// component is within 1.5e-12 of the exact value (the FP32 part of d
+// dominates; the table and the truncations are below 3e-15).
+__device__ __forceinline__ void dir_ff(uint32_t a, uint32_t b, float &xh, float &xl, float &yh,
+                                       float &yl, float &z)
+{
+    z = 1.f - 2.f * u24f(a);
+    const float om = 1.f - z, op = 1.f + z;           // exact
+    const float ph = om * op, pl = fmaf(om, op, -ph);  // (1 - z)(1 + z), exactly
+    const float sh0 = sqrtf(ph);
+    float sh = sh0, sl = 0.f;
+    if (sh0 > 0.f) {
+        sl = __fdividef(fmaf(-sh0, sh0, ph) + pl, 2.f * sh0);
+        quick_sum(sh, sl);
+    }
+    const uint32_t V = b >> 8;
+    const float4 tb = kTurn[V >> 16];
+    const float v = (float)(V & 0xFFFFu);              // exact
+    float th = v * kTurnUnitHi;
+    float tl = fmaf(v, kTurnUnitHi, -th);
+    tl = fmaf(v, kTurnUnitLo, tl);
+    quick_sum(th, tl);
+    float qh = th * th;
+    float ql = fmaf(th, th, -qh);
+    ql = fmaf(2.f * th, tl, ql);
+    quick_sum(qh, ql);
+    const float d = -(th * qh) * (1.f / 6.f) *
+                    fmaf(-qh * (1.f / 20.f), fmaf(-qh, 1.f / 42.f, 1.f), 1.f);
+    float s2h, s2l;
+    two_sum(th, d, s2h, s2l);
+    s2l += tl;
+    quick_sum(s2h, s2l);
+    const float r = qh * qh * (1.f / 24.f) * fmaf(-qh, 1.f / 30.f, 1.f);
+    float c2h, c2l;
+    two_sum(1.f, -0.5f * qh, c2h, c2l);
+    c2l += fmaf(-0.5f, ql, r);
+    quick_sum(c2h, c2l);
+    float ah, al, bh, bl, ch, cl, nh, nl;
+    ff_mul(tb.x, tb.z, c2h, c2l, ah, al);              // cos(2 pi m/256) cos t
+    ff_mul(tb.y, tb.w, s2h, s2l, bh, bl);              // sin(2 pi m/256) sin t
+    ff_sum(ah, al, -bh, -bl, ch, cl);
+    ff_mul(tb.y, tb.w, c2h, c2l, ah, al);
+    ff_mul(tb.x, tb.z, s2h, s2l, bh, bl);
+    ff_sum(ah, al, bh, bl, nh, nl);
+    ff_mul(sh, sl, ch, cl, xh, xl);
+    ff_mul(sh, sl, nh, nl, yh, yl);
 }
 
 template <int G>
@@ -448,7 +538,7 @@ template <int G, bool LJ>
 __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong &w,
                                               const Group<G> &g, int i, uint64_t tag, float ehx,
                                               float ehy, float ehz, float elx, float ely, float elz,
-                                              int exact_upto)
+                                              int exact_upto, float drift)
 {
     const int cx = cell_coord(ehx, w.inv_cell), cy = cell_coord(ehy, w.inv_cell),
               cz = cell_coord(ehz, w.inv_cell);
@@ -492,7 +582,7 @@ __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong 
             if (LJ) {
                 const float gn = sqrtf(L.w - 1.f) * 1.001f + 1e-6f;
                 w.nbs[slot] = pair_band(gn, L.w, i - 1 - max(j, exact_upto),
-                                        fminf(1.f + gn, a.dband));
+                                        fminf(1.f + gn, a.dband), drift);
             }
         }
         nn += __popc(m);
@@ -521,6 +611,14 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                                           uint32_t *genp = nullptr)
 {
     constexpr bool kLong = !std::is_same<W, ChainSmem>::value;
+    // Lennard-Jones groups whose lanes hold several trials (k > 32) commit
+    // float-float directions: their many trials make FP64 re-decisions the
+    // larger cost, and the positions then drift by ~1e-12 per step instead
+    // of 4e-7, so the error bands shrink.  (At k <= 32 the extra commit work
+    // costs about what the saved re-decisions gain.)  The drift of the band
+    // follows the commit mode of this instantiation.
+    constexpr bool kFF = LJ && G * T > 32;
+    const float drift = kFF ? a.drift : 4e-7f;
     const int N = a.N, k = a.k;
     const uint32_t chain = a.chain0 + (uint32_t)c;
 
@@ -564,7 +662,7 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
             float band = 0.f;    // largest bead band of the step (hard spheres)
             if constexpr (kLong)
                 nn = long_near_list<G, LJ>(a, w, g, i, tag, ehx, ehy, ehz, elx, ely, elz,
-                                           exact_upto);
+                                           exact_upto, drift);
             for (int b0 = 0; !kLong && b0 <= i - 2; b0 += G) {
                 const int j = b0 + g.gl;
                 float4 L = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -586,7 +684,8 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                     if (LJ) {
                         const float gn = sqrtf(L.w - 1.f) * 1.001f + 1e-6f;
                         w.nb[slot] =
-                            pair_band(gn, L.w, i - 1 - max(j, exact_upto), fminf(1.f + gn, a.dband));
+                            pair_band(gn, L.w, i - 1 - max(j, exact_upto),
+                                      fminf(1.f + gn, a.dband), drift);
                     }
                 }
                 nn += __popc(m);
@@ -597,11 +696,12 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                 // One band for the step: the oldest listed bead drifted longest, and
                 // |g| <= sqrt(rf2), c <= 1 + rf2 for every listed bead.
                 const int D = i - 1 - max(w.nj[0], exact_upto);
-                band = pair_band(a.rf, 1.f + a.rf2, D, a.dband);
+                band = pair_band(a.rf, 1.f + a.rf2, D, a.dband, drift);
             }
 
             // ---- 2. trials ----------------------------------------------------
             float ux[T], uy[T], uz[T];
+            uint32_t twa[T], twb[T];   // the trials' words (for float-float commits)
             bool valid[T];
             uint32_t selw = 0;
             uint4 x = make_uint4(0u, 0u, 0u, 0u);
@@ -617,6 +717,8 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                            ((x.w & 0xFFu) << 24);
                 uint32_t wa, wb;
                 trial_words(x, t, wa, wb);
+                twa[s] = wa;
+                twb[s] = wb;
                 const float3 u = dir32(wa, wb);
                 ux[s] = 2.f * u.x;   // 2u: d^2 = c + (2u).g
                 uy[s] = 2.f * u.y;
@@ -760,21 +862,43 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
             // ---- 6. commit ----------------------------------------------------
             {
                 const int ss = sel % T;
-                float vx = 0.f, vy = 0.f, vz = 0.f;
-#pragma unroll
-                for (int s = 0; s < T; ++s)
-                    if (s == ss) {
-                        vx = ux[s];
-                        vy = uy[s];
-                        vz = uz[s];
-                    }
                 const int src = sel / T;
-                vx = 0.5f * g.bcast(vx, src);
-                vy = 0.5f * g.bcast(vy, src);
-                vz = 0.5f * g.bcast(vz, src);
-                ff_add(ehx, elx, vx);
-                ff_add(ehy, ely, vy);
-                ff_add(ehz, elz, vz);
+                if constexpr (kFF) {
+                    // The chosen trial's direction in float-float, so that
+                    // positions drift by ~1e-12 per step instead of 4e-7.
+                    uint32_t wa = 0u, wb = 0u;
+#pragma unroll
+                    for (int s = 0; s < T; ++s)
+                        if (s == ss) {
+                            wa = twa[s];
+                            wb = twb[s];
+                        }
+                    float xh = 0.f, xl = 0.f, yh = 0.f, yl = 0.f, zz = 0.f;
+                    if (g.gl == src) dir_ff(wa, wb, xh, xl, yh, yl, zz);
+                    xh = g.bcast(xh, src);
+                    xl = g.bcast(xl, src);
+                    yh = g.bcast(yh, src);
+                    yl = g.bcast(yl, src);
+                    zz = g.bcast(zz, src);
+                    ff_sum(ehx, elx, xh, xl, ehx, elx);
+                    ff_sum(ehy, ely, yh, yl, ehy, ely);
+                    ff_add(ehz, elz, zz);
+                } else {
+                    float vx = 0.f, vy = 0.f, vz = 0.f;
+#pragma unroll
+                    for (int s = 0; s < T; ++s)
+                        if (s == ss) {
+                            vx = ux[s];
+                            vy = uy[s];
+                            vz = uz[s];
+                        }
+                    vx = 0.5f * g.bcast(vx, src);
+                    vy = 0.5f * g.bcast(vy, src);
+                    vz = 0.5f * g.bcast(vz, src);
+                    ff_add(ehx, elx, vx);
+                    ff_add(ehy, ely, vy);
+                    ff_add(ehz, elz, vz);
+                }
                 if (g.gl == 0) {
                     float link = 0.f;
                     if constexpr (kLong)

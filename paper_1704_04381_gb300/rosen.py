@@ -133,6 +133,8 @@ def load():
     L.rosen_offlattice_grow.restype = ctypes.c_int
     L.rosen_sphere_points.argtypes = [_vp, ctypes.c_int64, _vp, _vp]
     L.rosen_sphere_points.restype = ctypes.c_int
+    L.rosen_sphere_points_ff.argtypes = [_vp, ctypes.c_int64, _vp, _vp]
+    L.rosen_sphere_points_ff.restype = ctypes.c_int
     L.rosen_reduce_workspace_size.argtypes = [ctypes.c_int64]
     L.rosen_reduce_workspace_size.restype = ctypes.c_size_t
     L.rosen_reduce.argtypes = [ctypes.POINTER(rosen_reduce_in), _vp, _vp, ctypes.c_size_t, _vp]
@@ -245,6 +247,12 @@ def rosen_offlattice_grow(params, out, stream=None):
                              counters=_ptr(out.get("counters")),
                              attempts=_ptr(out.get("attempts")))
     _check(load().rosen_offlattice_grow(ctypes.byref(params), ctypes.byref(o), _stream(stream)))
+
+
+def rosen_sphere_points_ff(words, out, stream=None):
+    """out [n, 5] float32 <- float-float directions (x hi, x lo, y hi, y lo, z) of words [n, 2]."""
+    n = words.shape[0]
+    _check(load().rosen_sphere_points_ff(_ptr(words), int(n), _ptr(out), _stream(stream)))
 
 
 def rosen_offlattice_long_workspace_size(N, C):
