@@ -91,7 +91,8 @@ def test_hard_sphere_paths(rosen, N, k):
 
 
 @pytest.mark.parametrize("N,k,beta_eps", [(64, 32, 1.0), (48, 16, 0.5), (30, 64, 0.7),
-                                          (20, 32, 0.0), (16, 8, 1.0)])
+                                          (20, 32, 0.0), (16, 8, 1.0), (24, 128, 0.8),
+                                          (40, 64, 1.2)])
 def test_lennard_jones_paths(rosen, N, k, beta_eps):
     C = 2000
     g = grow(rosen, 12, N, C, k, potential=1, beta_eps=beta_eps)

@@ -58,7 +58,8 @@ def same(a, b):
 
 @pytest.mark.parametrize("N,k,pot,beta_eps,lanes", [
     (2, 32, 0, 0.0, 16), (3, 32, 0, 0.0, 16), (64, 32, 0, 0.0, 16), (300, 32, 0, 0.0, 16),
-    (1024, 16, 0, 0.0, 32), (64, 32, 1, 1.0, 32), (500, 32, 1, 0.6, 32), (200, 16, 1, 0.8, 16)])
+    (1024, 16, 0, 0.0, 32), (64, 32, 1, 1.0, 32), (500, 32, 1, 0.6, 32), (200, 16, 1, 0.8, 16),
+    (300, 64, 1, 1.0, 32)])
 def test_equals_shared_memory_kernel(rosen, N, k, pot, beta_eps, lanes):
     C = 600 if N >= 500 else 3001
     a = grow(rosen, 51, N, C, k, True, pot, beta_eps, lanes=lanes, chain0=77, ensemble=2)
@@ -88,7 +89,7 @@ def compare_oracle(g, o, N, beta_eps=0.0):
 
 
 @pytest.mark.parametrize("N,C,k,pot,beta_eps", [(1500, 40, 16, 0, 0.0), (3000, 12, 32, 0, 0.0),
-                                                (2000, 12, 16, 1, 0.7)])
+                                                (2000, 12, 16, 1, 0.7), (1200, 12, 64, 1, 1.0)])
 def test_long_chains_follow_the_oracle(rosen, N, C, k, pot, beta_eps):
     g = grow(rosen, 53, N, C, k, True, pot, beta_eps, lanes=32 if pot else 16, coords=False)
     o = oracle.offlattice_run(53, N, C, k, potential=pot, beta_eps=beta_eps, trace=True)
