@@ -5,6 +5,7 @@
 // primitives, the FP64 replay and re-decision, and off_chain itself.
 #pragma once
 
+#include <limits.h>
 #include <math.h>
 
 #include <type_traits>
@@ -534,25 +535,43 @@ __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, c
 // cell (lanes walk different cells) and then put in ascending bead order --
 // the order in which the full scan lists them, so the step's arithmetic is
 // the same as in the shared-memory kernels.
+// The heads of the 27 cells are kept between steps (cell[], heads[2] per
+// lane: cells gl and gl + G): while the end stays in one cell the only change
+// to those lists is the previous commit, which put bead i - 1 at the head of
+// the end's own cell (index 13).
 template <int G, bool LJ>
 __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong &w,
                                               const Group<G> &g, int i, uint64_t tag, float ehx,
                                               float ehy, float ehz, float elx, float ely, float elz,
-                                              int exact_upto, float drift)
+                                              int exact_upto, float drift, int (&cell)[3],
+                                              int (&heads)[2])
 {
     const int cx = cell_coord(ehx, w.inv_cell), cy = cell_coord(ehy, w.inv_cell),
               cz = cell_coord(ehz, w.inv_cell);
-    auto head = [&](int q) {
-        const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = q / 9 - 1;
-        return cell_head(w.cells, w.logH, cell_key(cx + dx, cy + dy, cz + dz) | tag, tag);
-    };
+    if (cx != cell[0] || cy != cell[1] || cz != cell[2]) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int q = g.gl + r * G;
+            const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = q / 9 - 1;
+            heads[r] = q < 27 ? cell_head(w.cells, w.logH,
+                                          cell_key(cx + dx, cy + dy, cz + dz) | tag, tag)
+                              : -1;
+        }
+        cell[0] = cx;
+        cell[1] = cy;
+        cell[2] = cz;
+    } else {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            if (g.gl + r * G == 13) heads[r] = i - 1;
+    }
     int q = g.gl;
-    int j = q < 27 ? head(q) : -1;
+    int j = heads[0];
     int nn = 0;
     for (;;) {
-        while (j < 0 && q < 27) {
+        if (j < 0 && q == g.gl) {
             q += G;
-            if (q < 27) j = head(q);
+            j = q < 27 ? heads[1] : -1;
         }
         const bool has = j >= 0;
         if (!g.ballot(has)) break;
@@ -640,6 +659,7 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
         dead_at = 0;
         exact_upto = 0;
         uint64_t tag = 0;
+        int cell[3] = {INT_MIN, 0, 0}, heads[2] = {-1, -1};   // long chains: cached cell heads
         if constexpr (kLong) {
             // A fresh generation of the cell grid for this growth; bead 0 in
             // the cell of the origin.
@@ -662,7 +682,7 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
             float band = 0.f;    // largest bead band of the step (hard spheres)
             if constexpr (kLong)
                 nn = long_near_list<G, LJ>(a, w, g, i, tag, ehx, ehy, ehz, elx, ely, elz,
-                                           exact_upto, drift);
+                                           exact_upto, drift, cell, heads);
             for (int b0 = 0; !kLong && b0 <= i - 2; b0 += G) {
                 const int j = b0 + g.gl;
                 float4 L = make_float4(0.f, 0.f, 0.f, 0.f);

@@ -145,10 +145,12 @@ extern "C" int rosen_offlattice_grow_long(const rosen_offlattice_params *p,
         return set_error(ROSEN_EINVAL, "rosen_offlattice_grow_long: workspace must be a "
                                        "non-NULL, 16-byte aligned device pointer");
     const bool lj = p->potential == ROSEN_LJ;
-    // Default lanes: hard spheres take a warp per chain here (one cell walk
-    // per lane: measured 21% faster than 16 lanes at N = 4096), Lennard-Jones
-    // the shared-memory kernel's default.
-    int G = p->lanes_per_chain ? p->lanes_per_chain : (lj ? offlattice_default_lanes(p->k, lj) : 32);
+    // Default lanes (measured on GB300 with the cached cell heads): hard
+    // spheres take a warp per chain from N = 2048 (one cell walk per lane;
+    // 71 vs 81 ms at N = 4096) and 16 lanes below (42 vs 46 ms at N = 1024);
+    // Lennard-Jones the shared-memory kernel's default.
+    int G = p->lanes_per_chain ? p->lanes_per_chain
+                               : (lj ? offlattice_default_lanes(p->k, lj) : (p->N >= 2048 ? 32 : 16));
     if (G < 16) G = 16;
     if ((p->k + G - 1) / G > 4) G = 32;
     OffArgs a;
