@@ -33,6 +33,8 @@ sys.path.insert(0, ROOT)
 N = 64
 C = 10_000_000
 K_TRIALS = 32
+REAL_POT = "hard_sphere"    # the step's real-space ensemble: hard_sphere or lj
+REAL_BETA = 0.0
 LATTICE = [(0.0, 2), (0.2, 3), (0.4, 4)]
 HS_SEED = 5
 WORKLOAD = ("N=64, 1e7 chains per ensemble: lattice ISAW beta*eps {0, 0.2, 0.4} + "
@@ -181,9 +183,11 @@ class Ensembles:
                 "stats": rosen.stats_tensor(dev)})
         if with_hs:
             out = rosen.offlattice_outputs(N, C, device=dev, counters=True, attempts=restart)
+            pot = rosen.ROSEN_LJ if REAL_POT == "lj" else rosen.ROSEN_HARD_SPHERE
             self.items.append({
-                "name": "hard_sphere_k32", "kind": "offlattice",
-                "params": rosen.offlattice_params(HS_SEED, N, C, K_TRIALS, chain0=chain0,
+                "name": "%s_k%d" % (REAL_POT, K_TRIALS), "kind": "offlattice",
+                "params": rosen.offlattice_params(HS_SEED, N, C, K_TRIALS, potential=pot,
+                                                  beta_eps=REAL_BETA, chain0=chain0,
                                                   max_attempts=max_attempts),
                 "out": out, "rin": rosen.offlattice_reduce_in(out, N, K_TRIALS),
                 "stats": rosen.stats_tensor(dev)})
@@ -289,7 +293,8 @@ def run_ours(args):
             sops = brute_offlattice_ops(N, K_TRIALS) * C
             part.update({"fp64_redecided_steps": cnt[0] / reps,
                          "listed_beads_per_step": listed / (C * (N - 1))})
-            kname = "offlattice_group_kernel<16,2,hard sphere>"
+            kname = ("offlattice_group_kernel<16,2,hard sphere>" if REAL_POT == "hard_sphere"
+                     else "offlattice_group_kernel<LJ, k=%d, beta eps %g>" % (K_TRIALS, REAL_BETA))
         part["ops_per_chain"] = ops / C
         part["brute_ops_per_chain"] = sops / C
         # Brute-force pair tests per second (every earlier monomer against
@@ -321,6 +326,7 @@ def run_ours(args):
         "data": "synthetic (Philox-seeded growth; no input data)",
         "config": {"workload": WORKLOAD, "N": N, "chains_per_ensemble": C * world,
                    "lattice_beta_eps": [b for b, _ in LATTICE], "hs_k": K_TRIALS,
+                   "real_space": {"potential": REAL_POT, "k": K_TRIALS, "beta_eps": REAL_BETA},
                    "max_attempts": max(1, args.max_attempts),
                    "l2": "no inputs; outputs 160-320 MB per ensemble > 129 MB L2, no flush",
                    "parallelism": "dp%d (chain ranges per GPU)" % world},
@@ -395,13 +401,16 @@ def oracle_rates(with_hs, threads, budget_s):
         notes.append("lattice beta_eps=%.1f: first %d chains (%.1f s)" % (b, S, dt))
     if with_hs:
         t = time.perf_counter()
-        oracle.offlattice_run(HS_SEED, N, 200, K_TRIALS, threads=threads)
+        pot = oracle.LJ if REAL_POT == "lj" else oracle.HARD_SPHERE
+        oracle.offlattice_run(HS_SEED, N, 200, K_TRIALS, potential=pot, beta_eps=REAL_BETA,
+                              threads=threads)
         cal = (time.perf_counter() - t) / 200
         S = n_hs or max(200, int(2 * budget_s / (len(LATTICE) + 2) / max(cal, 1e-9)))
         t = time.perf_counter()
-        oracle.offlattice_run(HS_SEED, N, S, K_TRIALS, threads=threads)
+        oracle.offlattice_run(HS_SEED, N, S, K_TRIALS, potential=pot, beta_eps=REAL_BETA,
+                              threads=threads)
         dt = time.perf_counter() - t
-        rates["hard_sphere_k32"] = S * (N - 1) / dt
+        rates["%s_k%d" % (REAL_POT, K_TRIALS)] = S * (N - 1) / dt
         notes.append("hard spheres k=32: first %d chains (%.1f s)" % (S, dt))
     # The whole step at these rates: total insertions / total time.
     total_time = sum(C * (N - 1) / r for r in rates.values())
@@ -767,11 +776,20 @@ def main():
     ap.add_argument("--max-queue", type=int, default=256)
     ap.add_argument("--max-attempts", type=int, default=0,
                     help="step: restart mode, growths per chain (0/1: dead ends keep W = 0)")
+    ap.add_argument("--real", default="hard_sphere", choices=["hard_sphere", "lj"],
+                    help="step: the real-space ensemble (default: hard spheres, k = 32)")
+    ap.add_argument("--real-k", type=int, default=32)
+    ap.add_argument("--real-beta-eps", type=float, default=1.0,
+                    help="step: LJ well depth over kT (with --real lj)")
     ap.add_argument("--long-n", default="1000,10000", help="long: chain lengths")
     ap.add_argument("--long-beta-eps", type=float, default=0.0)
     ap.add_argument("--long-real-n", default="1000,10000", help="long: real-space lengths")
     ap.add_argument("--long-real-chains", type=int, default=100_000)
     args = ap.parse_args()
+    global K_TRIALS, REAL_POT, REAL_BETA
+    K_TRIALS = args.real_k
+    REAL_POT = args.real
+    REAL_BETA = args.real_beta_eps if args.real == "lj" else 0.0
     if args.workload == "long":
         return run_long(args)
     if args.workload == "batched":
