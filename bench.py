@@ -259,10 +259,9 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     ms = t0.elapsed_time(t1)
+    from paper_1704_04381_gb300 import shard
     if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = shard.max_over_ranks(ms)
     ms_per_step = ms / args.steps
     ins_per_step = len(ens.items) * C * (N - 1) * world
     value = ins_per_step / (ms_per_step / 1e3)
@@ -278,6 +277,10 @@ def run_ours(args):
     for q, it in enumerate(ens.items):
         kms = statistics.mean(per_q[q])
         st = rosen.stats_dict(it["stats"])
+        if world > 1:
+            # Every rank grew its own chain range: merge the statistics (18
+            # numbers per rank) into the ensemble's.
+            st = shard.gather_stats(st, N, K_TRIALS if it["kind"] == "offlattice" else 0)
         part = {"kernel_ms": kms, "insertions_per_s": C * (N - 1) / (kms / 1e3),
                 "mean_r2": st["mean_r2"], "se_r2": st["se_r2"], "logZ": st["logZ"],
                 "n_alive": st["n_alive"], "growths": st["n"]}
