@@ -311,6 +311,28 @@ def run_ours(args):
     achieved = sops / (kms / 1e3)
     executed = ops / (kms / 1e3)
 
+    # The small correctness configuration, timed too: athermal lattice chains,
+    # N = 16, 10^5 chains, seed 1 (growth and reduction, CUDA events).
+    n16 = None
+    if rank == 0:
+        o16 = rosen.lattice_outputs(16, 100_000, device=dev)
+        p16 = rosen.lattice_params(1, 16, 100_000)
+        r16 = rosen.lattice_reduce_in(o16, 16, use_counts=1)
+        s16, w16 = rosen.stats_tensor(dev), rosen.reduce_workspace(100_000, dev)
+        for _ in range(3):
+            rosen.rosen_lattice_grow(p16, o16, stream)
+            rosen.rosen_reduce(r16, s16, w16, stream)
+        a16, b16 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a16.record(stream)
+        for _ in range(20):
+            rosen.rosen_lattice_grow(p16, o16, stream)
+            rosen.rosen_reduce(r16, s16, w16, stream)
+        b16.record(stream)
+        torch.cuda.synchronize()
+        ms16 = a16.elapsed_time(b16) / 20
+        n16 = {"workload": "lattice athermal N=16, 1e5 chains, seed 1", "ms": ms16,
+               "insertions_per_s": 100_000 * 15 / (ms16 / 1e3),
+               "logZ": rosen.stats_dict(s16)["logZ"]}
     e2e = None if args.no_e2e else measure_e2e(args, rosen, torch, dev, stream, chain0, ens)
     if world > 1:
         dist.destroy_process_group()
@@ -344,6 +366,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": launches,
         "served": served,
+        "small_config": n16,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(not args.lattice_only)
