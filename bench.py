@@ -660,10 +660,13 @@ def run_long(args):
             ms = e0.elapsed_time(e1) / args.steps
             sd = rosen.stats_dict(st)
             ins = Cr * (Nl - 1)
+            cnt = out["counters"].cpu().tolist()      # over warm-up and timed launches
+            launches = max(1, args.warmup) + args.steps
             parts["hard_sphere_k32_N%d" % Nl] = {
                 "ms": ms, "insertions_per_s": ins / (ms / 1e3), "chains": Cr,
                 "alive_frac": sd["n_alive"] / Cr, "logZ_norm": sd["logZ_norm"],
-                "mean_r2": sd["mean_r2"], "workspace_gb": ws.numel() * 8 / 1e9}
+                "mean_r2": sd["mean_r2"], "workspace_gb": ws.numel() * 8 / 1e9,
+                "fp64_redecided_steps_per_chain": cnt[0] / launches / Cr}
             tot_ins += ins
             tot_ms += ms
             del out, ws

@@ -376,15 +376,20 @@ struct Group {
     }
 };
 
-// FP64 replay of r_1 .. r_{i-1} from the chosen trials; the exact positions
-// are stored back into the float-float arrays and the end returned.
+// FP64 replay of r_{b+1} .. r_{i-1} from the chosen trials, starting at bead
+// b, the last bead replayed before (its float-float position is its FP64 one
+// to 2^-48 relative); the positions are stored back into the float-float
+// arrays and the end returned.  Only the steps since the last replay are
+// summed, so the cost does not grow with i.
 template <int G>
 __device__ __noinline__ void replay_positions(const OffArgs &a, const ChainSmem &w,
                                               const Group<G> &g, uint32_t chain, uint32_t aw,
-                                              int i, double &ex, double &ey, double &ez)
+                                              int b, int i, double &ex, double &ey, double &ez)
 {
-    double cx = 0.0, cy = 0.0, cz = 0.0;
-    for (int b0 = 1; b0 <= i - 1; b0 += G) {
+    const float4 bh = w.hi[b], bl = w.lo[b];
+    double cx = (double)bh.x + (double)bl.x, cy = (double)bh.y + (double)bl.y,
+           cz = (double)bh.z + (double)bl.z;
+    for (int b0 = b + 1; b0 <= i - 1; b0 += G) {
         const int s = b0 + g.gl;
         double x = 0.0, y = 0.0, z = 0.0;
         if (s <= i - 1) {
@@ -418,14 +423,15 @@ __device__ __noinline__ void replay_positions(const OffArgs &a, const ChainSmem 
 // the sequential FP64 arithmetic of the definition.
 template <int G, int T, bool LJ>
 __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, const Group<G> &g,
-                                      uint32_t chain, uint32_t aw, int i, int nn, uint32_t selw,
+                                      uint32_t chain, uint32_t aw, int b, int i, int nn,
+                                      uint32_t selw,
                                       const float *logm, float &ehx, float &ehy, float &ehz,
                                       float &elx, float &ely, float &elz, int &sel, float &logS,
                                       int &dead_at)
 {
     const int k = a.k;
     double ex, ey, ez;
-    replay_positions<G>(a, w, g, chain, aw, i, ex, ey, ez);
+    replay_positions<G>(a, w, g, chain, aw, b, i, ex, ey, ez);
     // The exact end, back into the float-float registers.
     ehx = (float)ex;
     elx = (float)(ex - ehx);
@@ -873,8 +879,8 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
             // ---- 5. FP64 re-decision of an ambiguous step -------------------
             if (!ok) {
                 ++rechecks;
-                redecide<G, T, LJ>(a, w, g, chain, aw, i, nn, selw, logm, ehx, ehy, ehz, elx, ely,
-                                   elz, sel, logS, dead_at);
+                redecide<G, T, LJ>(a, w, g, chain, aw, exact_upto, i, nn, selw, logm, ehx, ehy,
+                                   ehz, elx, ely, elz, sel, logS, dead_at);
                 exact_upto = i - 1;
             }
             if (dead_at) break;

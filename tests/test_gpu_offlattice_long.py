@@ -91,9 +91,17 @@ def compare_oracle(g, o, N, beta_eps=0.0):
 @pytest.mark.parametrize("N,C,k,pot,beta_eps", [(1500, 40, 16, 0, 0.0), (3000, 12, 32, 0, 0.0),
                                                 (2000, 12, 16, 1, 0.7), (1200, 12, 64, 1, 1.0)])
 def test_long_chains_follow_the_oracle(rosen, N, C, k, pot, beta_eps):
-    g = grow(rosen, 53, N, C, k, True, pot, beta_eps, lanes=32 if pot else 16, coords=False)
-    o = oracle.offlattice_run(53, N, C, k, potential=pot, beta_eps=beta_eps, trace=True)
+    g = grow(rosen, 53, N, C, k, True, pot, beta_eps, lanes=32 if pot else 16)
+    o = oracle.offlattice_run(53, N, C, k, potential=pot, beta_eps=beta_eps, trace=True,
+                              coords=True)
     compare_oracle(g, o, N, beta_eps)
+    # Positions of identical paths: within the FP32 drift bound of the
+    # oracle's, however many FP64 replays (each from the last replayed bead)
+    # the chain went through.
+    assert g["counters"][0] > 0
+    same = (g["trace"].T == o["trace"]).all(1) & (o["alive"] == 1)
+    xyz = np.transpose(g["coords"], (2, 0, 1))[same].astype(np.float64)
+    assert np.abs(xyz - o["coords"][same]).max() <= (N - 1) * 4e-7 + 1e-6
 
 
 def test_longest_chains(rosen):
