@@ -536,15 +536,19 @@ __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, c
     }
 }
 
-// Near list of step i for a long chain: the beads 0..i-2 of the 27 cells
-// around the end's cell that lie within the list radius, gathered cell by
-// cell (lanes walk different cells) and then put in ascending bead order --
-// the order in which the full scan lists them, so the step's arithmetic is
-// the same as in the shared-memory kernels.
+// Near list of step i for a long chain: the beads 0..i-2 that lie within the
+// list radius of the end, in ascending bead order -- the order in which the
+// full scan lists them, so the step's arithmetic is the same as in the
+// shared-memory kernels.
+// A bead is filed in the cell grid only once it is G steps old: the G most
+// recent non-bonded beads (i-1-G .. i-2), which are the ones most often near
+// the end and would make the end's own cell list long, are tested directly
+// (one per lane, independent loads); the lists of the 27 cells around the
+// end's cell then hold only beads 0..i-2-G, few of them near, and are walked
+// cell by cell (lanes on different cells).
 // The heads of the 27 cells are kept between steps (cell[], heads[2] per
 // lane: cells gl and gl + G): while the end stays in one cell the only change
-// to those lists is the previous commit, which put bead i - 1 at the head of
-// the end's own cell (index 13).
+// to those lists is the bead filed at this step, which heads its cell's list.
 template <int G, bool LJ>
 __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong &w,
                                               const Group<G> &g, int i, uint64_t tag, float ehx,
@@ -552,6 +556,26 @@ __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong 
                                               int exact_upto, float drift, int (&cell)[3],
                                               int (&heads)[2])
 {
+    // File bead i-2-G in the cell of its current position.
+    const int fb = i - 2 - G;
+    if (fb >= 0) {
+        const float4 hb = w.hi[fb];
+        const int bx = cell_coord(hb.x, w.inv_cell), by = cell_coord(hb.y, w.inv_cell),
+                  bz = cell_coord(hb.z, w.inv_cell);
+        if (g.gl == 0) {
+            const int link = cell_push(w.cells, w.logH, cell_key(bx, by, bz) | tag, tag, fb);
+            reinterpret_cast<float *>(w.hi + fb)[3] = __int_as_float(link);
+        }
+        const int dx = bx - cell[0], dy = by - cell[1], dz = bz - cell[2];
+        if (cell[0] != INT_MIN && dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 &&
+            dz <= 1) {
+            const int qb = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+                if (g.gl + r * G == qb) heads[r] = fb;
+        }
+        __syncwarp(g.mask);
+    }
     const int cx = cell_coord(ehx, w.inv_cell), cy = cell_coord(ehy, w.inv_cell),
               cz = cell_coord(ehz, w.inv_cell);
     if (cx != cell[0] || cy != cell[1] || cz != cell[2]) {
@@ -566,10 +590,6 @@ __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong 
         cell[0] = cx;
         cell[1] = cy;
         cell[2] = cz;
-    } else {
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-            if (g.gl + r * G == 13) heads[r] = i - 1;
     }
     int q = g.gl;
     int j = heads[0];
@@ -612,6 +632,33 @@ __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong 
         }
         nn += __popc(m);
         if (has) j = __float_as_int(h.w);
+    }
+    {
+        // The G most recent non-bonded beads, one per lane.
+        const int j = i - 1 - G + g.gl;
+        float4 L = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool near = false;
+        if (j >= 0) {
+            const float4 h = w.hi[j], l = w.lo[j];
+            const float gx = (ehx - h.x) + (elx - l.x);
+            const float gy = (ehy - h.y) + (ely - l.y);
+            const float gz = (ehz - h.z) + (elz - l.z);
+            const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+            L = make_float4(gx, gy, gz, 1.f + g2);
+            near = g2 < a.rf2;
+        }
+        const unsigned m = g.ballot(near);
+        if (near) {
+            const int slot = nn + __popc(m & ((1u << g.gl) - 1u));
+            w.nls[slot] = L;
+            w.njs[slot] = j;
+            if (LJ) {
+                const float gn = sqrtf(L.w - 1.f) * 1.001f + 1e-6f;
+                w.nbs[slot] = pair_band(gn, L.w, i - 1 - max(j, exact_upto),
+                                        fminf(1.f + gn, a.dband), drift);
+            }
+        }
+        nn += __popc(m);
     }
     __syncwarp(g.mask);
     for (int p = g.gl; p < nn; p += G) {
@@ -667,19 +714,14 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
         uint64_t tag = 0;
         int cell[3] = {INT_MIN, 0, 0}, heads[2] = {-1, -1};   // long chains: cached cell heads
         if constexpr (kLong) {
-            // A fresh generation of the cell grid for this growth; bead 0 in
-            // the cell of the origin.
+            // A fresh generation of the cell grid for this growth (beads are
+            // filed G steps after they are placed).
             if (++*genp > kCellGenMax) {
                 for (int h = g.gl; h < (1 << w.logH); h += G) w.cells[h] = make_uint4(0u, 0u, 0u, 0u);
                 *genp = 1;
                 __syncwarp(g.mask);
             }
             tag = (uint64_t)*genp << kCellGenShift;
-            if (g.gl == 0) {
-                const int link = cell_push(w.cells, w.logH, cell_key(0, 0, 0) | tag, tag, 0);
-                w.hi[0] = make_float4(0.f, 0.f, 0.f, __int_as_float(link));
-            }
-            __syncwarp(g.mask);
         }
 
         for (int i = 1; i < N; ++i) {
@@ -926,14 +968,8 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                     ff_add(ehz, elz, vz);
                 }
                 if (g.gl == 0) {
-                    float link = 0.f;
-                    if constexpr (kLong)
-                        link = __int_as_float(cell_push(
-                            w.cells, w.logH,
-                            cell_key(cell_coord(ehx, w.inv_cell), cell_coord(ehy, w.inv_cell),
-                                     cell_coord(ehz, w.inv_cell)) | tag,
-                            tag, i));
-                    w.hi[i] = make_float4(ehx, ehy, ehz, link);
+                    // (.w: a long chain's cell link, set when the bead is filed)
+                    w.hi[i] = make_float4(ehx, ehy, ehz, 0.f);
                     w.lo[i] = make_float4(elx, ely, elz, 0.f);
                     w.tr[i] = (uint8_t)sel;
                 }
