@@ -122,6 +122,20 @@ def test_longest_chains(rosen):
     compare(g, o, N, min_same=1.0)
 
 
+def test_longest_lennard_jones_chains_and_replayed_positions(rosen):
+    # Many re-decisions per chain: each FP64 replay starts at the bead the
+    # previous one ended on, so the positions carry the chained replays.
+    # They stay within the FP32 drift bound of the oracle's.
+    N, C, k = 1024, 8, 16
+    g = grow(rosen, 4, N, C, k, potential=1, beta_eps=0.8, coords=True)
+    o = oracle.offlattice_run(4, N, C, k, potential=oracle.LJ, beta_eps=0.8, trace=True,
+                              coords=True)
+    compare(g, o, N, 0.8, min_same=1.0)
+    assert g["counters"][0] >= 5 * C
+    xyz = np.transpose(g["coords"], (2, 0, 1)).astype(np.float64)
+    assert np.abs(xyz - o["coords"]).max() <= (N - 1) * 4e-7 + 1e-6
+
+
 def test_sharding_is_invisible(rosen):
     N, C = 32, 2000
     whole = grow(rosen, 9, N, C, 32, potential=1, beta_eps=0.8)
