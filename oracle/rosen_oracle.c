@@ -27,7 +27,7 @@
  *
  * Parity status of each function (what pins it to something other than
  * itself; the pins are the -m "not gpu" tests):
- *   orc_philox4x32_10      pinned on the GPU machine against cuRAND's
+ *   orc_philox4x32_10      pinned on the GPU against cuRAND's
  *                          Philox4_32_10 generator (a library routine)
  *   orc_lattice_chain      pinned by exact enumeration (c_n, <R^2>, Z_n)
  *   orc_offlattice_chain   pinned by closed forms (trimer), the ideal limit,
