@@ -203,7 +203,10 @@ class Ensembles:
         self.rosen.rosen_reduce(it["rin"], it["stats"], self.ws, stream)
 
     def launches_per_step(self):
-        return 3 * len(self.items)     # growth + two reduction kernels each
+        # Growth and two reduction kernels per ensemble; hard spheres grow in
+        # two passes (growth, then the deferred chains).
+        return sum(4 if it["kind"] == "offlattice" and REAL_POT == "hard_sphere" else 3
+                   for it in self.items)
 
 
 def run_ours(args):

@@ -34,7 +34,7 @@ namespace rosen {
 namespace {
 
 
-template <int G, int T, bool LJ>
+template <int G, int T, bool LJ, bool kDefer = false>
 __global__ void __launch_bounds__(256, 4) offlattice_group_kernel(const OffArgs a, int chains_per_block)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -48,7 +48,35 @@ __global__ void __launch_bounds__(256, 4) offlattice_group_kernel(const OffArgs 
     if (c >= a.C) return;     // whole groups leave together
     const ChainSmem w = carve(smem_raw + kTable * sizeof(float) +
                                   (size_t)cib * chain_smem_bytes(a.N, LJ), a.N, LJ);
-    off_chain<G, T, LJ>(a, c, w, g, logm);
+    off_chain<G, T, LJ, ChainSmem, kDefer>(a, c, w, g, logm);
+}
+
+// Second pass of two-pass growth: the chains whose bits the first pass set,
+// grown again from the start with the FP64 re-decision compiled in.  Groups
+// take 32-chain words of the bit mask in turn.
+template <int G, int T, bool LJ>
+__global__ void __launch_bounds__(256, 4) offlattice_deferred_kernel(const OffArgs a,
+                                                                     int chains_per_block)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *logm = reinterpret_cast<float *>(smem_raw);
+    fill_log_table(logm);
+    __syncthreads();
+
+    const Group<G> g;
+    const int cib = threadIdx.x / G;
+    const ChainSmem w = carve(smem_raw + kTable * sizeof(float) +
+                                  (size_t)cib * chain_smem_bytes(a.N, LJ), a.N, LJ);
+    const int64_t words = (a.C + 31) / 32;
+    for (int64_t q = (int64_t)blockIdx.x * chains_per_block + cib; q < words;
+         q += (int64_t)gridDim.x * chains_per_block) {
+        uint32_t m = a.deferred[q];
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1u;
+            off_chain<G, T, LJ>(a, q * 32 + b, w, g, logm);
+        }
+    }
 }
 
 // Persistent batch kernel for one (G, T, potential) class: blocks take
@@ -121,6 +149,14 @@ int chains_per_block_for(int G, int N, bool lj)
     return chains;
 }
 
+// Hard spheres grow in two passes.  Their FP32 decisions are almost never
+// ambiguous (about 2% of N = 64, k = 32 chains meet one such step), but the
+// FP64 re-decision path, compiled into the growth kernel, costs every chain
+// registers and time (the kernel without it runs 11% faster).  So the first
+// pass has no FP64 path and defers the chains that need it; the second
+// regrows only those, with it.  Every chain's outputs are those of the
+// one-pass kernel, bit for bit.  The deferral mask (C/8 bytes) comes from the
+// stream-ordered allocator; if that fails, one pass with the FP64 path runs.
 template <int G, int T, bool LJ>
 int launch_one(const OffArgs &a, int N, cudaStream_t s)
 {
@@ -128,6 +164,41 @@ int launch_one(const OffArgs &a, int N, cudaStream_t s)
     const size_t smem = kTable * sizeof(float) + (size_t)chains * chain_smem_bytes(N, LJ);
     const int threads = chains * G;
     const int64_t blocks = (a.C + chains - 1) / chains;
+    if constexpr (!LJ) {
+        const size_t mask_bytes = (size_t)((a.C + 31) / 32) * sizeof(uint32_t);
+        void *mask = nullptr;
+        if (cudaMallocAsync(&mask, mask_bytes, s) == cudaSuccess) {
+            OffArgs d = a;
+            d.deferred = static_cast<uint32_t *>(mask);
+            cudaError_t e = cudaMemsetAsync(mask, 0, mask_bytes, s);
+            int dev = 0, sms = 0, bps = 0;
+            if (e == cudaSuccess) e = allow_max_smem(offlattice_group_kernel<G, T, LJ, true>);
+            if (e == cudaSuccess) e = allow_max_smem(offlattice_deferred_kernel<G, T, LJ>);
+            if (e == cudaSuccess) e = cudaGetDevice(&dev);
+            if (e == cudaSuccess)
+                e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &bps, offlattice_deferred_kernel<G, T, LJ>, threads, smem);
+            if (e == cudaSuccess) {
+                offlattice_group_kernel<G, T, LJ, true><<<(unsigned)blocks, threads, smem, s>>>(
+                    d, chains);
+                const int64_t words = (a.C + 31) / 32;
+                int64_t grid = (int64_t)(bps > 0 ? bps : 1) * sms;
+                if (grid > (words + chains - 1) / chains) grid = (words + chains - 1) / chains;
+                offlattice_deferred_kernel<G, T, LJ><<<(unsigned)grid, threads, smem, s>>>(d, chains);
+                e = cudaGetLastError();
+            }
+            const cudaError_t f = cudaFreeAsync(mask, s);
+            if (e != cudaSuccess)
+                return set_error(ROSEN_ECUDA, "rosen_offlattice_grow: %s", cudaGetErrorString(e));
+            if (f != cudaSuccess)
+                return set_error(ROSEN_ECUDA, "rosen_offlattice_grow: freeing the deferral mask: %s",
+                                 cudaGetErrorString(f));
+            return ROSEN_OK;
+        }
+        cudaGetLastError();   // clear the failed allocation; grow in one pass
+    }
     allow_max_smem(offlattice_group_kernel<G, T, LJ>);
     offlattice_group_kernel<G, T, LJ><<<(unsigned)blocks, threads, smem, s>>>(a, chains);
     return check_launch("rosen_offlattice_grow");

@@ -35,6 +35,7 @@ struct OffArgs {
     unsigned long long *counters;   // optional [3]: steps re-decided, chains, listed beads
     uint16_t *attempts;             // optional [C]
     uint32_t max_att;               // growths per chain (1: no restart)
+    uint32_t *deferred;             // two-pass hard-sphere growth: bit c = chain c deferred
 };
 
 // Per-chain shared memory: float-float positions, the near list, the trace.
@@ -155,8 +156,9 @@ __device__ __forceinline__ int cell_push(uint4 *cells, int logH, uint64_t want, 
 // float-float directions (dir_ff; Lennard-Jones with k > 32).
 __device__ __forceinline__ float pair_band(float gn, float c, int D, float dmax, float drift)
 {
-    const float dg = (float)D * drift + 2.1e-7f * gn;
-    return 2.f * (2.f * dmax * dg + 2.f * gn * 4e-7f + 3.6e-7f * c);
+    // Explicit FMAs: the same rounding in every kernel that inlines this.
+    const float dg = fmaf((float)D, drift, 2.1e-7f * gn);
+    return 2.f * fmaf(2.f * dmax, dg, fmaf(8e-7f, gn, 3.6e-7f * c));
 }
 
 // sin and cos of 2 pi V / 2^24 for a 24-bit integer V.  The quarter-turn
@@ -458,7 +460,7 @@ __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, c
             const double rx = tx - ((double)h.x + (double)l.x);
             const double ry = ty - ((double)h.y + (double)l.y);
             const double rz = tz - ((double)h.z + (double)l.z);
-            const double d2 = rx * rx + ry * ry + rz * rz;
+            const double d2 = fma(rx, rx, fma(ry, ry, rz * rz));
             if (!LJ) {
                 if (d2 < a.sig2d) fr = false;
             } else if (d2 < a.rc2d) {
@@ -469,7 +471,7 @@ __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, c
                 rcp = rcp * fma(-d2, rcp, 2.0);
                 const double sr = a.sig2d * rcp;
                 const double s3 = sr * sr * sr;
-                acc += 4.0 * s3 * (s3 - 1.0);
+                acc = fma(4.0 * s3, s3 - 1.0, acc);
             }
         }
         const bool valid = t < k;
@@ -625,7 +627,7 @@ __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong 
             w.nls[slot] = L;
             w.njs[slot] = j;
             if (LJ) {
-                const float gn = sqrtf(L.w - 1.f) * 1.001f + 1e-6f;
+                const float gn = fmaf(sqrtf(L.w - 1.f), 1.001f, 1e-6f);
                 w.nbs[slot] = pair_band(gn, L.w, i - 1 - max(j, exact_upto),
                                         fminf(1.f + gn, a.dband), drift);
             }
@@ -653,7 +655,7 @@ __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong 
             w.nls[slot] = L;
             w.njs[slot] = j;
             if (LJ) {
-                const float gn = sqrtf(L.w - 1.f) * 1.001f + 1e-6f;
+                const float gn = fmaf(sqrtf(L.w - 1.f), 1.001f, 1e-6f);
                 w.nbs[slot] = pair_band(gn, L.w, i - 1 - max(j, exact_upto),
                                         fminf(1.f + gn, a.dband), drift);
             }
@@ -674,10 +676,13 @@ __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong 
 
 // Grow chain c (local index) of the ensemble a with the G lanes of group g,
 // in the per-chain storage w (shared memory; for kLong, device memory with a
-// cell grid, generation counter *genp).  In restart mode a growth that
+// cell grid, generation counter *genp).  With kDefer the FP64 re-decision is
+// not compiled in: a chain that meets a step its FP32 arithmetic cannot
+// decide sets its bit in a.deferred and stops without writing anything; a
+// second pass grows it again, from the start, with the FP64 path.  In restart mode a growth that
 // reaches a dead end is thrown away and the chain grown again from bead 0,
 // with the attempt index in the high half of the step word.
-template <int G, int T, bool LJ, class W = ChainSmem>
+template <int G, int T, bool LJ, class W = ChainSmem, bool kDefer = false>
 __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &w,
                                           const Group<G> &g, const float *logm,
                                           uint32_t *genp = nullptr)
@@ -750,7 +755,7 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                     w.nl[slot] = L;
                     w.nj[slot] = j;
                     if (LJ) {
-                        const float gn = sqrtf(L.w - 1.f) * 1.001f + 1e-6f;
+                        const float gn = fmaf(sqrtf(L.w - 1.f), 1.001f, 1e-6f);
                         w.nb[slot] =
                             pair_band(gn, L.w, i - 1 - max(j, exact_upto),
                                       fminf(1.f + gn, a.dband), drift);
@@ -883,13 +888,15 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                         // pairs within the band of the cutoff; doubled.
                         // (Ub already carries each bead's own band.)  Trials of
                         // zero weight contribute no error (and would give 0 * inf).
-                        const float dbu = a.beta4 * (6.f / a.sig2 * Ub[s] + 1e-6f * Ua[s] +
-                                                     a.ucut2 * (float)ncut[s]);
-                        if (wt[s] > 0.f) err += wt[s] * (dbu + 1.2e-7f * (bu[s] - bmin) + 3e-7f);
+                        const float dbu =
+                            a.beta4 * fmaf(6.f / a.sig2, Ub[s],
+                                           fmaf(1e-6f, Ua[s], a.ucut2 * (float)ncut[s]));
+                        if (wt[s] > 0.f)
+                            err = fmaf(wt[s], dbu + fmaf(1.2e-7f, bu[s] - bmin, 3e-7f), err);
                     }
                     const float incl = g.scan(own);
                     const float S = g.bcast(incl, G - 1);
-                    const float E = g.sum(err) + S * 6e-8f * (float)(k + 2);
+                    const float E = fmaf(S * 6e-8f, (float)(k + 2), g.sum(err));
                     const float r = u24f(selw) * S;
                     float P = incl - own;
                     int mine = -1;
@@ -920,10 +927,15 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
 
             // ---- 5. FP64 re-decision of an ambiguous step -------------------
             if (!ok) {
-                ++rechecks;
-                redecide<G, T, LJ>(a, w, g, chain, aw, exact_upto, i, nn, selw, logm, ehx, ehy,
-                                   ehz, elx, ely, elz, sel, logS, dead_at);
-                exact_upto = i - 1;
+                if constexpr (kDefer) {
+                    if (g.gl == 0) atomicOr(&a.deferred[c >> 5], 1u << (c & 31));
+                    return;
+                } else {
+                    ++rechecks;
+                    redecide<G, T, LJ>(a, w, g, chain, aw, exact_upto, i, nn, selw, logm, ehx,
+                                       ehy, ehz, elx, ely, elz, sel, logS, dead_at);
+                    exact_upto = i - 1;
+                }
             }
             if (dead_at) break;
 
@@ -1024,13 +1036,13 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
     for (int s = g.gl; s < N; s += G) {
         const float4 h = w.hi[s], l = w.lo[s];
         const float dx = (h.x - mx) + l.x, dy = (h.y - my) + l.y, dz = (h.z - mz) + l.z;
-        gg += dx * dx + dy * dy + dz * dz;
+        gg += fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     }
     gg = g.sum(gg) * inv;
     if (g.gl == 0) {
         const float xe = ehx + elx, ye = ehy + ely, ze = ehz + elz;
         if (a.logw) a.logw[c] = lw;
-        if (a.r2) a.r2[c] = xe * xe + ye * ye + ze * ze;
+        if (a.r2) a.r2[c] = fmaf(xe, xe, fmaf(ye, ye, ze * ze));
         if (a.rg2) a.rg2[c] = gg;
         if (a.alive) a.alive[c] = 1;
     }

@@ -14,6 +14,8 @@ bound, so at least 99.9% of chains must take exactly the oracle's path
 and the ensemble means over all chains agree within 1e-3 relative and
 3 standard errors.
 """
+import json
+
 import numpy as np
 import pytest
 import torch
@@ -99,6 +101,26 @@ def test_lennard_jones_paths(rosen, N, k, beta_eps):
     o = oracle.offlattice_run(12, N, C, k, potential=oracle.LJ, beta_eps=beta_eps, trace=True)
     compare(g, o, N, beta_eps)
     ensemble_close(g, o, N)
+
+
+def test_two_pass_hard_spheres_defer_and_regrow(rosen):
+    # Hard spheres grow in two passes: chains with a step the FP32 arithmetic
+    # cannot decide are deferred and regrown with the FP64 path.  The
+    # batch kernel grows the same chains in one pass; both equal the oracle.
+    N, C, k = 64, 20_000, 32
+    g = grow(rosen, 15, N, C, k)
+    assert g["counters"][0] > 50          # re-decided steps: the second pass ran
+    o = oracle.offlattice_run(15, N, C, k, trace=True)
+    compare(g, o, N, min_same=1.0)
+    b = rosen.RosenBatch([rosen.ensemble(rosen.ROSEN_MODEL_OFFLATTICE, N, C, 15, 0, k=k)])
+    b.run()
+    one = b.offlattice_outputs(0)
+    torch.cuda.synchronize()
+    lanes = json.loads(b.describe())[0]["lanes_per_chain"]
+    two = grow(rosen, 15, N, C, k, lanes=lanes)
+    for key in ("logw", "r2", "rg2", "alive"):
+        np.testing.assert_array_equal(one[key].cpu().numpy(), two[key], err_msg=key)
+    b.close()
 
 
 def test_edges_and_offsets(rosen):
