@@ -52,8 +52,11 @@ __global__ void __launch_bounds__(256, 4) offlattice_group_kernel(const OffArgs 
 }
 
 // Second pass of two-pass growth: the chains whose bits the first pass set,
-// grown again from the start with the FP64 re-decision compiled in.  Groups
-// take 32-chain words of the bit mask in turn.
+// grown again from the start with the FP64 re-decision compiled in.  Warps
+// take 32-chain words of the bit mask from a counter (the word after the
+// mask), so the few deferred chains spread evenly; the groups of a warp take
+// a word's set bits together, one each per round, so they step in lock-step
+// as in the first pass instead of diverging.
 template <int G, int T, bool LJ>
 __global__ void __launch_bounds__(256, 4) offlattice_deferred_kernel(const OffArgs a,
                                                                      int chains_per_block)
@@ -68,13 +71,20 @@ __global__ void __launch_bounds__(256, 4) offlattice_deferred_kernel(const OffAr
     const ChainSmem w = carve(smem_raw + kTable * sizeof(float) +
                                   (size_t)cib * chain_smem_bytes(a.N, LJ), a.N, LJ);
     const int64_t words = (a.C + 31) / 32;
-    for (int64_t q = (int64_t)blockIdx.x * chains_per_block + cib; q < words;
-         q += (int64_t)gridDim.x * chains_per_block) {
+    unsigned int *next = a.deferred + words;
+    const int gw = (threadIdx.x & 31) / G;     // this group's place in its warp
+    for (;;) {
+        unsigned int q = 0;
+        if ((threadIdx.x & 31) == 0) q = atomicAdd(next, 1u);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if ((int64_t)q >= words) break;
         uint32_t m = a.deferred[q];
         while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1u;
-            off_chain<G, T, LJ>(a, q * 32 + b, w, g, logm);
+            uint32_t mine = m;                   // the gw-th set bit of m, if any
+            for (int t = 0; t < gw && mine; ++t) mine &= mine - 1u;
+            if (mine) off_chain<G, T, LJ>(a, (int64_t)q * 32 + __ffs(mine) - 1, w, g, logm);
+            for (int t = 0; t < 32 / G && m; ++t) m &= m - 1u;
+            __syncwarp();
         }
     }
 }
@@ -165,7 +175,8 @@ int launch_one(const OffArgs &a, int N, cudaStream_t s)
     const int threads = chains * G;
     const int64_t blocks = (a.C + chains - 1) / chains;
     if constexpr (!LJ) {
-        const size_t mask_bytes = (size_t)((a.C + 31) / 32) * sizeof(uint32_t);
+        // The mask, then the second pass's word counter.
+        const size_t mask_bytes = (size_t)((a.C + 31) / 32 + 1) * sizeof(uint32_t);
         void *mask = nullptr;
         if (cudaMallocAsync(&mask, mask_bytes, s) == cudaSuccess) {
             OffArgs d = a;
