@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(256, 4) offlattice_batch_kernel(const OffArgs 
         for (int q = threadIdx.x; q < kWords; q += blockDim.x)
             reinterpret_cast<uint32_t *>(&sa)[q] = reinterpret_cast<const uint32_t *>(&ens[bi.ens])[q];
         __syncthreads();
-        if (cib < (int)bi.n) off_chain<G, T, LJ>(sa, bi.c0 + cib, w, g, logm);
+        if (cib < (int)bi.n) off_chain<G, T, LJ, ChainSmem, false, true>(sa, bi.c0 + cib, w, g, logm);
         __syncthreads();
     }
 }

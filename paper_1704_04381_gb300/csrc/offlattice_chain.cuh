@@ -383,7 +383,20 @@ struct Group {
 // to 2^-48 relative); the positions are stored back into the float-float
 // arrays and the end returned.  Only the steps since the last replay are
 // summed, so the cost does not grow with i.
-template <int G>
+// Philox draw of counter c under the ensemble's key.  kFly computes the round
+// keys on the fly from the first (two adds per round) instead of reading the
+// precomputed schedule: kernels whose OffArgs live in shared memory (the
+// batch kernels) would otherwise hold 20 key words in registers.
+template <bool kFly>
+__device__ __forceinline__ uint4 draw(const OffArgs &a, uint4 c)
+{
+    if constexpr (kFly)
+        return philox(c, a.key.k0[0], a.key.k1[0]);
+    else
+        return philox(c, a.key);
+}
+
+template <int G, bool kFly = false>
 __device__ __noinline__ void replay_positions(const OffArgs &a, const ChainSmem &w,
                                               const Group<G> &g, uint32_t chain, uint32_t aw,
                                               int b, int i, double &ex, double &ey, double &ez)
@@ -397,7 +410,7 @@ __device__ __noinline__ void replay_positions(const OffArgs &a, const ChainSmem 
         if (s <= i - 1) {
             const int t = w.tr[s];
             const uint4 q =
-                philox(make_uint4(chain, a.ens, (uint32_t)s | aw, 1u + (uint32_t)(t >> 1)), a.key);
+                draw<kFly>(a, make_uint4(chain, a.ens, (uint32_t)s | aw, 1u + (uint32_t)(t >> 1)));
             uint32_t wa, wb;
             trial_words(q, t, wa, wb);
             dir64(wa, wb, x, y, z);
@@ -423,7 +436,7 @@ __device__ __noinline__ void replay_positions(const OffArgs &a, const ChainSmem 
 // FP64 re-decision of step i: replay the exact positions, recompute every
 // trial's free flag or energy in FP64 from the listed beads, and select with
 // the sequential FP64 arithmetic of the definition.
-template <int G, int T, bool LJ>
+template <int G, int T, bool LJ, bool kFly = false>
 __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, const Group<G> &g,
                                       uint32_t chain, uint32_t aw, int b, int i, int nn,
                                       uint32_t selw,
@@ -433,7 +446,7 @@ __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, c
 {
     const int k = a.k;
     double ex, ey, ez;
-    replay_positions<G>(a, w, g, chain, aw, b, i, ex, ey, ez);
+    replay_positions<G, kFly>(a, w, g, chain, aw, b, i, ex, ey, ez);
     // The exact end, back into the float-float registers.
     ehx = (float)ex;
     elx = (float)(ex - ehx);
@@ -446,7 +459,7 @@ __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, c
     for (int s = 0; s < T; ++s) {
         const int t = T * g.gl + s;
         const uint4 xx =
-            philox(make_uint4(chain, a.ens, (uint32_t)i | aw, 1u + (uint32_t)(t >> 1)), a.key);
+            draw<kFly>(a, make_uint4(chain, a.ens, (uint32_t)i | aw, 1u + (uint32_t)(t >> 1)));
         uint32_t wa, wb;
         trial_words(xx, t, wa, wb);
         double dx, dy, dz;
@@ -682,7 +695,7 @@ __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong 
 // second pass grows it again, from the start, with the FP64 path.  In restart mode a growth that
 // reaches a dead end is thrown away and the chain grown again from bead 0,
 // with the attempt index in the high half of the step word.
-template <int G, int T, bool LJ, class W = ChainSmem, bool kDefer = false>
+template <int G, int T, bool LJ, class W = ChainSmem, bool kDefer = false, bool kFly = false>
 __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &w,
                                           const Group<G> &g, const float *logm,
                                           uint32_t *genp = nullptr)
@@ -783,8 +796,8 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                 const int t = T * g.gl + s;
                 valid[s] = t < k;
                 if (T == 1 || (s & 1) == 0)
-                    x = philox(make_uint4(chain, a.ens, (uint32_t)i | aw, 1u + (uint32_t)(t >> 1)),
-                               a.key);
+                    x = draw<kFly>(
+                        a, make_uint4(chain, a.ens, (uint32_t)i | aw, 1u + (uint32_t)(t >> 1)));
                 if (s == 0)
                     selw = (x.x & 0xFFu) | ((x.y & 0xFFu) << 8) | ((x.z & 0xFFu) << 16) |
                            ((x.w & 0xFFu) << 24);
@@ -932,7 +945,7 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                     return;
                 } else {
                     ++rechecks;
-                    redecide<G, T, LJ>(a, w, g, chain, aw, exact_upto, i, nn, selw, logm, ehx,
+                    redecide<G, T, LJ, kFly>(a, w, g, chain, aw, exact_upto, i, nn, selw, logm, ehx,
                                        ehy, ehz, elx, ely, elz, sel, logS, dead_at);
                     exact_upto = i - 1;
                 }
