@@ -343,11 +343,12 @@ def run_ours(args):
     if rank != 0:
         return
     # The metric's latency half: a short served run (one GPU only).
-    served = None
+    served = served_sf = None
     if not args.no_served and world == 1:
         del ens
         torch.cuda.empty_cache()
         served = served_run(rosen, 40.0, 5.0, 40.0, 256, 1.0)
+        served_sf = served_run(rosen, 40.0, 5.0, 40.0, 256, 1.0, shortest_first=True)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -370,6 +371,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": launches,
         "served": served,
+        "served_shortest_first": served_sf,
         "small_config": n16,
     }
     if not args.no_cpu_baseline:
@@ -696,17 +698,17 @@ def run_long(args):
     print(json.dumps(line), flush=True)
 
 
-def served_run(rosen, rate, duration, budget_gb, max_queue, scale):
+def served_run(rosen, rate, duration, budget_gb, max_queue, scale, shortest_first=False):
     """Poisson arrivals at `rate` per second for `duration` seconds, drawn from
     the batched configuration's distribution (x scale), 20% storing their
     conformations; returns the completed chains/s, latency percentiles and
-    admission counts."""
+    admission counts.  shortest_first: the server's priority streams."""
     import random
     import numpy as np
     pool = batch_config(rosen, n_ens=4096, seed=5, scale=scale)
     rng = random.Random(5)
     srv = rosen.RosenServer(mem_budget_bytes=int(budget_gb * (1 << 30)), max_slots=64,
-                            max_queue=max_queue)
+                            max_queue=max_queue, shortest_first=shortest_first)
     done, rejected, tickets = [], 0, []
     lock = threading.Lock()
     stop = threading.Event()
@@ -770,7 +772,7 @@ def run_served(args):
     from paper_1704_04381_gb300 import rosen
     torch.cuda.set_device(0)
     r = served_run(rosen, args.rate, args.duration, args.budget_gb, args.max_queue,
-                   args.batch_scale)
+                   args.batch_scale, shortest_first=args.shortest_first)
     line = {
         "metric": "served chains/s with p50/p99 latency (Poisson arrivals)",
         "value": r["chains_per_s"], "unit": "chains/s", "n_gpus": 1,
@@ -778,7 +780,7 @@ def run_served(args):
         "config": {"workload": "requests from the batched distribution x %g, 20%% store "
                                "conformations" % args.batch_scale, "rate_per_s": args.rate,
                    "duration_s": args.duration, "budget_gb": args.budget_gb,
-                   "max_queue": args.max_queue},
+                   "max_queue": args.max_queue, "shortest_first": args.shortest_first},
         "offered_requests": r["offered_requests"], "rejected_busy": r["rejected_busy"],
         "completed": r["completed"], "offered_chains_per_s": r["offered_chains_per_s"],
         "latency_ms": r["latency_ms"],
@@ -807,6 +809,8 @@ def main():
     ap.add_argument("--duration", type=float, default=20.0, help="served: seconds of arrivals")
     ap.add_argument("--budget-gb", type=float, default=40.0)
     ap.add_argument("--max-queue", type=int, default=256)
+    ap.add_argument("--shortest-first", action="store_true",
+                    help="served: priority streams by request work (small requests first)")
     ap.add_argument("--max-attempts", type=int, default=0,
                     help="step: restart mode, growths per chain (0/1: dead ends keep W = 0)")
     ap.add_argument("--real", default="hard_sphere", choices=["hard_sphere", "lj"],

@@ -396,7 +396,13 @@ typedef struct rosen_serve_config {
     int32_t max_slots;         /* requests on the GPU at once, 1..1024          */
     int32_t max_queue;         /* waiting requests before submit says EBUSY     */
     int32_t device;            /* CUDA device                                   */
-    int32_t reserved;          /* set to 0                                      */
+    int32_t shortest_first;    /* 0: running requests share the GPU as the
+                                  block scheduler interleaves their kernels;
+                                  1: streams get priorities by the request's
+                                  work (decades of pair tests from 1e8), so
+                                  small requests' blocks are dispatched first
+                                  (lower median latency, higher tail latency
+                                  for the largest requests under load)       */
 } rosen_serve_config;
 
 typedef struct rosen_request {

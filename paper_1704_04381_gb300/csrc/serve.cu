@@ -7,11 +7,15 @@
 // requests that arrive while others are on the GPU run concurrently with them
 // (the block scheduler interleaves the kernels of all active streams).  Output
 // memory comes from a stream-ordered pool; the statistics land in pinned host
-// memory.  Completion is detected with event queries on the host -- no kernel
+// memory.  With shortest_first the streams carry priorities by the request's
+// work (decades of pair tests): when SMs free up, the blocks of smaller
+// requests are dispatched first, so a small request does not wait behind the
+// waves of a large one (nothing is preempted).  Completion is detected with event queries on the host -- no kernel
 // ever waits -- and waits by clients are bounded condition-variable waits.
 // A request's chains are a pure function of its parameters (stateless Philox
 // keyed by seed, ensemble, chain and step), so its result does not depend on
 // what else is running.
+#include <math.h>
 #include <stdio.h>
 #include <string.h>
 #include <time.h>
@@ -47,6 +51,7 @@ struct Request {
     State state = QUEUED;
     int status = ROSEN_OK;
     char message[256] = "";
+    int level = 0;             // stream priority class (0: the least work)
     size_t work_bytes = 0;     // outputs + reduction workspace (freed at completion)
     size_t coord_bytes = 0;    // stored conformations (freed at release)
     void *work = nullptr;
@@ -72,7 +77,9 @@ struct rosen_server {
     std::deque<Request *> queue;
     std::vector<Request *> running;
     std::unordered_map<uint64_t, Request *> all;
-    std::vector<cudaStream_t> streams;
+    std::vector<std::vector<cudaStream_t>> streams;   // idle streams per priority class
+    int prio_greatest = 0;     // CUDA priority of class 0 (numerically lowest)
+    int levels = 1;
     std::vector<cudaEvent_t> events;
     std::vector<rosen_stats *> pinned;
     size_t used = 0;
@@ -128,6 +135,20 @@ void request_bytes(const rosen_request &r, size_t *work, size_t *coords)
     b += align256(rosen_reduce_workspace_size(r.C)) + align256(sizeof(rosen_stats));
     *work = b;
     *coords = r.store_coords ? align256(12 * N * C) : 0;
+}
+
+// Priority class of a request (shortest_first): decades of its pair tests
+// (chains x (N-1)(N-2)/2 x trials per step), class 0 -- the highest priority,
+// well under a millisecond of GPU time -- below 1e8, up to the last class.
+int work_level(const rosen_request &r, int levels)
+{
+    const double n = (double)r.N;
+    const double pairs = (double)r.C * (n - 1.0) * (n - 2.0) * 0.5 *
+                         (r.model == ROSEN_MODEL_LATTICE ? 1.0 : (double)r.k);
+    int level = pairs < 1.0 ? 0 : (int)floor(log10(pairs)) - 7;
+    if (level < 0) level = 0;
+    if (level > levels - 1) level = levels - 1;
+    return level;
 }
 
 int validate_request(const rosen_request &r)
@@ -332,7 +353,7 @@ void scheduler(rosen_server *s)
                 q->coords = nullptr;
                 s->used -= q->coord_bytes;
             }
-            s->streams.push_back(q->stream);
+            s->streams[q->level].push_back(q->stream);
             s->events.push_back(q->done);
             s->pinned.push_back(q->host_stats);
             q->stream = nullptr;
@@ -354,11 +375,23 @@ void scheduler(rosen_server *s)
             }
             const size_t need = q->work_bytes + q->coord_bytes;
             if (s->used + need > s->cfg.mem_budget_bytes) break;
+            // A stream of the request's priority class (created on first use;
+            // at most max_slots per class are ever in use).
+            std::vector<cudaStream_t> &idle = s->streams[q->level];
+            if (idle.empty()) {
+                cudaStream_t st;
+                if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking,
+                                                 s->prio_greatest + q->level) != cudaSuccess) {
+                    cudaGetLastError();
+                    break;   // the request stays queued; retried at the next pass
+                }
+                idle.push_back(st);
+            }
             s->queue.pop_front();
             q->in_queue = false;
             s->used += need;
-            q->stream = s->streams.back();
-            s->streams.pop_back();
+            q->stream = idle.back();
+            idle.pop_back();
             q->done = s->events.back();
             s->events.pop_back();
             q->host_stats = s->pinned.back();
@@ -402,9 +435,10 @@ void fill_result(const Request *q, rosen_result *out)
 extern "C" int rosen_serve_create(const rosen_serve_config *cfg, rosen_server **out)
 {
     if (!cfg || !out) return set_error(ROSEN_EINVAL, "rosen_serve_create: NULL argument");
-    if (cfg->max_slots < 1 || cfg->max_slots > 1024 || cfg->max_queue < 1 || cfg->mem_budget_bytes == 0)
-        return set_error(ROSEN_EINVAL, "rosen_serve_create: max_slots in [1, 1024], max_queue >= 1 "
-                                       "and a non-zero budget are required");
+    if (cfg->max_slots < 1 || cfg->max_slots > 1024 || cfg->max_queue < 1 ||
+        cfg->mem_budget_bytes == 0 || (cfg->shortest_first != 0 && cfg->shortest_first != 1))
+        return set_error(ROSEN_EINVAL, "rosen_serve_create: max_slots in [1, 1024], max_queue >= 1, "
+                                       "a non-zero budget and shortest_first 0 or 1 are required");
     rosen_server *s = new rosen_server();
     s->cfg = *cfg;
     s->device = cfg->device;
@@ -420,22 +454,25 @@ extern "C" int rosen_serve_create(const rosen_serve_config *cfg, rosen_server **
         e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->free_stream, cudaStreamNonBlocking);
+    int least = 0, greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    // Without shortest_first every stream has the default priority.
+    s->prio_greatest = cfg->shortest_first ? greatest : 0;
+    s->levels = cfg->shortest_first ? least - greatest + 1 : 1;
+    if (s->levels < 1) s->levels = 1;
+    s->streams.resize((size_t)s->levels);
     for (int i = 0; e == cudaSuccess && i < cfg->max_slots; ++i) {
-        cudaStream_t st;
         cudaEvent_t ev;
         rosen_stats *h;
-        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h), sizeof(rosen_stats));
         if (e == cudaSuccess) {
-            s->streams.push_back(st);
             s->events.push_back(ev);
             s->pinned.push_back(h);
         }
     }
     if (e != cudaSuccess) {
         if (s->free_stream) cudaStreamDestroy(s->free_stream);
-        for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
         for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
         for (rosen_stats *h : s->pinned) cudaFreeHost(h);
         if (s->pool) cudaMemPoolDestroy(s->pool);
@@ -455,6 +492,7 @@ extern "C" int rosen_serve_submit(rosen_server *s, const rosen_request *r, uint6
     Request *q = new Request();
     q->req = *r;
     request_bytes(*r, &q->work_bytes, &q->coord_bytes);
+    q->level = work_level(*r, s->levels);
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->stop) {
         delete q;
@@ -596,7 +634,8 @@ extern "C" int rosen_serve_destroy(rosen_server *s)
     for (auto &f : s->to_free) cudaFreeAsync(f.first, s->free_stream);
     cudaStreamSynchronize(s->free_stream);
     cudaStreamDestroy(s->free_stream);
-    for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+    for (auto &pool : s->streams)
+        for (cudaStream_t st : pool) cudaStreamDestroy(st);
     for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
     for (rosen_stats *h : s->pinned) cudaFreeHost(h);
     cudaMemPoolDestroy(s->pool);

@@ -472,7 +472,7 @@ class rosen_stats_t(ctypes.Structure):
 class rosen_serve_config(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
                 ("max_queue", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("shortest_first", ctypes.c_int32)]
 
 
 class rosen_request(ctypes.Structure):
@@ -536,9 +536,11 @@ def result_dict(r):
 class RosenServer:
     """The request loop (rosen_serve_*): submit, poll/wait, release."""
 
-    def __init__(self, mem_budget_bytes, max_slots=32, max_queue=4096, device=0):
+    def __init__(self, mem_budget_bytes, max_slots=32, max_queue=4096, device=0,
+                 shortest_first=False):
         cfg = rosen_serve_config(mem_budget_bytes=int(mem_budget_bytes), max_slots=int(max_slots),
-                                 max_queue=int(max_queue), device=int(device), reserved=0)
+                                 max_queue=int(max_queue), device=int(device),
+                                 shortest_first=int(bool(shortest_first)))
         h = _vp()
         _check(_serve_lib().rosen_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h

@@ -42,8 +42,11 @@ def mix(rosen):
     ]
 
 
-def test_alone_and_in_the_mix(rosen):
-    srv = rosen.RosenServer(mem_budget_bytes=8 << 30, max_slots=8)
+@pytest.mark.parametrize("shortest_first", [False, True])
+def test_alone_and_in_the_mix(rosen, shortest_first):
+    # With shortest_first the streams carry priorities by work; the results
+    # are the same either way.
+    srv = rosen.RosenServer(mem_budget_bytes=8 << 30, max_slots=8, shortest_first=shortest_first)
     alone = []
     for r in mix(rosen):
         t = srv.submit(r)
