@@ -51,6 +51,34 @@ __global__ void __launch_bounds__(256, 4) offlattice_group_kernel(const OffArgs 
     off_chain<G, T, LJ, ChainSmem, kDefer>(a, c, w, g, logm);
 }
 
+// The same growth with chains handed out one at a time: every group takes
+// its next chain from a counter as soon as it is done with the last, so a
+// block holds no lanes idle while its slowest chain finishes (chains differ
+// in their number of FP64 re-decisions and dead ends).  The grid is what the
+// GPU holds at once.
+template <int G, int T, bool LJ, bool kDefer = false>
+__global__ void __launch_bounds__(256, 4) offlattice_queue_kernel(const OffArgs a,
+                                                                  int chains_per_block,
+                                                                  unsigned long long *next)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *logm = reinterpret_cast<float *>(smem_raw);
+    fill_log_table(logm);
+    __syncthreads();
+
+    const Group<G> g;
+    const int cib = threadIdx.x / G;
+    const ChainSmem w = carve(smem_raw + kTable * sizeof(float) +
+                                  (size_t)cib * chain_smem_bytes(a.N, LJ), a.N, LJ);
+    for (;;) {
+        unsigned long long c = 0;
+        if (g.gl == 0) c = atomicAdd(next, 1ull);
+        c = g.bcast(c, 0);
+        if (c >= (unsigned long long)a.C) break;
+        off_chain<G, T, LJ, ChainSmem, kDefer>(a, (int64_t)c, w, g, logm);
+    }
+}
+
 // Second pass of two-pass growth: the chains whose bits the first pass set,
 // grown again from the start with the FP64 re-decision compiled in.  Warps
 // take 32-chain words of the bit mask from a counter (the word after the
@@ -159,14 +187,16 @@ int chains_per_block_for(int G, int N, bool lj)
     return chains;
 }
 
-// Hard spheres grow in two passes.  Their FP32 decisions are almost never
-// ambiguous (about 2% of N = 64, k = 32 chains meet one such step), but the
-// FP64 re-decision path, compiled into the growth kernel, costs every chain
-// registers and time (the kernel without it runs 11% faster).  So the first
-// pass has no FP64 path and defers the chains that need it; the second
-// regrows only those, with it.  Every chain's outputs are those of the
-// one-pass kernel, bit for bit.  The deferral mask (C/8 bytes) comes from the
-// stream-ordered allocator; if that fails, one pass with the FP64 path runs.
+// Single-ensemble growth.  Groups take chains from a counter
+// (offlattice_queue_kernel).  Hard spheres grow in two passes: their FP32
+// decisions are almost never ambiguous (about 2% of N = 64, k = 32 chains meet
+// one such step), but the FP64 re-decision path, compiled into the growth
+// kernel, costs every chain registers and time (the kernel without it runs
+// 11% faster).  So the first pass has no FP64 path and defers the chains that
+// need it; the second regrows only those, with it.  Every chain's outputs are
+// those of the one-pass kernel, bit for bit.  The counter and the deferral
+// mask (C/8 bytes) come from the stream-ordered allocator; if that fails, the
+// one-pass kernel runs with one block per chains_per_block chains.
 template <int G, int T, bool LJ>
 int launch_one(const OffArgs &a, int N, cudaStream_t s)
 {
@@ -174,42 +204,53 @@ int launch_one(const OffArgs &a, int N, cudaStream_t s)
     const size_t smem = kTable * sizeof(float) + (size_t)chains * chain_smem_bytes(N, LJ);
     const int threads = chains * G;
     const int64_t blocks = (a.C + chains - 1) / chains;
-    if constexpr (!LJ) {
-        // The mask, then the second pass's word counter.
-        const size_t mask_bytes = (size_t)((a.C + 31) / 32 + 1) * sizeof(uint32_t);
-        void *mask = nullptr;
-        if (cudaMallocAsync(&mask, mask_bytes, s) == cudaSuccess) {
-            OffArgs d = a;
-            d.deferred = static_cast<uint32_t *>(mask);
-            cudaError_t e = cudaMemsetAsync(mask, 0, mask_bytes, s);
-            int dev = 0, sms = 0, bps = 0;
-            if (e == cudaSuccess) e = allow_max_smem(offlattice_group_kernel<G, T, LJ, true>);
-            if (e == cudaSuccess) e = allow_max_smem(offlattice_deferred_kernel<G, T, LJ>);
-            if (e == cudaSuccess) e = cudaGetDevice(&dev);
-            if (e == cudaSuccess)
-                e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &bps, offlattice_deferred_kernel<G, T, LJ>, threads, smem);
-            if (e == cudaSuccess) {
-                offlattice_group_kernel<G, T, LJ, true><<<(unsigned)blocks, threads, smem, s>>>(
-                    d, chains);
-                const int64_t words = (a.C + 31) / 32;
-                int64_t grid = (int64_t)(bps > 0 ? bps : 1) * sms;
-                if (grid > (words + chains - 1) / chains) grid = (words + chains - 1) / chains;
-                offlattice_deferred_kernel<G, T, LJ><<<(unsigned)grid, threads, smem, s>>>(d, chains);
-                e = cudaGetLastError();
+    // Counter of the queue kernel, then (hard spheres) the deferral mask and
+    // the second pass's word counter.
+    const int64_t words = (a.C + 31) / 32;
+    const size_t bytes = sizeof(unsigned long long) +
+                         (LJ ? 0 : (size_t)(words + 1) * sizeof(uint32_t));
+    void *buf = nullptr;
+    if (cudaMallocAsync(&buf, bytes, s) == cudaSuccess) {
+        unsigned long long *next = static_cast<unsigned long long *>(buf);
+        OffArgs d = a;
+        if (!LJ) d.deferred = reinterpret_cast<uint32_t *>(next + 1);
+        constexpr bool kDefer = !LJ;
+        cudaError_t e = cudaMemsetAsync(buf, 0, bytes, s);
+        int dev = 0, sms = 0, bps = 0;
+        if (e == cudaSuccess) e = allow_max_smem(offlattice_queue_kernel<G, T, LJ, kDefer>);
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &bps, offlattice_queue_kernel<G, T, LJ, kDefer>, threads, smem);
+        if (e == cudaSuccess) {
+            int64_t grid = (int64_t)(bps > 0 ? bps : 1) * sms;
+            if (grid > blocks) grid = blocks;
+            offlattice_queue_kernel<G, T, LJ, kDefer><<<(unsigned)grid, threads, smem, s>>>(
+                d, chains, next);
+            if constexpr (!LJ) {
+                int bps2 = 0;
+                e = allow_max_smem(offlattice_deferred_kernel<G, T, LJ>);
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        &bps2, offlattice_deferred_kernel<G, T, LJ>, threads, smem);
+                int64_t grid2 = (int64_t)(bps2 > 0 ? bps2 : 1) * sms;
+                if (grid2 > (words + chains - 1) / chains) grid2 = (words + chains - 1) / chains;
+                if (e == cudaSuccess)
+                    offlattice_deferred_kernel<G, T, LJ><<<(unsigned)grid2, threads, smem, s>>>(
+                        d, chains);
             }
-            const cudaError_t f = cudaFreeAsync(mask, s);
-            if (e != cudaSuccess)
-                return set_error(ROSEN_ECUDA, "rosen_offlattice_grow: %s", cudaGetErrorString(e));
-            if (f != cudaSuccess)
-                return set_error(ROSEN_ECUDA, "rosen_offlattice_grow: freeing the deferral mask: %s",
-                                 cudaGetErrorString(f));
-            return ROSEN_OK;
+            if (e == cudaSuccess) e = cudaGetLastError();
         }
-        cudaGetLastError();   // clear the failed allocation; grow in one pass
+        const cudaError_t f = cudaFreeAsync(buf, s);
+        if (e != cudaSuccess)
+            return set_error(ROSEN_ECUDA, "rosen_offlattice_grow: %s", cudaGetErrorString(e));
+        if (f != cudaSuccess)
+            return set_error(ROSEN_ECUDA, "rosen_offlattice_grow: freeing the work counter: %s",
+                             cudaGetErrorString(f));
+        return ROSEN_OK;
     }
+    cudaGetLastError();   // clear the failed allocation; grow in one pass
     allow_max_smem(offlattice_group_kernel<G, T, LJ>);
     offlattice_group_kernel<G, T, LJ><<<(unsigned)blocks, threads, smem, s>>>(a, chains);
     return check_launch("rosen_offlattice_grow");
