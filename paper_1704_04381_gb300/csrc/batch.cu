@@ -218,6 +218,10 @@ int shape_class(rosen_batch *b, ClassPlan &c)
 
 int upload_items(ClassPlan &c, const std::vector<BatchItem> &items)
 {
+    // Real-space classes hand out chains by a 32-bit ticket counter.
+    if (!c.lattice && (uint64_t)items.size() * (uint64_t)c.cpb >= (uint64_t(1) << 31))
+        return set_error(ROSEN_EINVAL, "rosen_batch: a real-space class of more than 2^31 chains; "
+                                       "split the ensembles over several batches");
     if (c.d_items) cudaFree(c.d_items);
     c.d_items = nullptr;
     c.n_items = (int)items.size();

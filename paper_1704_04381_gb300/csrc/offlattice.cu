@@ -117,9 +117,13 @@ __global__ void __launch_bounds__(256, 4) offlattice_deferred_kernel(const OffAr
     }
 }
 
-// Persistent batch kernel for one (G, T, potential) class: blocks take
-// (ensemble, chain range) items from a queue sorted by decreasing cost; every
-// chain is grown by the same off_chain code as in the single-ensemble kernel.
+// Persistent batch kernel for one (G, T, potential) class.  The queue holds
+// (ensemble, chain range) items of up to chains_per_block chains, sorted by
+// decreasing cost; ticket t of a counter is chain t % chains_per_block of
+// item t / chains_per_block.  Every group takes its own tickets, keeps the
+// arguments of its current ensemble in shared memory, and grows each chain
+// with the same off_chain code as the single-ensemble kernels -- no group
+// waits for the others of its block.
 template <int G, int T, bool LJ>
 __global__ void __launch_bounds__(256, 4) offlattice_batch_kernel(const OffArgs *__restrict__ ens,
                                                                   const BatchItem *__restrict__ items,
@@ -127,26 +131,35 @@ __global__ void __launch_bounds__(256, 4) offlattice_batch_kernel(const OffArgs 
                                                                   int chains_per_block, int Nmax)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ OffArgs sa;
-    __shared__ int s_item;
+    __shared__ OffArgs sa[256 / G];
     float *logm = reinterpret_cast<float *>(smem_raw);
     fill_log_table(logm);
+    __syncthreads();
     const Group<G> g;
     const int cib = threadIdx.x / G;
     const ChainSmem w = carve(smem_raw + kTable * sizeof(float) +
                                   (size_t)cib * chain_smem_bytes(Nmax, LJ), Nmax, LJ);
+    OffArgs &my = sa[cib];
+    const unsigned int tickets = (unsigned int)n_items * (unsigned int)chains_per_block;
+    unsigned int *next = reinterpret_cast<unsigned int *>(head);
+    int cur = -1;     // the ensemble whose arguments are in my
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(head, 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= n_items) break;
-        const BatchItem bi = items[it];
-        constexpr int kWords = (int)(sizeof(OffArgs) / 4);
-        for (int q = threadIdx.x; q < kWords; q += blockDim.x)
-            reinterpret_cast<uint32_t *>(&sa)[q] = reinterpret_cast<const uint32_t *>(&ens[bi.ens])[q];
-        __syncthreads();
-        if (cib < (int)bi.n) off_chain<G, T, LJ, ChainSmem, false, true>(sa, bi.c0 + cib, w, g, logm);
-        __syncthreads();
+        unsigned int t = 0;
+        if (g.gl == 0) t = atomicAdd(next, 1u);
+        t = g.bcast(t, 0);
+        if (t >= tickets) break;
+        const BatchItem bi = items[t / (unsigned int)chains_per_block];
+        const unsigned int off = t % (unsigned int)chains_per_block;
+        if (off >= bi.n) continue;
+        if ((int)bi.ens != cur) {
+            constexpr int kWords = (int)(sizeof(OffArgs) / 4);
+            for (int q = g.gl; q < kWords; q += G)
+                reinterpret_cast<uint32_t *>(&my)[q] =
+                    reinterpret_cast<const uint32_t *>(&ens[bi.ens])[q];
+            __syncwarp(g.mask);
+            cur = (int)bi.ens;
+        }
+        off_chain<G, T, LJ, ChainSmem, false, true>(my, bi.c0 + off, w, g, logm);
     }
 }
 
