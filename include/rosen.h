@@ -152,15 +152,18 @@ ROSEN_API int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_latt
  * `workspace`, one 16-byte entry (key and occupancy bitmap) per 4x4x4 block
  * of sites, so a step costs a few block lookups, not a scan of the chain.  A
  * lane owns one table of 16 * 2^ceil(log2(max(N + 1, 64))) bytes and grows
- * its chains one after another.  The call grows min(C, workspace_bytes /
- * table) chains at a time, so a smaller workspace means fewer chains in
- * flight and no other change.
- * workspace: caller-owned device memory, 16-byte aligned; the call zeroes the
- * part it uses on the stream first, so its contents need not be kept between
- * calls.  rosen_lattice_long_workspace_size gives the size for
- * min(C, 131072) tables in flight.
+ * chains one after another, taking the next from a counter as soon as it is
+ * done.  The call grows min(C, (workspace_bytes - 256) / table) chains at a
+ * time, so a smaller workspace means fewer chains in flight and no other
+ * change.
+ * workspace: caller-owned device memory, 16-byte aligned: a 256-byte header
+ * (the chain counter), then the tables; the call zeroes the part it uses on
+ * the stream first, so its contents need not be kept between calls.
+ * rosen_lattice_long_workspace_size gives the size for min(C, 131072)
+ * tables in flight.
  * Errors: those of rosen_lattice_grow with N <= 32768; EINVAL for a NULL or
- * misaligned workspace; ENOMEM if workspace_bytes is below one table.
+ * misaligned workspace; ENOMEM if the workspace holds no table after the
+ * header.
  */
 ROSEN_API size_t rosen_lattice_long_workspace_size(int32_t N, int64_t C);
 ROSEN_API int rosen_lattice_grow_long(const rosen_lattice_params *p, const rosen_lattice_out *o,
@@ -236,9 +239,10 @@ ROSEN_API int rosen_offlattice_grow(const rosen_offlattice_params *p,
  * cells around the end instead of every earlier bead.  The near list is put
  * in bead order, so a chain's arithmetic is that of rosen_offlattice_grow
  * with the same lanes per chain, and its outputs are identical.
- * As many chains are grown at once as the workspace holds slots of
- * (rosen_offlattice_long_workspace_size(N, 1)) bytes, at most as many as are
- * resident on the GPU.
+ * As many chains are grown at once as the workspace holds slots
+ * (rosen_offlattice_long_workspace_size(N, 1) - 256 bytes each) after its
+ * 256-byte header, at most as many as are resident on the GPU; a slot takes
+ * its next chain from a counter in the header as soon as it is done.
  * workspace: caller-owned device memory, 16-byte aligned; the call zeroes
  * the part it uses on the stream first.  rosen_offlattice_long_workspace_size
  * gives the size for min(C, 9728) slots.

@@ -677,11 +677,13 @@ __device__ __forceinline__ bool long_attempt(const LatticeArgs &a, int64_t c, ui
     return false;
 }
 
-// One lane per chain at a time; lane l grows chains l, l + lanes, ... in its
-// own table (2^logH entries at ws + l 2^logH).
+// One lane per chain at a time, in its own table (2^logH entries at
+// ws + l 2^logH for lane l); each lane takes its next chain from the counter
+// *next as soon as it is done, so lanes whose chains die early take more.
 template <bool kIsaw>
 __global__ void __launch_bounds__(256) lattice_long_kernel(const LatticeArgs a, ulonglong2 *ws,
-                                                           int64_t lanes, int logH)
+                                                           int64_t lanes, int logH,
+                                                           unsigned long long *next)
 {
     __shared__ uint8_t seltab[kSelBytes];
     __shared__ float wt32[8];
@@ -697,9 +699,11 @@ __global__ void __launch_bounds__(256) lattice_long_kernel(const LatticeArgs a, 
     if (lane >= lanes) return;
     ulonglong2 *tab = ws + (lane << logH);
     uint32_t gen = 0;
-    for (int64_t c = lane; c < a.C; c += lanes) {
+    for (;;) {
+        const unsigned long long c = atomicAdd(next, 1ull);
+        if (c >= (unsigned long long)a.C) break;
         uint32_t att = 0;
-        while (long_attempt<kIsaw>(a, c, att, tab, logH, gen, seltab, wt32, wt64)) ++att;
+        while (long_attempt<kIsaw>(a, (int64_t)c, att, tab, logH, gen, seltab, wt32, wt64)) ++att;
     }
 }
 
@@ -851,6 +855,7 @@ extern "C" int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lat
 namespace {
 
 constexpr int64_t kLongLanes = 1 << 17;   // tables the default workspace holds
+constexpr size_t kLongHeader = 256;       // the chain counter, at the head of the workspace
 
 // log2 of the table entries per lane: more than N (a chain fills at most N
 // blocks) and at least 64.
@@ -867,7 +872,7 @@ extern "C" size_t rosen_lattice_long_workspace_size(int32_t N, int64_t C)
 {
     if (N < 2 || N > ROSEN_LATTICE_LONG_NMAX || C < 1) return 0;
     const int64_t lanes = C < kLongLanes ? C : kLongLanes;
-    return (size_t)lanes * (sizeof(ulonglong2) << long_log_entries(N));
+    return kLongHeader + (size_t)lanes * (sizeof(ulonglong2) << long_log_entries(N));
 }
 
 extern "C" int rosen_lattice_grow_long(const rosen_lattice_params *p, const rosen_lattice_out *o,
@@ -881,23 +886,27 @@ extern "C" int rosen_lattice_grow_long(const rosen_lattice_params *p, const rose
                                        "16-byte aligned device pointer");
     const int logH = long_log_entries(p->N);
     const size_t table = sizeof(ulonglong2) << logH;
-    int64_t lanes = (int64_t)(workspace_bytes / table);
+    int64_t lanes = workspace_bytes > kLongHeader
+                        ? (int64_t)((workspace_bytes - kLongHeader) / table) : 0;
     if (lanes > p->C) lanes = p->C;
     if (lanes < 1)
         return set_error(ROSEN_ENOMEM,
                          "rosen_lattice_grow_long: workspace of %zu bytes holds no table of %zu "
-                         "bytes (N = %d)", workspace_bytes, table, p->N);
+                         "bytes after its %zu-byte header (N = %d)", workspace_bytes, table,
+                         kLongHeader, p->N);
     LatticeArgs a;
     lattice_make_args(p, o, &a);
     cudaStream_t s = (cudaStream_t)stream;
-    const cudaError_t e = cudaMemsetAsync(workspace, 0, (size_t)lanes * table, s);
+    const cudaError_t e = cudaMemsetAsync(workspace, 0, kLongHeader + (size_t)lanes * table, s);
     if (e != cudaSuccess)
         return set_error(ROSEN_ECUDA, "rosen_lattice_grow_long: clearing %lld tables of %zu bytes: %s",
                          (long long)lanes, table, cudaGetErrorString(e));
     const unsigned grid = (unsigned)((lanes + 255) / 256);
-    ulonglong2 *ws = static_cast<ulonglong2 *>(workspace);
-    if (a.isaw) lattice_long_kernel<true><<<grid, 256, 0, s>>>(a, ws, lanes, logH);
-    else lattice_long_kernel<false><<<grid, 256, 0, s>>>(a, ws, lanes, logH);
+    unsigned long long *next = static_cast<unsigned long long *>(workspace);
+    ulonglong2 *ws = reinterpret_cast<ulonglong2 *>(static_cast<unsigned char *>(workspace) +
+                                                    kLongHeader);
+    if (a.isaw) lattice_long_kernel<true><<<grid, 256, 0, s>>>(a, ws, lanes, logH, next);
+    else lattice_long_kernel<false><<<grid, 256, 0, s>>>(a, ws, lanes, logH, next);
     return check_launch("rosen_lattice_grow_long (kernel launch)");
 }
 

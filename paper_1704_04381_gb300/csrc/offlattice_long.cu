@@ -22,6 +22,7 @@ namespace rosen {
 namespace {
 
 constexpr int64_t kLongSlots = 9728;   // default slots: 152 SMs x 1024 threads / 16 lanes
+constexpr size_t kLongHeader = 256;    // the chain counter, at the head of the workspace
 
 __host__ __device__ inline size_t r16(size_t x) { return (x + 15) & ~size_t(15); }
 
@@ -63,10 +64,14 @@ __device__ ChainLong carve_long(unsigned char *base, int N, int logH, float inv_
     return w;
 }
 
+// Each slot grows one chain at a time and takes its next chain from the
+// counter *next as soon as it is done, so slots whose chains die early (most
+// long hard-sphere chains) take more.
 template <int G, int T, bool LJ>
 __global__ void __launch_bounds__(256, 4) offlattice_long_kernel(const OffArgs a, unsigned char *ws,
                                                                  int64_t slots, size_t slot_bytes,
-                                                                 int logH, float inv_cell, float pre2)
+                                                                 int logH, float inv_cell, float pre2,
+                                                                 unsigned long long *next)
 {
     __shared__ float logm[kTable];
     fill_log_table(logm);
@@ -76,7 +81,13 @@ __global__ void __launch_bounds__(256, 4) offlattice_long_kernel(const OffArgs a
     if (slot >= slots) return;     // whole groups leave together
     const ChainLong w = carve_long(ws + slot * slot_bytes, a.N, logH, inv_cell, pre2);
     uint32_t gen = 0;
-    for (int64_t c = slot; c < a.C; c += slots) off_chain<G, T, LJ>(a, c, w, g, logm, &gen);
+    for (;;) {
+        unsigned long long c = 0;
+        if (g.gl == 0) c = atomicAdd(next, 1ull);
+        c = g.bcast(c, 0);
+        if (c >= (unsigned long long)a.C) break;
+        off_chain<G, T, LJ>(a, (int64_t)c, w, g, logm, &gen);
+    }
 }
 
 template <int G, int T, bool LJ>
@@ -92,20 +103,22 @@ int launch_long(const OffArgs &a, unsigned char *ws, size_t bytes, int logH, flo
         return set_error(ROSEN_ECUDA, "rosen_offlattice_grow_long: device query: %s",
                          cudaGetErrorString(e));
     const size_t slot_bytes = long_slot_bytes(a.N, logH);
-    int64_t slots = (int64_t)(bytes / slot_bytes);
+    int64_t slots = bytes > kLongHeader ? (int64_t)((bytes - kLongHeader) / slot_bytes) : 0;
     const int64_t resident = (int64_t)(bps > 0 ? bps : 1) * sms * (256 / G);
     if (slots > resident) slots = resident;
     if (slots > a.C) slots = a.C;
     if (slots < 1)
         return set_error(ROSEN_ENOMEM,
                          "rosen_offlattice_grow_long: workspace of %zu bytes holds no chain slot "
-                         "of %zu bytes (N = %d)", bytes, slot_bytes, a.N);
-    e = cudaMemsetAsync(ws, 0, (size_t)slots * slot_bytes, s);
+                         "of %zu bytes after its %zu-byte header (N = %d)", bytes, slot_bytes,
+                         kLongHeader, a.N);
+    e = cudaMemsetAsync(ws, 0, kLongHeader + (size_t)slots * slot_bytes, s);
     if (e != cudaSuccess)
         return set_error(ROSEN_ECUDA, "rosen_offlattice_grow_long: clearing %lld slots of %zu bytes: %s",
                          (long long)slots, slot_bytes, cudaGetErrorString(e));
     const int64_t grid = (slots * G + 255) / 256;
-    kern<<<(unsigned)grid, 256, 0, s>>>(a, ws, slots, slot_bytes, logH, inv_cell, pre2);
+    kern<<<(unsigned)grid, 256, 0, s>>>(a, ws + kLongHeader, slots, slot_bytes, logH, inv_cell, pre2,
+                                       reinterpret_cast<unsigned long long *>(ws));
     return check_launch("rosen_offlattice_grow_long (kernel launch)");
 }
 
@@ -128,7 +141,7 @@ extern "C" size_t rosen_offlattice_long_workspace_size(int32_t N, int64_t C)
 {
     if (N < 2 || N > ROSEN_OFFLATTICE_LONG_NMAX || C < 1) return 0;
     const int64_t slots = C < kLongSlots ? C : kLongSlots;
-    return (size_t)slots * long_slot_bytes(N, long_log_cells(N));
+    return kLongHeader + (size_t)slots * long_slot_bytes(N, long_log_cells(N));
 }
 
 extern "C" int rosen_offlattice_grow_long(const rosen_offlattice_params *p,

@@ -106,9 +106,10 @@ def test_long_lattice_validation(rosen):
     assert rosen.rosen_lattice_long_workspace_size(1, 10) == 0
     assert rosen.rosen_lattice_long_workspace_size(32769, 10) == 0
     assert rosen.rosen_lattice_long_workspace_size(1000, 0) == 0
-    # N + 1 = 1001 -> 1024 entries of 16 bytes per table; min(C, 131072) tables.
-    assert rosen.rosen_lattice_long_workspace_size(1000, 10) == 10 * 1024 * 16
-    assert rosen.rosen_lattice_long_workspace_size(2, 10 ** 9) == (1 << 17) * 64 * 16
+    # A 256-byte header (the chain counter), then min(C, 131072) tables;
+    # N + 1 = 1001 -> 1024 entries of 16 bytes per table.
+    assert rosen.rosen_lattice_long_workspace_size(1000, 10) == 256 + 10 * 1024 * 16
+    assert rosen.rosen_lattice_long_workspace_size(2, 10 ** 9) == 256 + (1 << 17) * 64 * 16
 
     def grow_long(ws, nbytes, **kw):
         p = rosen.lattice_params(**{**dict(seed=1, N=1000, C=10), **kw})
@@ -131,10 +132,11 @@ def test_long_offlattice_validation(rosen):
     assert rosen.rosen_offlattice_long_workspace_size(1, 10) == 0
     assert rosen.rosen_offlattice_long_workspace_size(16385, 10) == 0
     assert rosen.rosen_offlattice_long_workspace_size(1000, 0) == 0
-    one = rosen.rosen_offlattice_long_workspace_size(1000, 1)
-    assert one % 16 == 0 and one > 1000 * 4 * 16
-    assert rosen.rosen_offlattice_long_workspace_size(1000, 10) == 10 * one
-    assert rosen.rosen_offlattice_long_workspace_size(1000, 10 ** 9) == 9728 * one
+    # A 256-byte header (the chain counter), then min(C, 9728) slots.
+    slot = rosen.rosen_offlattice_long_workspace_size(1000, 1) - 256
+    assert slot % 16 == 0 and slot > 1000 * 4 * 16
+    assert rosen.rosen_offlattice_long_workspace_size(1000, 10) == 256 + 10 * slot
+    assert rosen.rosen_offlattice_long_workspace_size(1000, 10 ** 9) == 256 + 9728 * slot
 
     def grow_long(ws, nbytes, **kw):
         p = rosen.offlattice_params(**{**dict(seed=1, N=1000, C=10, k=32), **kw})
