@@ -201,15 +201,18 @@ int chains_per_block_for(int G, int N, bool lj)
 }
 
 // Single-ensemble growth.  Groups take chains from a counter
-// (offlattice_queue_kernel).  Hard spheres grow in two passes: their FP32
-// decisions are almost never ambiguous (about 2% of N = 64, k = 32 chains meet
-// one such step), but the FP64 re-decision path, compiled into the growth
-// kernel, costs every chain registers and time (the kernel without it runs
-// 11% faster).  So the first pass has no FP64 path and defers the chains that
-// need it; the second regrows only those, with it.  Every chain's outputs are
-// those of the one-pass kernel, bit for bit.  The counter and the deferral
-// mask (C/8 bytes) come from the stream-ordered allocator; if that fails, the
-// one-pass kernel runs with one block per chains_per_block chains.
+// (offlattice_queue_kernel).  Short hard-sphere chains (N <= 128) grow in two
+// passes: their FP32 decisions are almost never ambiguous (about 2% of
+// N = 64, k = 32 chains meet one such step), but the FP64 re-decision path,
+// compiled into the growth kernel, costs every chain registers and time (the
+// kernel without it runs 11% faster).  So the first pass has no FP64 path and
+// defers the chains that need it; the second regrows only those, with it.
+// Longer chains meet ambiguous steps more often (a third of N = 512 chains),
+// and regrowing them costs more than the first pass saves, so they grow in
+// one pass.  Every chain's outputs are those of the one-pass kernel, bit for
+// bit.  The counter and the deferral mask (C/8 bytes) come from the
+// stream-ordered allocator; if that fails, the one-pass kernel runs with one
+// block per chains_per_block chains.
 template <int G, int T, bool LJ>
 int launch_one(const OffArgs &a, int N, cudaStream_t s)
 {
@@ -220,38 +223,42 @@ int launch_one(const OffArgs &a, int N, cudaStream_t s)
     // Counter of the queue kernel, then (hard spheres) the deferral mask and
     // the second pass's word counter.
     const int64_t words = (a.C + 31) / 32;
+    const bool two_pass = !LJ && N <= 128;
     const size_t bytes = sizeof(unsigned long long) +
-                         (LJ ? 0 : (size_t)(words + 1) * sizeof(uint32_t));
+                         (two_pass ? (size_t)(words + 1) * sizeof(uint32_t) : 0);
     void *buf = nullptr;
     if (cudaMallocAsync(&buf, bytes, s) == cudaSuccess) {
         unsigned long long *next = static_cast<unsigned long long *>(buf);
         OffArgs d = a;
-        if (!LJ) d.deferred = reinterpret_cast<uint32_t *>(next + 1);
-        constexpr bool kDefer = !LJ;
+        if (two_pass) d.deferred = reinterpret_cast<uint32_t *>(next + 1);
         cudaError_t e = cudaMemsetAsync(buf, 0, bytes, s);
         int dev = 0, sms = 0, bps = 0;
-        if (e == cudaSuccess) e = allow_max_smem(offlattice_queue_kernel<G, T, LJ, kDefer>);
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // The first pass without the FP64 path, or the one pass with it.
+        auto first = two_pass ? offlattice_queue_kernel<G, T, LJ, !LJ>
+                              : offlattice_queue_kernel<G, T, LJ, false>;
+        if (e == cudaSuccess) e = allow_max_smem(first);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &bps, offlattice_queue_kernel<G, T, LJ, kDefer>, threads, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, first, threads, smem);
         if (e == cudaSuccess) {
             int64_t grid = (int64_t)(bps > 0 ? bps : 1) * sms;
             if (grid > blocks) grid = blocks;
-            offlattice_queue_kernel<G, T, LJ, kDefer><<<(unsigned)grid, threads, smem, s>>>(
-                d, chains, next);
+            first<<<(unsigned)grid, threads, smem, s>>>(d, chains, next);
             if constexpr (!LJ) {
-                int bps2 = 0;
-                e = allow_max_smem(offlattice_deferred_kernel<G, T, LJ>);
-                if (e == cudaSuccess)
-                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        &bps2, offlattice_deferred_kernel<G, T, LJ>, threads, smem);
-                int64_t grid2 = (int64_t)(bps2 > 0 ? bps2 : 1) * sms;
-                if (grid2 > (words + chains - 1) / chains) grid2 = (words + chains - 1) / chains;
-                if (e == cudaSuccess)
-                    offlattice_deferred_kernel<G, T, LJ><<<(unsigned)grid2, threads, smem, s>>>(
-                        d, chains);
+                if (two_pass) {
+                    int bps2 = 0;
+                    e = allow_max_smem(offlattice_deferred_kernel<G, T, LJ>);
+                    if (e == cudaSuccess)
+                        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &bps2, offlattice_deferred_kernel<G, T, LJ>, threads, smem);
+                    int64_t grid2 = (int64_t)(bps2 > 0 ? bps2 : 1) * sms;
+                    if (grid2 > (words + chains - 1) / chains)
+                        grid2 = (words + chains - 1) / chains;
+                    if (e == cudaSuccess)
+                        offlattice_deferred_kernel<G, T, LJ>
+                            <<<(unsigned)grid2, threads, smem, s>>>(d, chains);
+                }
             }
             if (e == cudaSuccess) e = cudaGetLastError();
         }
