@@ -299,9 +299,9 @@ def run_ours(args):
             sops = brute_offlattice_ops(N, K_TRIALS) * C
             part.update({"fp64_redecided_steps": cnt[0] / reps,
                          "listed_beads_per_step": listed / (C * (N - 1))})
-            kname = ("offlattice_group_kernel<16,2,hard sphere> + offlattice_deferred_kernel"
+            kname = ("offlattice_queue_kernel<16,2,hard sphere,defer> + offlattice_deferred_kernel"
                      if REAL_POT == "hard_sphere"
-                     else "offlattice_group_kernel<LJ, k=%d, beta eps %g>" % (K_TRIALS, REAL_BETA))
+                     else "offlattice_queue_kernel<LJ, k=%d, beta eps %g>" % (K_TRIALS, REAL_BETA))
         part["ops_per_chain"] = ops / C
         part["brute_ops_per_chain"] = sops / C
         # Brute-force pair tests per second (every earlier monomer against

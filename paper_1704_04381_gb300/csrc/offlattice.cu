@@ -34,7 +34,7 @@ namespace rosen {
 namespace {
 
 
-template <int G, int T, bool LJ, bool kDefer = false>
+template <int G, int T, bool LJ>
 __global__ void __launch_bounds__(256, 4) offlattice_group_kernel(const OffArgs a, int chains_per_block)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(256, 4) offlattice_group_kernel(const OffArgs 
     if (c >= a.C) return;     // whole groups leave together
     const ChainSmem w = carve(smem_raw + kTable * sizeof(float) +
                                   (size_t)cib * chain_smem_bytes(a.N, LJ), a.N, LJ);
-    off_chain<G, T, LJ, ChainSmem, kDefer>(a, c, w, g, logm);
+    off_chain<G, T, LJ>(a, c, w, g, logm);
 }
 
 // The same growth with chains handed out one at a time: every group takes
