@@ -383,7 +383,8 @@ def measure_e2e(args, rosen, torch, dev, stream, chain0, ens):
     """The same metric through the C ABI with host buffers: per step the
     per-chain results (log W, R^2, R_g^2) and the statistics of every ensemble
     are copied back to pinned host memory; the only host-to-device input is
-    the parameter block of each call."""
+    the parameter block of each call.  Each ensemble's copies run on a second
+    stream, after its reduction, while the next ensemble grows."""
     host = []
     d2h = 0
     for it in ens.items:
@@ -394,13 +395,19 @@ def measure_e2e(args, rosen, torch, dev, stream, chain0, ens):
         d2h += sum(v.numel() * v.element_size() for v in h.values()) + hs.numel() * 8
     h2d = sum(ctypes.sizeof(it["params"]) for it in ens.items)
 
+    copier = torch.cuda.Stream(device=dev)
+
     def step():
         for it, (h, hs) in zip(ens.items, host):
             ens.grow(it, stream)
             ens.reduce(it, stream)
-            for k in h:
-                h[k].copy_(it["out"][k], non_blocking=True)
-            hs.copy_(it["stats"], non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(stream)
+            copier.wait_event(done)
+            with torch.cuda.stream(copier):
+                for k in h:
+                    h[k].copy_(it["out"][k], non_blocking=True)
+                hs.copy_(it["stats"], non_blocking=True)
         torch.cuda.synchronize()
 
     for _ in range(max(1, min(args.warmup, 2))):
