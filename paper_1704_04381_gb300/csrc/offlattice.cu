@@ -23,6 +23,11 @@
 // its chosen trials, stores them back (so later steps start from exact
 // positions), and re-decides the step with the sequential FP64 arithmetic of
 // the definition.  The grown path is the one an FP64 implementation takes.
+//
+// Scheduling: the grid is what the GPU holds at once, and every group takes
+// its next chain from a counter (chains differ in cost by their re-decisions
+// and dead ends).  Short hard-sphere chains grow in two passes, the second
+// regrowing, with the FP64 path, the few chains the first could not decide.
 #include <math.h>
 #include <string.h>
 
