@@ -541,7 +541,7 @@ int create(rosen_batch *b, const rosen_ensemble *ens, int n)
             c.B = 128;
             while (c.B > 32 && lattice_smem_bytes(c.Nmax, c.B) > 200 * 1024) c.B /= 2;
         } else {
-            c.G = offlattice_default_lanes(c.k, c.lj);
+            c.G = offlattice_default_lanes(c.k, c.lj, c.Nmax);
         }
         int st = shape_class(b, c);
         if (st != ROSEN_OK) return st;

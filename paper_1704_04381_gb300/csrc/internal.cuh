@@ -23,7 +23,7 @@ int offlattice_validate(const rosen_offlattice_params *p, const rosen_offlattice
 size_t offlattice_args_size();
 void offlattice_make_args(const rosen_offlattice_params *p, const rosen_offlattice_out *o,
                           unsigned long long *counters, void *out);
-int offlattice_default_lanes(int k, bool lj);
+int offlattice_default_lanes(int k, bool lj, int N = 0);
 int offlattice_batch_prepare(int G, int T, bool lj, int Nmax, int *chains_per_block, size_t *smem,
                              int *blocks_per_sm);
 void offlattice_batch_launch(int G, int T, bool lj, const void *dev_args, const BatchItem *items,

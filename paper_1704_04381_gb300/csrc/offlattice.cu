@@ -363,11 +363,18 @@ int offlattice_validate(const rosen_offlattice_params *p, const rosen_offlattice
     return ROSEN_OK;
 }
 
-// Default lanes per chain (measured on GB300, N = 64): hard spheres run best
-// with two chains per warp (16 lanes), Lennard-Jones -- whose pair work is
-// several times heavier -- with a whole warp per chain once k > 16.
-int offlattice_default_lanes(int k, bool lj)
+// Default lanes per chain for the shared-memory kernels (measured on GB300):
+// at N = 64 hard spheres run best with two chains per warp (16 lanes) and
+// Lennard-Jones -- whose pair work is several times heavier -- with a whole
+// warp per chain once k > 16.  Longer chains spend more of each step in the
+// scan of earlier beads, which a whole warp does twice as fast: from N = 100
+// every k takes 32 lanes (N = 128 / 256, hard spheres k = 32: 11.4 / 17.2 ms
+// with 32 lanes against 13.7 / 38.0 ms with 16; LJ k = 16: 25.9 / 46.0
+// against 29.3 / 71.8 ms).  N = 0: the chain length is not known (the
+// long-chain kernel, whose near lists come from cells).
+int offlattice_default_lanes(int k, bool lj, int N)
 {
+    if (N >= 100) return 32;
     if (lj) return k <= 16 ? 16 : 32;
     if (k <= 64) return 16;
     return 32;
@@ -425,7 +432,8 @@ int offlattice_launch(const rosen_offlattice_params *p, const rosen_offlattice_o
     OffArgs a;
     offlattice_make_args(p, o, counters, &a);
     const bool lj = p->potential == ROSEN_LJ;
-    const int G = p->lanes_per_chain ? p->lanes_per_chain : offlattice_default_lanes(p->k, lj);
+    const int G =
+        p->lanes_per_chain ? p->lanes_per_chain : offlattice_default_lanes(p->k, lj, p->N);
     return lj ? launch_lj<true>(a, G, p->N, p->k, s) : launch_lj<false>(a, G, p->N, p->k, s);
 }
 
