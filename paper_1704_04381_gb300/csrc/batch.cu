@@ -268,7 +268,16 @@ int tune_class(rosen_batch *b, ClassPlan &c)
         for (int G : {8, 16, 32})
             if ((c.k + G - 1) / G <= 4) cands.push_back(G);
     }
-    double best = 1e300;
+    // The untuned default shape is kept unless another is clearly faster on
+    // the sample (which, for small classes, holds few chains per group).
+    int def = 0;
+    if (c.lattice) {
+        def = 128;
+        while (def > 32 && lattice_smem_bytes(c.Nmax, def) > 200 * 1024) def /= 2;
+    } else {
+        def = offlattice_default_lanes(c.k, c.lj, c.Nmax);
+    }
+    double best = 1e300, def_per = 1e300;
     int best_cand = cands.empty() ? 0 : cands[0];
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -295,6 +304,7 @@ int tune_class(rosen_batch *b, ClassPlan &c)
             CK(cudaEventElapsedTime(&ms, e0, e1));
         }
         const double per = ms / std::max(work, 1.0);
+        if (cand == def) def_per = per;
         if (per < best) {
             best = per;
             best_cand = cand;
@@ -302,6 +312,10 @@ int tune_class(rosen_batch *b, ClassPlan &c)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (def_per < 1e300 && best > 0.9 * def_per) {
+        best_cand = def;
+        best = def_per;
+    }
     if (c.lattice) c.B = best_cand;
     else c.G = best_cand;
     c.tuned_ms_per_work = best;
