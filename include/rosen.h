@@ -222,6 +222,12 @@ typedef struct rosen_offlattice_out {
  * Coordinates are FP32 (float-float sums); decisions that FP32 rounding
  * could flip are re-taken in FP64, so the path equals that of an FP64
  * implementation of the same rule.
+ * Scratch: the call takes 8 bytes (plus, for hard spheres with N <= 128, a
+ * bit per chain) from the device's stream-ordered allocator on `stream` and
+ * frees it there: a chain counter for the persistent grid and the mask of
+ * chains deferred to the FP64 second pass.  If that allocation fails, the
+ * chains grow in one pass with one block per few chains; the results are
+ * the same bit for bit.
  * Errors: EINVAL for N outside [2, 1024], k outside [1, 128], bad chain
  * range, unknown potential, sigma/cutoff/beta_eps out of range, unknown
  * flags or lanes_per_chain, max_attempts outside [0, ROSEN_MAX_ATTEMPTS].
