@@ -337,7 +337,7 @@ def run_ours(args):
         n16 = {"workload": "lattice athermal N=16, 1e5 chains, seed 1", "ms": ms16,
                "insertions_per_s": 100_000 * 15 / (ms16 / 1e3),
                "logZ": rosen.stats_dict(s16)["logZ"]}
-    e2e = None if args.no_e2e else measure_e2e(args, rosen, torch, dev, stream, chain0, ens)
+    e2e = None if args.no_e2e else measure_e2e(args, rosen, torch, dev, stream, chain0, ens, world)
     if world > 1:
         dist.destroy_process_group()
     if rank != 0:
@@ -379,7 +379,7 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
-def measure_e2e(args, rosen, torch, dev, stream, chain0, ens):
+def measure_e2e(args, rosen, torch, dev, stream, chain0, ens, world=1):
     """The same metric through the C ABI with host buffers: per step the
     per-chain results (log W, R^2, R_g^2) and the statistics of every ensemble
     are copied back to pinned host memory; the only host-to-device input is
@@ -413,11 +413,18 @@ def measure_e2e(args, rosen, torch, dev, stream, chain0, ens):
     for _ in range(max(1, min(args.warmup, 2))):
         step()
     steps = max(1, min(args.steps, 5))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(steps):
         step()
     dt = (time.perf_counter() - t0) / steps
-    return {"value": len(ens.items) * C * (N - 1) / dt, "unit": UNIT,
+    if world > 1:
+        # The whole job: every rank's chains over the slowest rank's time.
+        from paper_1704_04381_gb300 import shard
+        dt = shard.max_over_ranks(dt)
+    return {"value": len(ens.items) * C * (N - 1) * world / dt, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
