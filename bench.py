@@ -425,7 +425,7 @@ def measure_e2e(args, rosen, torch, dev, stream, chain0, ens, world=1):
         from paper_1704_04381_gb300 import shard
         dt = shard.max_over_ranks(dt)
     return {"value": len(ens.items) * C * (N - 1) * world / dt, "unit": UNIT,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+            "h2d_bytes_per_step": h2d * world, "d2h_bytes_per_step": d2h * world}
 
 
 def oracle_rates(with_hs, threads, budget_s):
