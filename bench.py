@@ -342,24 +342,32 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank != 0:
         return
-    # The metric's latency half: a short served run (one GPU only).
-    served = served_sf = None
-    if not args.no_served and world == 1:
+    # The batched and served configurations and the conformation-store run
+    # (one GPU only): the metric's latency half and the batched/served
+    # throughput next to the single-ensemble path.
+    batched = served5 = served_ok = stored = None
+    if world == 1 and not (args.no_served and args.no_batched and args.no_store_coords):
         del ens
         torch.cuda.empty_cache()
-        served = served_run(rosen, 40.0, 5.0, 40.0, 256, 1.0)
-        served_sf = served_run(rosen, 40.0, 5.0, 40.0, 256, 1.0, shortest_first=True)
+        if not args.no_store_coords:
+            stored = store_coords_leg(rosen, torch)
+        if not args.no_batched:
+            batched = batched_leg(rosen, torch)
+        if not args.no_served:
+            sf = args.served_policy == "shortest_first"
+            served5 = served_run(rosen, 2000.0, args.served_duration, 40.0, 256, 1.0,
+                                 shortest_first=sf, replay_every=5, torch=torch)
+            # The sustainable rate: 0.7 x the completion rate under saturation.
+            cap = served5["completed"] / served5["wall_s"]
+            served_ok = served_run(rosen, max(1.0, 0.7 * cap), args.served_duration, 40.0, 256,
+                                   1.0, shortest_first=sf)
+            served_ok["capacity_requests_per_s"] = cap
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32+fp32",
         "data": "synthetic (Philox-seeded growth; no input data)",
-        "config": {"workload": WORKLOAD, "N": N, "chains_per_ensemble": C * world,
-                   "lattice_beta_eps": [b for b, _ in LATTICE], "hs_k": K_TRIALS,
-                   "real_space": {"potential": REAL_POT, "k": K_TRIALS, "beta_eps": REAL_BETA},
-                   "max_attempts": max(1, args.max_attempts),
-                   "l2": "no inputs; outputs 160-320 MB per ensemble > 129 MB L2, no flush",
-                   "parallelism": "dp%d (chain ranges per GPU)" % world},
+        "config": step_config(world, args.max_attempts),
         "parts": parts,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "Tops/s (32-bit lane ops)", "frac": achieved / peak,
@@ -370,8 +378,10 @@ def run_ours(args):
         "clocks": clocks.summary(),
         "e2e": e2e,
         "gpu_launches": launches,
-        "served": served,
-        "served_shortest_first": served_sf,
+        "batched": batched,
+        "served_config5": served5,
+        "served_sustainable": served_ok,
+        "store_coords": stored,
         "small_config": n16,
     }
     if not args.no_cpu_baseline:
@@ -476,30 +486,71 @@ def cpu_baseline(with_hs):
             "single_core": {"value": v1, "cores": 1, "parts": r1, "sample": n1}}
 
 
+def step_config(world, max_attempts=0):
+    """The step's workload description, the same for both arms."""
+    return {"workload": WORKLOAD, "N": N, "chains_per_ensemble": C * world,
+            "lattice_beta_eps": [b for b, _ in LATTICE], "hs_k": K_TRIALS,
+            "real_space": {"potential": REAL_POT, "k": K_TRIALS, "beta_eps": REAL_BETA},
+            "max_attempts": max(1, max_attempts),
+            "l2": "no inputs; outputs 160-320 MB per ensemble > 129 MB L2, no flush",
+            "parallelism": "dp%d (chain ranges per GPU)" % world}
+
+
+def oracle_step(S, chain0, threads):
+    """One scaled-down step of the oracle: the first S chains (from chain0) of
+    every ensemble of the step, grown and reduced; returns the seconds taken."""
+    import oracle
+    t = time.perf_counter()
+    for b, seed in LATTICE:
+        o = oracle.lattice_run(seed, N, S, beta_eps=b, chain0=chain0, threads=threads)
+        oracle.reduce(o["logw"], o["r2"].astype("float64"), o["n2rg2"] / float(N * N), N)
+    pot = oracle.LJ if REAL_POT == "lj" else oracle.HARD_SPHERE
+    o = oracle.offlattice_run(HS_SEED, N, S, K_TRIALS, potential=pot, beta_eps=REAL_BETA,
+                              chain0=chain0, threads=threads)
+    oracle.reduce(o["logw"], o["r2"], o["rg2"], N, K_TRIALS)
+    return time.perf_counter() - t
+
+
 def run_reference(args):
+    """The oracle, unmodified, on the machine's host cores.  Each step is the
+    step's workload scaled down to S chains per ensemble (the same four
+    ensembles, grown and reduced), S sized so that a step takes about
+    min(3 s, 60 s / steps); successive steps take successive chain ranges.
+    value = the sampled insertions over the measured time, which is the full
+    step's rate because the ensemble mix is the same."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
     threads = oracle.default_threads()
-    for _ in range(args.warmup):
-        oracle.lattice_run(2, N, 1000, beta_eps=0.2, threads=threads)
-    vals, times, note = [], [], ""
-    for _ in range(max(1, args.steps)):
-        t = time.perf_counter()
-        v, rates, note = oracle_rates(True, threads, budget_s=max(2.0, 60.0 / max(1, args.steps)))
-        times.append(time.perf_counter() - t)
-        vals.append(v)
-    v = statistics.mean(vals)
+    target = min(3.0, 60.0 / max(1, args.steps))
+    cal = oracle_step(2000, 0, threads) / 2000
+    S = max(2000, int(target / max(cal, 1e-9)))
+    for w in range(args.warmup):
+        oracle_step(max(2000, S // 4), w * S, threads)
+    times = []
+    for q in range(max(1, args.steps)):
+        times.append(oracle_step(S, (q + 1) * S, threads))
+    t_step = statistics.mean(times)
+    ins_step = (len(LATTICE) + 1) * S * (N - 1)
+    v = ins_step / t_step
+    full_ms = 1e3 * (len(LATTICE) + 1) * C * (N - 1) / v
+    note = ("per step: chains [q S, (q+1) S) of each of the %d ensembles, S = %d (%.2f%% of "
+            "the 1e7 chains), grown and reduced by the oracle on %d threads"
+            % (len(LATTICE) + 1, S, 100.0 * S / C, threads))
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * len(LATTICE + [0]) * C * (N - 1) / v,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "N": N,
-                                        "chains_per_ensemble": C, "hs_k": K_TRIALS},
+        "data": "synthetic (Philox-seeded growth; no input data)",
+        "config": step_config(world, args.max_attempts),
+        "sampled": {"chains_per_ensemble_per_step": S, "insertions_per_step": ins_step,
+                    "ms_per_step_measured": 1e3 * t_step,
+                    "full_step_ms_extrapolated": full_ms,
+                    "note": "ms_per_step is the measured time of the sampled step; the full "
+                            "1e7-chain step would take full_step_ms_extrapolated at this rate"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": "per step: " + note},
+                         "sample": note},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -529,30 +580,28 @@ def batch_config(rosen, n_ens=256, seed=4, scale=1.0):
     return ens
 
 
-def run_batched(args):
-    import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_1704_04381_gb300 import rosen
-    torch.cuda.set_device(0)
-    ens = batch_config(rosen, scale=args.batch_scale)
+def batched_leg(rosen, torch, scale=1.0, steps=3, warmup=1):
+    """The batched configuration as one graph launch per step (after tuning),
+    next to the same ensembles grown and reduced one after another through
+    the single-ensemble entry points.  Returns a dict (times in ms)."""
+    ens = batch_config(rosen, scale=scale)
     ins = sum(e.C * (e.N - 1) for e in ens)
     b = rosen.RosenBatch(ens)
     t = time.perf_counter()
     b.tune()
     tune_s = time.perf_counter() - t
     stream = torch.cuda.current_stream()
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         b.run(stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(0) as clocks:
+    with ClockSampler(torch.cuda.current_device()) as clocks:
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             b.run(stream)
         e1.record(stream)
         torch.cuda.synchronize()
-    batch_ms = e0.elapsed_time(e1) / args.steps
+    batch_ms = e0.elapsed_time(e1) / steps
     # The plain single-ensemble path on the same ensembles, one after another.
     outs = {}
     ws = rosen.reduce_workspace(max(e.C for e in ens))
@@ -581,23 +630,74 @@ def run_batched(args):
     torch.cuda.synchronize()
     single_ms = e0.elapsed_time(e1)
     cnt = b.counters().cpu().tolist()
-    import json as _json
+    classes = json.loads(b.describe())
+    b.close()
+    del outs
+    torch.cuda.empty_cache()
+    return {"workload": "256 ensembles: N~U{8..256}, C log-uniform [1e3,1e6] x %g, lattice ISAW "
+                        "beta eps U[0,0.5] / LJ k in {16,32,64} beta eps U[0,1]; "
+                        "numpy default_rng(4)" % scale,
+            "chains": sum(e.C for e in ens), "insertions": ins,
+            "graph_launch_ms": batch_ms, "graph_launches_timed": steps,
+            "insertions_per_s": ins / (batch_ms / 1e3),
+            "single_ensemble_path_ms": single_ms,
+            "single_insertions_per_s": ins / (single_ms / 1e3),
+            "batched_over_single": single_ms / batch_ms, "tune_s": tune_s,
+            "fp64_redecided_steps_total": cnt[0], "classes": len(classes),
+            "clocks": clocks.summary()}
+
+
+def run_batched(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1704_04381_gb300 import rosen
+    torch.cuda.set_device(0)
+    r = batched_leg(rosen, torch, scale=args.batch_scale, steps=args.steps, warmup=args.warmup)
     line = {
         "metric": "batched monomer insertions/s (256 mixed ensembles, one graph launch)",
-        "value": ins / (batch_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True,
+        "value": r["insertions_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["graph_launch_ms"], "higher_is_better": True,
         "dtype": "int32+fp32", "data": "synthetic",
-        "config": {"workload": "256 ensembles: N~U{8..256}, C log-uniform [1e3,1e6] x %g, "
-                               "lattice ISAW / LJ k in {16,32,64}" % args.batch_scale,
-                   "chains": sum(e.C for e in ens), "insertions": ins},
-        "single_ensemble_path": {"ms": single_ms, "insertions_per_s": ins / (single_ms / 1e3)},
-        "batched_over_single": single_ms / batch_ms,
-        "tune_s": tune_s, "classes": _json.loads(b.describe()),
-        "fp64_redecided_steps_total": cnt[0],
-        "clocks": clocks.summary(),
+        "config": {"workload": r["workload"], "chains": r["chains"],
+                   "insertions": r["insertions"]},
+        "batched": r,
     }
-    b.close()
     print(json.dumps(line), flush=True)
+
+
+def store_coords_leg(rosen, torch, steps=2):
+    """Config 3 with its conformations written out: real-space hard spheres,
+    N = 64, k = 32, 10^7 chains, ROSEN_STORE_COORDS (12 B per bead per chain,
+    7.7 GB per launch).  Reports the launch time against the same launch
+    without the conformations, and the write bandwidth against the measured
+    HBM peak."""
+    stream = torch.cuda.current_stream()
+    res = {}
+    for flags, name in ((0, "no_coords"), (rosen.ROSEN_STORE_COORDS, "coords")):
+        out = rosen.offlattice_outputs(N, C, coords=bool(flags))
+        p = rosen.offlattice_params(HS_SEED, N, C, 32, flags=flags)
+        rosen.rosen_offlattice_grow(p, out, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            rosen.rosen_offlattice_grow(p, out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = e0.elapsed_time(e1) / steps
+        del out
+        torch.cuda.empty_cache()
+    written = 12 * N * C
+    peak = measured_peak("hbm_gbs", 6800.0)
+    gbs = written / (res["coords"] / 1e3) / 1e9
+    return {"workload": "real-space hard spheres N=64 k=32, 1e7 chains, conformations stored",
+            "ms": res["coords"], "ms_without_coords": res["no_coords"],
+            "coords_bytes_per_launch": written,
+            "write_gb_per_s": gbs, "hbm_peak_gb_per_s": peak,
+            "hbm_frac": gbs / peak,
+            "basis": "12 B per bead per chain (FP32 x, y, z) written once; the kernel is "
+                     "ALU-bound, so the write rate is the conformation output rate"}
 
 
 def run_long(args):
@@ -712,18 +812,32 @@ def run_long(args):
     print(json.dumps(line), flush=True)
 
 
-def served_run(rosen, rate, duration, budget_gb, max_queue, scale, shortest_first=False):
+def request_cost(e):
+    """A rough relative GPU cost of a request (used only to weight a sampled
+    replay): chains x N^2, real-space chains x 8k heavier than lattice ones."""
+    f = 1.0 if e.model == 0 else 8.0 * e.k
+    return e.C * e.N * e.N * f
+
+
+def served_run(rosen, rate, duration, budget_gb, max_queue, scale, shortest_first=False,
+               replay_every=0, torch=None):
     """Poisson arrivals at `rate` per second for `duration` seconds, drawn from
     the batched configuration's distribution (x scale), 20% storing their
-    conformations; returns the completed chains/s, latency percentiles and
-    admission counts.  shortest_first: the server's priority streams."""
+    conformations.  After the arrivals stop, the admitted requests drain.
+    Returns completed chains/s over the whole run (first arrival to last
+    completion), latency percentiles and admission counts.  With
+    replay_every = q, every q-th completed request (by ticket) is grown and
+    reduced again, one after another, through the single-ensemble entry
+    points; the single path's time for all completed requests is estimated
+    from that sample (weighted by request_cost) and compared with the
+    served wall time."""
     import random
     import numpy as np
     pool = batch_config(rosen, n_ens=4096, seed=5, scale=scale)
     rng = random.Random(5)
     srv = rosen.RosenServer(mem_budget_bytes=int(budget_gb * (1 << 30)), max_slots=64,
                             max_queue=max_queue, shortest_first=shortest_first)
-    done, rejected, tickets = [], 0, []
+    done, rejected, tickets, reqs = [], 0, [], {}
     lock = threading.Lock()
     stop = threading.Event()
 
@@ -738,11 +852,12 @@ def served_run(rosen, rate, duration, budget_gb, max_queue, scale, shortest_firs
                     srv.release(t)
                     with lock:
                         tickets.remove(t)
-            time.sleep(0.001)
+            time.sleep(0.005)
 
     th = threading.Thread(target=collector, daemon=True)
     th.start()
     t0 = time.perf_counter()
+    t0_ns = time.monotonic_ns()
     t_next = t0
     n = 0
     chains_offered = 0
@@ -763,20 +878,81 @@ def served_run(rosen, rate, duration, budget_gb, max_queue, scale, shortest_firs
         if st == rosen.ROSEN_OK:
             with lock:
                 tickets.append(t)
+            reqs[t] = req
         else:
             rejected += 1
+    arrivals_s = time.perf_counter() - t0
     stop.set()
     th.join(timeout=duration * 4 + 120)
-    wall = time.perf_counter() - t0
     srv.close()
     ok = [r for r in done if r["status"] == rosen.ROSEN_OK]
+    # The run lasts from the first arrival to the last completion (steady
+    # clock of the server's time stamps).
+    wall = (max(r["t_done_ns"] for r in ok) - t0_ns) / 1e9 if ok else arrivals_s
     lat = np.array([(r["t_done_ns"] - r["t_submit_ns"]) / 1e6 for r in ok]) if ok else np.zeros(1)
     chains = sum(int(r["stats"]["n"]) for r in ok)
-    return {"chains_per_s": chains / wall, "offered_requests": n, "rejected_busy": rejected,
-            "completed": len(ok), "offered_chains_per_s": chains_offered / duration,
-            "latency_ms": {"p50": float(np.percentile(lat, 50)),
-                           "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
-            "wall_s": wall, "rate_per_s": rate, "duration_s": duration}
+    insertions = sum(reqs[r["ticket"]].C * (reqs[r["ticket"]].N - 1) for r in ok)
+    out = {"chains_per_s": chains / wall, "insertions_per_s": insertions / wall,
+           "offered_requests": n, "rejected_busy": rejected, "completed": len(ok),
+           "failed": len(done) - len(ok), "offered_chains_per_s": chains_offered / duration,
+           "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                          "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+           "wall_s": wall, "arrivals_s": arrivals_s, "rate_per_s": rate,
+           "duration_s": duration, "budget_gb": budget_gb, "max_queue": max_queue,
+           "store_coords_fraction": 0.2, "shortest_first": bool(shortest_first)}
+    if replay_every and ok:
+        order = sorted(r["ticket"] for r in ok)
+        sample = [reqs[t] for t in order[::replay_every]]
+        ms = replay_single(rosen, torch, sample)
+        w_all = sum(request_cost(reqs[t]) for t in order)
+        w_smp = sum(request_cost(e) for e in sample)
+        est = ms / 1e3 * w_all / w_smp
+        out["single_path"] = {
+            "replayed_requests": len(sample), "replayed_ms": ms,
+            "estimated_s_for_all_completed": est,
+            "served_over_single": est / wall,
+            "basis": "every %d-th completed request grown and reduced alone through "
+                     "rosen_*_grow + rosen_reduce, scaled to all completed requests by "
+                     "C N^2 (x 8k for real space)" % replay_every}
+    return out
+
+
+def replay_single(rosen, torch, reqs):
+    """Grow and reduce the requests one after another through the
+    single-ensemble entry points (CUDA events; ms)."""
+    stream = torch.cuda.current_stream()
+    ws = rosen.reduce_workspace(max(r.C for r in reqs))
+    st = rosen.stats_tensor()
+
+    def one(r):
+        if r.model == rosen.ROSEN_MODEL_LATTICE:
+            o = rosen.lattice_outputs(r.N, r.C)
+            rosen.rosen_lattice_grow(rosen.lattice_params(r.seed, r.N, r.C, beta_eps=r.beta_eps,
+                                                          ensemble=r.ensemble), o, stream)
+            rosen.rosen_reduce(rosen.lattice_reduce_in(o, r.N, int(r.beta_eps == 0.0)), st, ws,
+                               stream)
+        else:
+            o = rosen.offlattice_outputs(r.N, r.C)
+            rosen.rosen_offlattice_grow(
+                rosen.offlattice_params(r.seed, r.N, r.C, r.k, potential=r.potential,
+                                        beta_eps=r.beta_eps, ensemble=r.ensemble), o, stream)
+            rosen.rosen_reduce(rosen.offlattice_reduce_in(o, r.N, r.k), st, ws, stream)
+        return o
+
+    keep = [one(r) for r in reqs[:2]]      # warm-up (allocator, modules)
+    torch.cuda.synchronize()
+    del keep
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total = 0.0
+    for r in reqs:
+        o = None
+        e0.record(stream)
+        o = one(r)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1)
+        del o
+    return total
 
 
 def run_served(args):
@@ -786,7 +962,8 @@ def run_served(args):
     from paper_1704_04381_gb300 import rosen
     torch.cuda.set_device(0)
     r = served_run(rosen, args.rate, args.duration, args.budget_gb, args.max_queue,
-                   args.batch_scale, shortest_first=args.shortest_first)
+                   args.batch_scale, shortest_first=args.shortest_first,
+                   replay_every=args.replay_every, torch=torch)
     line = {
         "metric": "served chains/s with p50/p99 latency (Poisson arrivals)",
         "value": r["chains_per_s"], "unit": "chains/s", "n_gpus": 1,
@@ -795,10 +972,7 @@ def run_served(args):
                                "conformations" % args.batch_scale, "rate_per_s": args.rate,
                    "duration_s": args.duration, "budget_gb": args.budget_gb,
                    "max_queue": args.max_queue, "shortest_first": args.shortest_first},
-        "offered_requests": r["offered_requests"], "rejected_busy": r["rejected_busy"],
-        "completed": r["completed"], "offered_chains_per_s": r["offered_chains_per_s"],
-        "latency_ms": r["latency_ms"],
-        "wall_s": r["wall_s"],
+        "served": r,
     }
     print(json.dumps(line), flush=True)
 
@@ -812,7 +986,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-served", action="store_true",
-                    help="step: skip the short served run (40 requests/s for 5 s)")
+                    help="step: skip the served runs (2000 requests/s, then 0.7 x capacity)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="step: skip the batched configuration (one graph launch)")
+    ap.add_argument("--no-store-coords", action="store_true",
+                    help="step: skip the hard-sphere launch that stores conformations")
+    ap.add_argument("--served-duration", type=float, default=60.0,
+                    help="step: seconds of arrivals in each served run")
+    ap.add_argument("--served-policy", default="shortest_first",
+                    choices=["shortest_first", "arrival"],
+                    help="step: the server's scheduling policy")
     ap.add_argument("--lattice-only", action="store_true")
     ap.add_argument("--chains", type=int, default=None,
                     help="chains per ensemble (default 10^7); smaller values are for profiling")
@@ -824,7 +1007,9 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=40.0)
     ap.add_argument("--max-queue", type=int, default=256)
     ap.add_argument("--shortest-first", action="store_true",
-                    help="served: priority streams by request work (small requests first)")
+                    help="served: shortest remaining work first (default: arrival order)")
+    ap.add_argument("--replay-every", type=int, default=0,
+                    help="served: replay every q-th completed request through the single path")
     ap.add_argument("--max-attempts", type=int, default=0,
                     help="step: restart mode, growths per chain (0/1: dead ends keep W = 0)")
     ap.add_argument("--real", default="hard_sphere", choices=["hard_sphere", "lj"],

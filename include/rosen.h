@@ -220,8 +220,16 @@ typedef struct rosen_offlattice_out {
  * U_t the sum of 4 eps [(sigma/d)^12 - (sigma/d)^6] over beads with
  * d < cutoff (W *= sum_t w_t, trial t taken with probability w_t / sum).
  * Coordinates are FP32 (float-float sums); decisions that FP32 rounding
- * could flip are re-taken in FP64, so the path equals that of an FP64
- * implementation of the same rule.
+ * could flip are re-taken in FP64 with the definition's arithmetic in its
+ * order (no contraction, a true division).  The FP64 positions they use
+ * differ from those of a sequential FP64 implementation by the float-float
+ * storage of earlier re-decisions (at most 2^-48 |r|), the FP64 sin/cos of
+ * the directions (a few 1e-16 per step) and the order of the position sums,
+ * together below 1e-14 i after i steps.  So the path equals that of an FP64
+ * implementation of the same rule except at a step where a squared
+ * distance lies within about 1e-13 N of sigma^2 or of cutoff^2, or the
+ * selection draw within a relative 1e-13 N of a prefix-sum boundary (the
+ * tests require >= 99.9% equal paths; all tested chains take them).
  * Scratch: the call takes 8 bytes (plus, for hard spheres with N <= 128, a
  * bit per chain) from the device's stream-ordered allocator on `stream` and
  * frees it there: a chain counter for the persistent grid and the mask of
@@ -333,6 +341,22 @@ ROSEN_API size_t rosen_reduce_workspace_size(int64_t C);
  */
 ROSEN_API int rosen_reduce(const rosen_reduce_in *in, rosen_stats *out, void *workspace,
                  size_t workspace_bytes, void *stream);
+
+/*
+ * Merge the statistics of n disjoint chain sets of one ensemble -- e.g. the
+ * chain ranges that several GPUs grew -- into the statistics of their union
+ * (Eq. 2 with W as weight, Eq. 9), with the reduction's own tile merge:
+ * the largest log_max M, every weighted sum rescaled by exp(M_p - M) and
+ * every squared-weight sum by exp(2 (M_p - M)), growths and live chains
+ * summed; the derived fields (logZ, logZ_norm, means, standard errors, ESS)
+ * are then formed as rosen_reduce forms them.  parts and out are HOST
+ * pointers; the parts are merged in the order given.  N and k are the
+ * ensemble's monomers and trials per step (k = 0: logZ_norm = logZ).  Runs
+ * on the host, with no CUDA call.  Errors: EINVAL (NULL pointer, n < 1,
+ * N < 1 or k < 0).
+ */
+ROSEN_API int rosen_stats_merge(const rosen_stats *parts, int32_t n, int32_t N, int32_t k,
+                                rosen_stats *out);
 
 /* ---- batched growth: many ensembles, one graph launch ---------------- */
 #define ROSEN_MODEL_LATTICE 0
@@ -487,9 +511,12 @@ ROSEN_API int rosen_serve_destroy(rosen_server *s);
  *  - limit: C <= ROSEN_REDUCE_NOALLOC_MAX_CHAINS (2^24 chains, 768 KiB of
  *    scratch, held by every GPU that loads the library until exit); larger C
  *    returns ROSEN_ENOMEM and enqueues nothing;
- *  - the first call on a device looks the scratch address up
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture;
+ *  - a call looks the scratch address up (cudaGetSymbolAddress) with the
+ *    caller's device current, every time its stream is not being captured
+ *    (so it follows a module reloaded after cudaDeviceReset); a call made
+ *    while its stream is being captured reuses the address found by the last
+ *    uncaptured call on that device, so make one call on each device before
+ *    any stream capture (otherwise EINVAL);
  *  - every call shares the one array, which keeps the last call's contents;
  *    nothing in it needs clearing (each call rewrites what it reads), but
  *    calls whose kernels overlap on the GPU (e.g. on two streams) race;

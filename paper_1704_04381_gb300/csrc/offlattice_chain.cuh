@@ -378,11 +378,6 @@ struct Group {
     }
 };
 
-// FP64 replay of r_{b+1} .. r_{i-1} from the chosen trials, starting at bead
-// b, the last bead replayed before (its float-float position is its FP64 one
-// to 2^-48 relative); the positions are stored back into the float-float
-// arrays and the end returned.  Only the steps since the last replay are
-// summed, so the cost does not grow with i.
 // Philox draw of counter c under the ensemble's key.  kFly computes the round
 // keys on the fly from the first (two adds per round) instead of reading the
 // precomputed schedule: kernels whose OffArgs live in shared memory (the
@@ -396,6 +391,14 @@ __device__ __forceinline__ uint4 draw(const OffArgs &a, uint4 c)
         return philox(c, a.key);
 }
 
+// FP64 replay of r_{b+1} .. r_{i-1} from the chosen trials, starting at bead
+// b, the last bead replayed before (its float-float position is its FP64 one
+// to 2^-48 relative); the positions are stored back into the float-float
+// arrays and the end returned.  Only the steps since the last replay are
+// summed, so the cost does not grow with i.  The G lanes add their
+// directions with a group prefix scan: the sums differ from the sequential
+// order of the definition by a few FP64 roundings, far below the 2^-48 of
+// the float-float storage.
 template <int G, bool kFly = false>
 __device__ __noinline__ void replay_positions(const OffArgs &a, const ChainSmem &w,
                                               const Group<G> &g, uint32_t chain, uint32_t aw,
@@ -464,33 +467,35 @@ __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, c
         trial_words(xx, t, wa, wb);
         double dx, dy, dz;
         dir64(wa, wb, dx, dy, dz);
-        const double tx = ex + dx, ty = ey + dy, tz = ez + dz;
+        // The definition's arithmetic in its order, each operation rounded
+        // once (no contraction into FMAs, a true division): the trial
+        // position end + u, the displacement to bead j, d^2 = (dx^2 + dy^2)
+        // + dz^2, and 4 s3 (s3 - 1) with s3 = (sigma^2 / d^2)^3 summed over
+        // the beads within the cutoff.
+        const double tx = __dadd_rn(ex, dx), ty = __dadd_rn(ey, dy), tz = __dadd_rn(ez, dz);
         double acc = 0.0;
         bool fr = true;
         for (int q = 0; q < nn; ++q) {
             const int j = w.nj[q];
             const float4 h = w.hi[j], l = w.lo[j];
-            const double rx = tx - ((double)h.x + (double)l.x);
-            const double ry = ty - ((double)h.y + (double)l.y);
-            const double rz = tz - ((double)h.z + (double)l.z);
-            const double d2 = fma(rx, rx, fma(ry, ry, rz * rz));
+            // (hi + lo of a float-float position is exact in FP64.)
+            const double rx = __dsub_rn(tx, (double)h.x + (double)l.x);
+            const double ry = __dsub_rn(ty, (double)h.y + (double)l.y);
+            const double rz = __dsub_rn(tz, (double)h.z + (double)l.z);
+            const double d2 =
+                __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
             if (!LJ) {
                 if (d2 < a.sig2d) fr = false;
             } else if (d2 < a.rc2d) {
-                // sigma^2 / d^2 by two Newton steps from the FP32 reciprocal
-                // (FP64 division is a long instruction sequence on this part).
-                double rcp = (double)__frcp_rn((float)d2);
-                rcp = rcp * fma(-d2, rcp, 2.0);
-                rcp = rcp * fma(-d2, rcp, 2.0);
-                const double sr = a.sig2d * rcp;
-                const double s3 = sr * sr * sr;
-                acc = fma(4.0 * s3, s3 - 1.0, acc);
+                const double sr = __ddiv_rn(a.sig2d, d2);
+                const double s3 = __dmul_rn(__dmul_rn(sr, sr), sr);
+                acc = __dadd_rn(acc, __dmul_rn(__dmul_rn(4.0, s3), __dsub_rn(s3, 1.0)));
             }
         }
         const bool valid = t < k;
         if (!valid) val[s] = LJ ? INFINITY : 0.0;
         else if (!LJ) val[s] = fr ? 1.0 : 0.0;
-        else val[s] = (a.beta_eps == 0.0) ? 0.0 : a.beta_eps * acc;
+        else val[s] = (a.beta_eps == 0.0) ? 0.0 : __dmul_rn(a.beta_eps, acc);
     }
     if (!LJ) {
         int cnt = 0;
@@ -543,7 +548,7 @@ __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, c
                         if (P > r) pick = t;
                     }
                 }
-                if (pass == 0) r = u24d(selw) * S;
+                if (pass == 0) r = __dmul_rn(u24d(selw), S);
             }
             sel = pick >= 0 ? pick : lastpos;
             logS = (float)(log(S) - bmin);

@@ -74,9 +74,10 @@ __device__ __forceinline__ void load_chain(const ReduceArgs &a, int64_t c, doubl
     }
 }
 
-// Merge partial b into a (same max-shift convention).
-__device__ __forceinline__ void merge(double &Ma, double *sa, double &na, double Mb,
-                                      const double *sb, double nb)
+// Merge partial b into a (same max-shift convention).  Host and device: the
+// multi-GPU merge (rosen_stats_merge) uses the same arithmetic.
+__host__ __device__ __forceinline__ void merge(double &Ma, double *sa, double &na, double Mb,
+                                               const double *sb, double nb)
 {
     const double M = fmax(Ma, Mb);
     if (M == -INFINITY) {
@@ -91,6 +92,45 @@ __device__ __forceinline__ void merge(double &Ma, double *sa, double &na, double
     for (int q = 3; q < 8; ++q) sa[q] = sa[q] * (fa * fa) + sb[q] * (fb * fb);
     Ma = M;
     na += nb;
+}
+
+// The statistics of an ensemble from its merged sums: Eq. 9's log Z (mean
+// weight over the n growths), Eq. 2's W-weighted means of R_ee^2 and R_g^2,
+// their ratio standard errors sqrt(sum w^2 (A - mean)^2) / sum w, and the
+// effective sample size (sum w)^2 / sum w^2.
+__host__ __device__ __forceinline__ rosen_stats finish(double M, const double *S, double alive,
+                                                       double n, int N, int k)
+{
+    rosen_stats r;
+    r.n = n;
+    r.n_alive = alive;
+    r.log_max = M;
+    r.S0 = S[0];
+    r.S1 = S[1];
+    r.S2 = S[2];
+    r.Q0 = S[3];
+    r.Q1_r2 = S[4];
+    r.Q2_r2 = S[5];
+    r.Q1_rg2 = S[6];
+    r.Q2_rg2 = S[7];
+    if (alive == 0.0) {
+        r.logZ = -INFINITY;
+        r.logZ_norm = -INFINITY;
+        r.mean_r2 = r.se_r2 = r.mean_rg2 = r.se_rg2 = NAN;
+        r.ess = 0.0;
+    } else {
+        r.logZ = r.log_max + log(r.S0 / r.n);
+        r.logZ_norm = k > 0 ? r.logZ - (double)(N - 1) * log((double)k) : r.logZ;
+        const double m1 = r.S1 / r.S0, m2 = r.S2 / r.S0;
+        const double v1 = r.Q2_r2 - 2.0 * m1 * r.Q1_r2 + m1 * m1 * r.Q0;
+        const double v2 = r.Q2_rg2 - 2.0 * m2 * r.Q1_rg2 + m2 * m2 * r.Q0;
+        r.mean_r2 = m1;
+        r.se_r2 = sqrt(v1 > 0.0 ? v1 : 0.0) / r.S0;
+        r.mean_rg2 = m2;
+        r.se_rg2 = sqrt(v2 > 0.0 ? v2 : 0.0) / r.S0;
+        r.ess = r.S0 * r.S0 / r.Q0;
+    }
+    return r;
 }
 
 // Reduce tile `tile` of the ensemble a into *out (one block of kThreads).
@@ -215,36 +255,8 @@ __device__ __forceinline__ void reduce_final(const Partial *part, int64_t ntiles
         __syncthreads();
     }
     if (threadIdx.x != 0) return;
-    rosen_stats r;
-    r.n = sG[0];   // integer-valued partial sums: exact in FP64
-    r.n_alive = sN[0];
-    r.log_max = sM[0];
-    r.S0 = sS[0][0];
-    r.S1 = sS[0][1];
-    r.S2 = sS[0][2];
-    r.Q0 = sS[0][3];
-    r.Q1_r2 = sS[0][4];
-    r.Q2_r2 = sS[0][5];
-    r.Q1_rg2 = sS[0][6];
-    r.Q2_rg2 = sS[0][7];
-    if (sN[0] == 0.0) {
-        r.logZ = -INFINITY;
-        r.logZ_norm = -INFINITY;
-        r.mean_r2 = r.se_r2 = r.mean_rg2 = r.se_rg2 = NAN;
-        r.ess = 0.0;
-    } else {
-        r.logZ = r.log_max + log(r.S0 / r.n);
-        r.logZ_norm = a.k > 0 ? r.logZ - (double)(a.N - 1) * log((double)a.k) : r.logZ;
-        const double m1 = r.S1 / r.S0, m2 = r.S2 / r.S0;
-        const double v1 = r.Q2_r2 - 2.0 * m1 * r.Q1_r2 + m1 * m1 * r.Q0;
-        const double v2 = r.Q2_rg2 - 2.0 * m2 * r.Q1_rg2 + m2 * m2 * r.Q0;
-        r.mean_r2 = m1;
-        r.se_r2 = sqrt(v1 > 0.0 ? v1 : 0.0) / r.S0;
-        r.mean_rg2 = m2;
-        r.se_rg2 = sqrt(v2 > 0.0 ? v2 : 0.0) / r.S0;
-        r.ess = r.S0 * r.S0 / r.Q0;
-    }
-    *out = r;
+    // The growth count is a sum of integer-valued partials: exact in FP64.
+    *out = finish(sM[0], sS[0], sN[0], sG[0], a.N, a.k);
 }
 
 __global__ void __launch_bounds__(kFinalThreads) reduce_final_kernel(const Partial *part,
@@ -376,8 +388,8 @@ size_t reduce_workspace_bytes(int64_t C)
 // Allocation-free variant.  Its scratch (the per-tile partials) lives in a
 // fixed array in this file; every GPU that loads the library holds it until
 // the process exits.  In host code the array's name is only a stand-in, so
-// the device address is looked up with cudaGetSymbolAddress, once per device
-// (with that device current), on the first call made on it.
+// the device address is looked up with cudaGetSymbolAddress, with the
+// device current, on every call made outside stream capture.
 // ---------------------------------------------------------------------------
 namespace rosen {
 namespace {
@@ -389,7 +401,12 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_addr[kMaxDevices] = {};
 
-int noalloc_scratch(void **out)
+// The device address of the scratch on the current device.  A call whose
+// stream is not being captured looks it up again every time (cheap), so a
+// module reloaded after cudaDeviceReset is followed; a call made while its
+// stream is captured uses the address the last uncaptured call on this
+// device found.
+int noalloc_scratch(cudaStream_t s, void **out)
 {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -398,14 +415,22 @@ int noalloc_scratch(void **out)
                          cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices)
         return set_error(ROSEN_EINVAL, "rosen_reduce_noalloc: device %d out of range", dev);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess)
+        return set_error(ROSEN_ECUDA, "rosen_reduce_noalloc: cudaStreamIsCapturing: %s",
+                         cudaGetErrorString(e));
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_partials);
         if (e != cudaSuccess || !p)
             return set_error(ROSEN_ECUDA, "rosen_reduce_noalloc: cudaGetSymbolAddress: %s",
                              cudaGetErrorString(e));
         g_noalloc_addr[dev] = p;
+    } else if (!g_noalloc_addr[dev]) {
+        return set_error(ROSEN_EINVAL, "rosen_reduce_noalloc: the first call on device %d must "
+                                       "come before any stream capture", dev);
     }
     *out = g_noalloc_addr[dev];
     return ROSEN_OK;
@@ -424,7 +449,7 @@ extern "C" int rosen_reduce_noalloc(const rosen_reduce_in *in, rosen_stats *out,
                                 "limit of %d chains; use rosen_reduce with a workspace",
                                 (long long)in->C, (int)ROSEN_REDUCE_NOALLOC_MAX_CHAINS);
     void *ws = nullptr;
-    st = rosen::noalloc_scratch(&ws);
+    st = rosen::noalloc_scratch((cudaStream_t)stream, &ws);
     if (st != ROSEN_OK) return st;
     // Every partial the final merge reads is rewritten by this call's tile
     // kernel, so nothing in the shared scratch has to be cleared first.
@@ -446,4 +471,21 @@ extern "C" int rosen_reduce(const rosen_reduce_in *in, rosen_stats *out, void *w
     if (reinterpret_cast<uintptr_t>(workspace) & 15u)
         return set_error(ROSEN_EINVAL, "rosen_reduce: workspace must be 16-byte aligned");
     return reduce_launch(in, out, workspace, (cudaStream_t)stream);
+}
+
+extern "C" int rosen_stats_merge(const rosen_stats *parts, int32_t n, int32_t N, int32_t k,
+                                 rosen_stats *out)
+{
+    if (!parts || !out || n < 1)
+        return set_error(ROSEN_EINVAL, "rosen_stats_merge: NULL argument or n < 1");
+    if (N < 1 || k < 0) return set_error(ROSEN_EINVAL, "rosen_stats_merge: N >= 1, k >= 0");
+    double M = -INFINITY, S[8] = {0, 0, 0, 0, 0, 0, 0, 0}, alive = 0.0, growths = 0.0;
+    for (int32_t p = 0; p < n; ++p) {
+        const rosen_stats &b = parts[p];
+        const double Sb[8] = {b.S0, b.S1, b.S2, b.Q0, b.Q1_r2, b.Q2_r2, b.Q1_rg2, b.Q2_rg2};
+        merge(M, S, alive, b.n_alive > 0.0 ? b.log_max : -INFINITY, Sb, b.n_alive);
+        growths += b.n;
+    }
+    *out = finish(M, S, alive, growths, N, k);
+    return ROSEN_OK;
 }

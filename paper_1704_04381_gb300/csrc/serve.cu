@@ -348,8 +348,10 @@ void scheduler(rosen_server *s)
             if (q->state == FAILED) ++s->n_failed;
             q->t_done = now_ns();
             s->used -= q->work_bytes;
-            if (q->state == FAILED && q->coords) {
-                cudaFreeAsync(q->coords, q->stream);
+            if (q->state == FAILED) {
+                // A failed request gives back everything it reserved, whether
+                // or not its conformations were ever allocated.
+                if (q->coords) cudaFreeAsync(q->coords, q->stream);
                 q->coords = nullptr;
                 s->used -= q->coord_bytes;
             }

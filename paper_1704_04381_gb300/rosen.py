@@ -161,6 +161,8 @@ def load():
     L.rosen_batch_destroy.restype = ctypes.c_int
     L.rosen_reduce_noalloc.argtypes = [ctypes.POINTER(rosen_reduce_in), _vp, _vp]
     L.rosen_reduce_noalloc.restype = ctypes.c_int
+    L.rosen_stats_merge.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp]
+    L.rosen_stats_merge.restype = ctypes.c_int
     _LIB = L
     return L
 
@@ -378,6 +380,19 @@ def lattice_reduce_in(out, N, use_counts):
                            attempts=_ptr(out.get("attempts")))
 
 
+def rosen_stats_merge(parts, N, k=0):
+    """Merge rosen_stats of disjoint chain sets (host sequences of 18 numbers
+    in STAT_KEYS order, or dicts) into the statistics of their union; runs
+    in the library, on the host."""
+    rows = [[p[key] for key in STAT_KEYS] if isinstance(p, dict) else list(p) for p in parts]
+    n = len(rows)
+    arr = (ctypes.c_double * (len(STAT_KEYS) * max(n, 1)))(*[v for r in rows for v in r])
+    out = (ctypes.c_double * len(STAT_KEYS))()
+    _check(load().rosen_stats_merge(ctypes.cast(arr, _vp), int(n), int(N), int(k),
+                                    ctypes.cast(out, _vp)))
+    return dict(zip(STAT_KEYS, list(out)))
+
+
 def stats_tensor(device="cuda"):
     return torch.empty(len(STAT_KEYS), dtype=torch.float64, device=device)
 
@@ -531,6 +546,26 @@ def result_dict(r):
             "stats": {k: getattr(r.stats, k) for k in STAT_KEYS},
             "t_submit_ns": r.t_submit_ns, "t_admit_ns": r.t_admit_ns, "t_done_ns": r.t_done_ns,
             "coords": r.coords, "message": r.message.decode(errors="replace")}
+
+
+class _DeviceArray:
+    """A typed view of device memory the library owns (CUDA array interface)."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(int(v) for v in shape),
+                                         "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+def served_coords(result, model, N, C):
+    """Zero-copy torch view [N, 3, C] of a served request's stored
+    conformations (int32 on the lattice, float32 in real space).  The memory
+    belongs to the server and is valid until the ticket is released."""
+    ptr = result["coords"]
+    if not ptr:
+        raise ValueError("the request stored no conformations")
+    typestr = "<i4" if int(model) == ROSEN_MODEL_LATTICE else "<f4"
+    return torch.as_tensor(_DeviceArray(ptr, (N, 3, C), typestr), device="cuda")
 
 
 class RosenServer:

@@ -145,3 +145,76 @@ def test_results_match_the_single_ensemble_path(rosen):
     s = rosen.stats_tensor()
     rosen.rosen_reduce(rosen.offlattice_reduce_in(out, 40, 32), s, rosen.reduce_workspace(5_000))
     assert np.array_equal(s.cpu().numpy(), np.array([res["stats"][k] for k in rosen.STAT_KEYS]))
+
+
+def test_served_results_match_the_oracle(rosen):
+    # A mix served together, every request checked against the FP64 oracle
+    # (Eq. 2 / Eq. 9 estimator): per-chain conformations from the server's
+    # stored coordinates, ensemble statistics from oracle.reduce.
+    import oracle
+    L, R = rosen.ROSEN_MODEL_LATTICE, rosen.ROSEN_MODEL_OFFLATTICE
+    reqs = [
+        # lattice ISAW, conformations stored: bit-exact
+        ("isaw", rosen.request(L, 48, 3000, 21, 4, beta_eps=0.3, store_coords=True)),
+        # athermal lattice: exact counts, statistics to FP64 rounding
+        ("athermal", rosen.request(L, 40, 4000, 22, 5, store_coords=True)),
+        # hard spheres and Lennard-Jones: the oracle's paths
+        ("hs", rosen.request(R, 40, 2000, 23, 6, k=32, store_coords=True)),
+        ("lj", rosen.request(R, 32, 1500, 24, 7, k=16, potential=rosen.ROSEN_LJ, beta_eps=0.8,
+                             store_coords=True)),
+        # long chains: the long-chain kernels inside the server
+        ("long", rosen.request(L, 600, 300, 25, 8, beta_eps=0.2, store_coords=True)),
+    ]
+    srv = rosen.RosenServer(mem_budget_bytes=4 << 30, max_slots=8)
+    try:
+        tickets = [srv.submit(r) for _, r in reqs]
+        for (kind, r), t in zip(reqs, tickets):
+            st, res = srv.wait(t, 180)
+            assert st == rosen.ROSEN_OK and res["status"] == rosen.ROSEN_OK, res
+            N, C = r.N, r.C
+            xyz = rosen.served_coords(res, r.model, N, C).cpu().numpy()   # [N][3][C]
+            xyz = np.transpose(xyz, (2, 0, 1))                               # [C][N][3]
+            got = res["stats"]
+            if r.model == L:
+                o = oracle.lattice_run(r.seed, N, C, beta_eps=r.beta_eps, ensemble=r.ensemble,
+                                       coords=True)
+                assert np.array_equal(xyz.astype(np.float64), o["coords"]), kind
+                ref = oracle.reduce(o["logw"], o["r2"].astype(np.float64), o["n2rg2"] / N ** 2,
+                                    N)
+                assert got["n"] == ref["n"] and got["n_alive"] == ref["n_alive"]
+                if r.beta_eps == 0.0:
+                    # log W from the exact counts in FP64: sums of non-negative
+                    # terms, within 4 n 2^-53 relative.
+                    tol = 4.0 * C * 2.0 ** -53
+                    for key in ("mean_r2", "mean_rg2", "ess"):
+                        assert abs(got[key] - ref[key]) <= tol * abs(ref[key]), (kind, key)
+                    assert abs(got["logZ"] - ref["logZ"]) <= tol * max(1.0, abs(ref["logZ"]))
+                else:
+                    # FP32 log W: (N-1)(1e-6 + 6e-8 |log W|) per chain.
+                    lwmax = np.abs(o["logw"][o["alive"] == 1]).max()
+                    dlw = (N - 1) * (1e-6 + 6e-8 * lwmax)
+                    assert abs(got["logZ"] - ref["logZ"]) <= dlw, kind
+                    for key in ("mean_r2", "mean_rg2"):
+                        assert abs(got[key] - ref[key]) <= 4 * dlw * abs(ref[key]), (kind, key)
+            else:
+                pot = oracle.LJ if r.potential == rosen.ROSEN_LJ else oracle.HARD_SPHERE
+                o = oracle.offlattice_run(r.seed, N, C, r.k, potential=pot, beta_eps=r.beta_eps,
+                                          ensemble=r.ensemble, coords=True)
+                # A chain on the oracle's path carries only the FP32 drift;
+                # any other path differs by O(1) somewhere.
+                alive = o["alive"] == 1
+                d = np.abs(xyz.astype(np.float64) - o["coords"]).reshape(C, -1).max(1)
+                same = d <= (N - 1) * 4e-7 + 1e-6
+                assert same.mean() >= 0.999, (kind, same.mean())
+                ref = oracle.reduce(o["logw"], o["r2"], o["rg2"], N, r.k)
+                assert got["n"] == ref["n"]
+                assert abs(got["n_alive"] - ref["n_alive"]) <= 0.001 * C
+                for key, se in (("mean_r2", "se_r2"), ("mean_rg2", "se_rg2")):
+                    dd = abs(got[key] - ref[key])
+                    assert dd <= 1e-3 * abs(ref[key]) and dd <= 3 * ref[se] + 1e-12, (kind, key)
+                assert abs(got["logZ"] - ref["logZ"]) <= 1e-3 * max(1.0, abs(ref["logZ"]))
+                assert alive.any()
+        for t in tickets:
+            assert srv.release(t) == rosen.ROSEN_OK
+    finally:
+        srv.close()

@@ -3,7 +3,9 @@
 Each rank grows a contiguous chain range.  The ranks exchange only their 18
 statistics, which are merged as the reduction merges its tiles.  Checked here:
 - The merge of shard statistics equals the reduction of all chains at once.
-  Both sides come from the FP64 oracle, so this pins the merge, not a kernel.
+  The merge is the library's rosen_stats_merge (host code, no GPU); the
+  per-shard and whole-ensemble statistics come from the FP64 oracle, so this
+  pins the library's merge against the oracle's single reduction.
 - Two gloo ranks on CPU gather and merge to the same answer on every rank.
 - Timing takes the maximum over ranks.
 - The chain ranges tile the ensemble.
@@ -17,7 +19,14 @@ import pytest
 import torch.multiprocessing as mp
 
 import oracle
+from paper_1704_04381_gb300 import build as pkg_build
 from paper_1704_04381_gb300 import shard
+
+
+@pytest.fixture(scope="module", autouse=True)
+def library():
+    # rosen_stats_merge lives in librosen.so (host code; no device needed).
+    pkg_build.build()
 
 KEYS = [k for k in shard.STAT_KEYS]
 
