@@ -427,16 +427,19 @@ ROSEN_API int rosen_batch_destroy(rosen_batch *b);
 /* ---- serving: a request loop with continuous admission --------------- */
 typedef struct rosen_serve_config {
     uint64_t mem_budget_bytes; /* device memory the requests may hold at once  */
-    int32_t max_slots;         /* requests on the GPU at once, 1..1024          */
+    int32_t max_slots;         /* requests admitted (on the GPU) at once,
+                                  1..1024                                      */
     int32_t max_queue;         /* waiting requests before submit says EBUSY     */
     int32_t device;            /* CUDA device                                   */
-    int32_t shortest_first;    /* 0: running requests share the GPU as the
-                                  block scheduler interleaves their kernels;
-                                  1: streams get priorities by the request's
-                                  work (decades of pair tests from 1e8), so
-                                  small requests' blocks are dispatched first
-                                  (lower median latency, higher tail latency
-                                  for the largest requests under load)       */
+    int32_t shortest_first;    /* order in which admitted requests get GPU time
+                                  slices: 0 = arrival order; 1 = least
+                                  estimated remaining GPU time first, divided
+                                  by 1 + the seconds the request has waited
+                                  (so large requests are not starved)          */
+    uint64_t pool_max_bytes;   /* cap of the server's device memory pool (0: no
+                                  cap); a request whose memory the pool cannot
+                                  supply fails with ROSEN_ENOMEM and gives its
+                                  share of the budget back                     */
 } rosen_serve_config;
 
 typedef struct rosen_request {
@@ -474,10 +477,25 @@ typedef struct rosen_serve_counters {
 typedef struct rosen_server rosen_server;   /* opaque */
 
 /*
- * Start a server: a scheduler thread that admits submitted requests in
- * arrival order as soon as a slot and enough of the memory budget are free,
- * and runs each admitted request (growth + FP64 reduction) on a stream of
- * its own, concurrently with the others.  Errors: EINVAL, ECUDA.
+ * Start a server: a scheduler thread that
+ *  - admits submitted requests in arrival order as soon as a slot and enough
+ *    of the memory budget are free (a request that does not fit may be
+ *    passed by later ones that do for at most one second; then nothing
+ *    behind it is admitted until it fits);
+ *  - grows every admitted request in slices of its chains (about 4 ms of GPU
+ *    time each; long-chain requests in one piece) on a stream of its own,
+ *    choosing the request of each next slice by the shortest_first policy,
+ *    and keeps a few milliseconds of slices enqueued so the GPU does not
+ *    idle; a request that arrives while others run starts within a slice or
+ *    two and shares the GPU with them;
+ *  - after a request's last slice, reduces it in FP64 (rosen_reduce).
+ * Every chain is grown by the kernel and lanes per chain that
+ * rosen_lattice_grow / rosen_offlattice_grow (or their long-chain forms)
+ * use, so a request's statistics and conformations are those of the
+ * single-ensemble entry points, bit for bit, alone or in any mix.  Device
+ * memory (outputs, scratch, stored conformations) comes from the server's
+ * own stream-ordered pool and is counted against the budget.
+ * Errors: EINVAL, ECUDA.
  */
 ROSEN_API int rosen_serve_create(const rosen_serve_config *cfg, rosen_server **out);
 /* Submit from any thread.  EINVAL if the request is invalid or needs more

@@ -12,6 +12,10 @@ int lattice_validate(const rosen_lattice_params *p, const rosen_lattice_out *o,
 size_t lattice_args_size();
 void lattice_make_args(const rosen_lattice_params *p, const rosen_lattice_out *o, void *out);
 size_t lattice_smem_bytes(int N, int B);
+// Local chains [c_lo, c_hi) of a validated ensemble (shared-memory kernels,
+// N <= 512); outputs are those of rosen_lattice_grow, bit for bit.
+int lattice_grow_range(const rosen_lattice_params *p, const rosen_lattice_out *o, int64_t c_lo,
+                       int64_t c_hi, cudaStream_t s);
 int lattice_batch_prepare(int B, int Nmax, size_t *smem, int *blocks_per_sm);
 void lattice_batch_launch(const void *dev_args, const BatchItem *items, int n_items, int *head,
                           int B, size_t smem, int grid, cudaStream_t s);
@@ -24,6 +28,16 @@ size_t offlattice_args_size();
 void offlattice_make_args(const rosen_offlattice_params *p, const rosen_offlattice_out *o,
                           unsigned long long *counters, void *out);
 int offlattice_default_lanes(int k, bool lj, int N = 0);
+// Local chains [c_lo, c_hi) of a validated ensemble (shared-memory kernels,
+// N <= 1024), with caller-owned scratch of offlattice_range_scratch_bytes(C)
+// bytes (16-byte aligned) whose deferral mask (after a 16-byte header) is
+// zero before the first range of the ensemble; ranges of one ensemble run
+// in stream order and, for hard spheres, start at multiples of 32 chains
+// (any others cost regrowths of shared mask words, same outputs).  Outputs
+// are those of rosen_offlattice_grow, bit for bit.
+size_t offlattice_range_scratch_bytes(int64_t C);
+int offlattice_grow_range(const rosen_offlattice_params *p, const rosen_offlattice_out *o,
+                          int64_t c_lo, int64_t c_hi, void *scratch, cudaStream_t s);
 int offlattice_batch_prepare(int G, int T, bool lj, int Nmax, int *chains_per_block, size_t *smem,
                              int *blocks_per_sm);
 void offlattice_batch_launch(int G, int T, bool lj, const void *dev_args, const BatchItem *items,

@@ -304,8 +304,11 @@ __device__ __forceinline__ void lattice_chain(const LatticeArgs &a, int64_t c, u
 }
 
 
+// Local chains [c_lo, c_hi) of the ensemble, one per lane (a call grows
+// [0, C); the server grows a request in slices of chain ranges).
 template <bool kIsaw>
-__global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a)
+__global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a, int64_t c_lo,
+                                                           int64_t c_hi)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *lut = smem;
@@ -322,8 +325,8 @@ __global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a)
     __syncthreads();
 
     const int B = blockDim.x;
-    const int64_t c = (int64_t)blockIdx.x * B + threadIdx.x;
-    if (c >= a.C) return;
+    const int64_t c = c_lo + (int64_t)blockIdx.x * B + threadIdx.x;
+    if (c >= c_hi) return;
     lattice_chain<kIsaw>(a, c, keys + threadIdx.x, B, lut, seltab, wt32, wt64);
 }
 
@@ -334,7 +337,8 @@ __global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a)
 // index, in the warp's next pass next to fresh chains.  No lane waits for a
 // regrowth while the others idle, and no block waits for one warp.
 template <bool kIsaw>
-__global__ void __launch_bounds__(256) lattice_retry_kernel(const LatticeArgs a, int64_t per_warp)
+__global__ void __launch_bounds__(256) lattice_retry_kernel(const LatticeArgs a, int64_t per_warp,
+                                                            int64_t c_lo, int64_t c_hi)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     uint32_t *lut = smem;
@@ -354,8 +358,8 @@ __global__ void __launch_bounds__(256) lattice_retry_kernel(const LatticeArgs a,
     __syncthreads();
 
     const int64_t w = (int64_t)blockIdx.x * wpb + wib;
-    const int64_t hi = (w + 1) * per_warp < a.C ? (w + 1) * per_warp : a.C;
-    int64_t next = w * per_warp;
+    const int64_t hi = c_lo + (w + 1) * per_warp < c_hi ? c_lo + (w + 1) * per_warp : c_hi;
+    int64_t next = c_lo + w * per_warp;
     int queued = 0;          // warp-uniform
     for (;;) {
         const int take = queued;
@@ -802,8 +806,9 @@ void lattice_batch_launch(const void *dev_args, const BatchItem *items, int n_it
 }
 
 // Restart mode: as many warps as fit on the GPU at once (at most one per 32
-// chains), each with a contiguous range of chains.
-int lattice_retry_launch(const LatticeArgs &a, int N, int B, cudaStream_t s)
+// chains), each with a contiguous range of the chains [c_lo, c_hi).
+int lattice_retry_launch(const LatticeArgs &a, int N, int B, int64_t c_lo, int64_t c_hi,
+                         cudaStream_t s)
 {
     const int wpb = B / 32;
     const size_t smem = (size_t)(kLutWords + kSelBytes / 4 + 8 + 16) * 4 +
@@ -817,10 +822,34 @@ int lattice_retry_launch(const LatticeArgs &a, int N, int B, cudaStream_t s)
     if (e != cudaSuccess)
         return set_error(ROSEN_ECUDA, "rosen_lattice_grow: %s", cudaGetErrorString(e));
     if (bps < 1) return set_error(ROSEN_ECUDA, "rosen_lattice_grow: kernel does not fit an SM");
-    const int64_t warps = std::min<int64_t>((int64_t)bps * sms * wpb, (a.C + 31) / 32);
-    const int64_t per_warp = (a.C + warps - 1) / warps;
-    const int64_t grid = ((a.C + per_warp - 1) / per_warp + wpb - 1) / wpb;
-    kern<<<(unsigned)grid, B, smem, s>>>(a, per_warp);
+    const int64_t n = c_hi - c_lo;
+    const int64_t warps = std::min<int64_t>((int64_t)bps * sms * wpb, (n + 31) / 32);
+    const int64_t per_warp = (n + warps - 1) / warps;
+    const int64_t grid = ((n + per_warp - 1) / per_warp + wpb - 1) / wpb;
+    kern<<<(unsigned)grid, B, smem, s>>>(a, per_warp, c_lo, c_hi);
+    return check_launch("rosen_lattice_grow");
+}
+
+// Grow local chains [c_lo, c_hi) of a validated ensemble (shared-memory
+// kernels, N <= 512).  Every chain's outputs are those of a call over all C
+// chains, bit for bit: a chain is grown by one lane whatever its block.
+int lattice_grow_range(const rosen_lattice_params *p, const rosen_lattice_out *o, int64_t c_lo,
+                       int64_t c_hi, cudaStream_t s)
+{
+    if (c_hi <= c_lo) return ROSEN_OK;
+    LatticeArgs a;
+    lattice_make_args(p, o, &a);
+    const int B = lattice_block(p->N);
+    if (a.max_att > 1) return lattice_retry_launch(a, p->N, B, c_lo, c_hi, s);
+    const size_t smem = lattice_smem_bytes(p->N, B);
+    const int64_t blocks = (c_hi - c_lo + B - 1) / B;
+    if (p->beta_eps == 0.0) {
+        allow_max_smem(lattice_lane_kernel<false>);
+        lattice_lane_kernel<false><<<(unsigned)blocks, B, smem, s>>>(a, c_lo, c_hi);
+    } else {
+        allow_max_smem(lattice_lane_kernel<true>);
+        lattice_lane_kernel<true><<<(unsigned)blocks, B, smem, s>>>(a, c_lo, c_hi);
+    }
     return check_launch("rosen_lattice_grow");
 }
 
@@ -834,21 +863,7 @@ extern "C" int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lat
     const int st = lattice_validate(p, o);
     if (st != ROSEN_OK) return st;
     if (p->C == 0) return ROSEN_OK;
-    LatticeArgs a;
-    lattice_make_args(p, o, &a);
-    const int B = lattice_block(p->N);
-    cudaStream_t s = (cudaStream_t)stream;
-    if (a.max_att > 1) return lattice_retry_launch(a, p->N, B, s);
-    const size_t smem = lattice_smem_bytes(p->N, B);
-    const int64_t blocks = (p->C + B - 1) / B;
-    if (p->beta_eps == 0.0) {
-        allow_max_smem(lattice_lane_kernel<false>);
-        lattice_lane_kernel<false><<<(unsigned)blocks, B, smem, s>>>(a);
-    } else {
-        allow_max_smem(lattice_lane_kernel<true>);
-        lattice_lane_kernel<true><<<(unsigned)blocks, B, smem, s>>>(a);
-    }
-    return check_launch("rosen_lattice_grow");
+    return lattice_grow_range(p, o, 0, p->C, (cudaStream_t)stream);
 }
 
 // ---- long chains -------------------------------------------------------------

@@ -64,7 +64,8 @@ __global__ void __launch_bounds__(256, 4) offlattice_group_kernel(const OffArgs 
 template <int G, int T, bool LJ, bool kDefer = false>
 __global__ void __launch_bounds__(256, 4) offlattice_queue_kernel(const OffArgs a,
                                                                   int chains_per_block,
-                                                                  unsigned long long *next)
+                                                                  unsigned long long *next,
+                                                                  int64_t c_lo, int64_t c_hi)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *logm = reinterpret_cast<float *>(smem_raw);
@@ -77,22 +78,24 @@ __global__ void __launch_bounds__(256, 4) offlattice_queue_kernel(const OffArgs 
                                   (size_t)cib * chain_smem_bytes(a.N, LJ), a.N, LJ);
     for (;;) {
         unsigned long long c = 0;
-        if (g.gl == 0) c = atomicAdd(next, 1ull);
+        if (g.gl == 0) c = (unsigned long long)c_lo + atomicAdd(next, 1ull);
         c = g.bcast(c, 0);
-        if (c >= (unsigned long long)a.C) break;
+        if (c >= (unsigned long long)c_hi) break;
         off_chain<G, T, LJ, ChainSmem, kDefer>(a, (int64_t)c, w, g, logm);
     }
 }
 
-// Second pass of two-pass growth: the chains whose bits the first pass set,
-// grown again from the start with the FP64 re-decision compiled in.  Warps
-// take 32-chain words of the bit mask from a counter (the word after the
-// mask), so the few deferred chains spread evenly; the groups of a warp take
-// a word's set bits together, one each per round, so they step in lock-step
-// as in the first pass instead of diverging.
+// Second pass of two-pass growth: the chains of [c_lo, c_hi) whose bits the
+// first pass set, grown again from the start with the FP64 re-decision
+// compiled in.  Warps take 32-chain words of the bit mask from a counter, so
+// the few deferred chains spread evenly; the groups of a warp take a word's
+// set bits together, one each per round, so they step in lock-step as in
+// the first pass instead of diverging.
 template <int G, int T, bool LJ>
 __global__ void __launch_bounds__(256, 4) offlattice_deferred_kernel(const OffArgs a,
-                                                                     int chains_per_block)
+                                                                     int chains_per_block,
+                                                                     unsigned int *next,
+                                                                     int64_t c_lo, int64_t c_hi)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *logm = reinterpret_cast<float *>(smem_raw);
@@ -103,19 +106,23 @@ __global__ void __launch_bounds__(256, 4) offlattice_deferred_kernel(const OffAr
     const int cib = threadIdx.x / G;
     const ChainSmem w = carve(smem_raw + kTable * sizeof(float) +
                                   (size_t)cib * chain_smem_bytes(a.N, LJ), a.N, LJ);
-    const int64_t words = (a.C + 31) / 32;
-    unsigned int *next = a.deferred + words;
+    const int64_t w_lo = c_lo / 32, w_hi = (c_hi + 31) / 32;
     const int gw = (threadIdx.x & 31) / G;     // this group's place in its warp
     for (;;) {
-        unsigned int q = 0;
-        if ((threadIdx.x & 31) == 0) q = atomicAdd(next, 1u);
+        int64_t q = 0;
+        if ((threadIdx.x & 31) == 0) q = w_lo + (int64_t)atomicAdd(next, 1u);
         q = __shfl_sync(0xffffffffu, q, 0);
-        if ((int64_t)q >= words) break;
+        if (q >= w_hi) break;
+        // Only the chains of this range (the words at its ends may hold
+        // chains of neighbouring ranges).
+        const int64_t b0 = q * 32;
         uint32_t m = a.deferred[q];
+        if (b0 < c_lo) m &= ~0u << (uint32_t)(c_lo - b0);
+        if (b0 + 32 > c_hi) m &= (c_hi - b0 >= 32) ? ~0u : ((1u << (uint32_t)(c_hi - b0)) - 1u);
         while (m) {
             uint32_t mine = m;                   // the gw-th set bit of m, if any
             for (int t = 0; t < gw && mine; ++t) mine &= mine - 1u;
-            if (mine) off_chain<G, T, LJ>(a, (int64_t)q * 32 + __ffs(mine) - 1, w, g, logm);
+            if (mine) off_chain<G, T, LJ>(a, b0 + __ffs(mine) - 1, w, g, logm);
             for (int t = 0; t < 32 / G && m; ++t) m &= m - 1u;
             __syncwarp();
         }
@@ -205,97 +212,130 @@ int chains_per_block_for(int G, int N, bool lj)
     return chains;
 }
 
-// Single-ensemble growth.  Groups take chains from a counter
-// (offlattice_queue_kernel).  Short hard-sphere chains (N <= 128) grow in two
-// passes: their FP32 decisions are almost never ambiguous (about 2% of
-// N = 64, k = 32 chains meet one such step), but the FP64 re-decision path,
-// compiled into the growth kernel, costs every chain registers and time (the
-// kernel without it runs 11% faster).  So the first pass has no FP64 path and
-// defers the chains that need it; the second regrows only those, with it.
-// Longer chains meet ambiguous steps more often (a third of N = 512 chains),
-// and regrowing them costs more than the first pass saves, so they grow in
-// one pass.  Every chain's outputs are those of the one-pass kernel, bit for
-// bit.  The counter and the deferral mask (C/8 bytes) come from the
-// stream-ordered allocator; if that fails, the one-pass kernel runs with one
-// block per chains_per_block chains.
+// Scratch of a range launch: the chain counter (8 bytes), the second pass's
+// word counter (4 bytes, padded to 16), then the deferral mask, one bit per
+// chain of the ensemble.  The counters are zeroed by every launch; the mask
+// must be zero before the first launch over an ensemble's chains.
+constexpr size_t kScratchHeader = 16;
+
+size_t mask_bytes(int64_t C) { return (size_t)((C + 31) / 32) * sizeof(uint32_t); }
+
+// Growth of local chains [c_lo, c_hi).  Groups take chains from a counter
+// (offlattice_queue_kernel); the grid is what the GPU holds at once.  Short
+// hard-sphere chains (N <= 128) grow in two passes: their FP32 decisions are
+// almost never ambiguous (about 2% of N = 64, k = 32 chains meet one such
+// step), but the FP64 re-decision path, compiled into the growth kernel,
+// costs every chain registers and time (the kernel without it runs 11%
+// faster).  So the first pass has no FP64 path and defers the chains that
+// need it; the second regrows only those, with it.  Longer chains meet
+// ambiguous steps more often (a third of N = 512 chains), and regrowing them
+// costs more than the first pass saves, so they grow in one pass.  Every
+// chain's outputs are those of the one-pass kernel, bit for bit.
 template <int G, int T, bool LJ>
-int launch_one(const OffArgs &a, int N, cudaStream_t s)
+int launch_range(const OffArgs &a, int N, int64_t c_lo, int64_t c_hi, void *scratch,
+                 cudaStream_t s)
 {
     const int chains = chains_per_block_for(G, N, LJ);
     const size_t smem = kTable * sizeof(float) + (size_t)chains * chain_smem_bytes(N, LJ);
     const int threads = chains * G;
-    const int64_t blocks = (a.C + chains - 1) / chains;
-    // Counter of the queue kernel, then (hard spheres) the deferral mask and
-    // the second pass's word counter.
-    const int64_t words = (a.C + 31) / 32;
+    const int64_t n = c_hi - c_lo;
+    const int64_t blocks = (n + chains - 1) / chains;
     const bool two_pass = !LJ && N <= 128;
-    const size_t bytes = sizeof(unsigned long long) +
-                         (two_pass ? (size_t)(words + 1) * sizeof(uint32_t) : 0);
+    unsigned char *sc = static_cast<unsigned char *>(scratch);
+    unsigned long long *next = reinterpret_cast<unsigned long long *>(sc);
+    unsigned int *wnext = reinterpret_cast<unsigned int *>(sc + 8);
+    OffArgs d = a;
+    if (two_pass) d.deferred = reinterpret_cast<uint32_t *>(sc + kScratchHeader);
+    cudaError_t e = cudaMemsetAsync(sc, 0, kScratchHeader, s);
+    int dev = 0, sms = 0, bps = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // The first pass without the FP64 path, or the one pass with it.
+    auto first = two_pass ? offlattice_queue_kernel<G, T, LJ, !LJ>
+                          : offlattice_queue_kernel<G, T, LJ, false>;
+    if (e == cudaSuccess) e = allow_max_smem(first);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, first, threads, smem);
+    if (e == cudaSuccess) {
+        int64_t grid = (int64_t)(bps > 0 ? bps : 1) * sms;
+        if (grid > blocks) grid = blocks;
+        first<<<(unsigned)grid, threads, smem, s>>>(d, chains, next, c_lo, c_hi);
+        if constexpr (!LJ) {
+            if (two_pass) {
+                int bps2 = 0;
+                e = allow_max_smem(offlattice_deferred_kernel<G, T, LJ>);
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        &bps2, offlattice_deferred_kernel<G, T, LJ>, threads, smem);
+                const int64_t words = (c_hi + 31) / 32 - c_lo / 32;
+                int64_t grid2 = (int64_t)(bps2 > 0 ? bps2 : 1) * sms;
+                if (grid2 > (words + chains - 1) / chains) grid2 = (words + chains - 1) / chains;
+                if (e == cudaSuccess)
+                    offlattice_deferred_kernel<G, T, LJ>
+                        <<<(unsigned)grid2, threads, smem, s>>>(d, chains, wnext, c_lo, c_hi);
+            }
+        }
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (e != cudaSuccess)
+        return set_error(ROSEN_ECUDA, "rosen_offlattice_grow: %s", cudaGetErrorString(e));
+    return ROSEN_OK;
+}
+
+// A whole ensemble: the scratch comes from the stream-ordered allocator; if
+// that fails, the one-pass kernel runs with one block per chains_per_block
+// chains (same outputs).
+template <int G, int T, bool LJ>
+int launch_one(const OffArgs &a, int N, cudaStream_t s)
+{
+    const bool two_pass = !LJ && N <= 128;
+    const size_t bytes = kScratchHeader + (two_pass ? mask_bytes(a.C) : 0);
     void *buf = nullptr;
     if (cudaMallocAsync(&buf, bytes, s) == cudaSuccess) {
-        unsigned long long *next = static_cast<unsigned long long *>(buf);
-        OffArgs d = a;
-        if (two_pass) d.deferred = reinterpret_cast<uint32_t *>(next + 1);
-        cudaError_t e = cudaMemsetAsync(buf, 0, bytes, s);
-        int dev = 0, sms = 0, bps = 0;
-        if (e == cudaSuccess) e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        // The first pass without the FP64 path, or the one pass with it.
-        auto first = two_pass ? offlattice_queue_kernel<G, T, LJ, !LJ>
-                              : offlattice_queue_kernel<G, T, LJ, false>;
-        if (e == cudaSuccess) e = allow_max_smem(first);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, first, threads, smem);
-        if (e == cudaSuccess) {
-            int64_t grid = (int64_t)(bps > 0 ? bps : 1) * sms;
-            if (grid > blocks) grid = blocks;
-            first<<<(unsigned)grid, threads, smem, s>>>(d, chains, next);
-            if constexpr (!LJ) {
-                if (two_pass) {
-                    int bps2 = 0;
-                    e = allow_max_smem(offlattice_deferred_kernel<G, T, LJ>);
-                    if (e == cudaSuccess)
-                        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                            &bps2, offlattice_deferred_kernel<G, T, LJ>, threads, smem);
-                    int64_t grid2 = (int64_t)(bps2 > 0 ? bps2 : 1) * sms;
-                    if (grid2 > (words + chains - 1) / chains)
-                        grid2 = (words + chains - 1) / chains;
-                    if (e == cudaSuccess)
-                        offlattice_deferred_kernel<G, T, LJ>
-                            <<<(unsigned)grid2, threads, smem, s>>>(d, chains);
-                }
-            }
-            if (e == cudaSuccess) e = cudaGetLastError();
-        }
+        cudaError_t e = two_pass ? cudaMemsetAsync(static_cast<unsigned char *>(buf) +
+                                                       kScratchHeader, 0, bytes - kScratchHeader, s)
+                                 : cudaSuccess;
+        int st = e == cudaSuccess ? launch_range<G, T, LJ>(a, N, 0, a.C, buf, s)
+                                  : set_error(ROSEN_ECUDA, "rosen_offlattice_grow: %s",
+                                              cudaGetErrorString(e));
         const cudaError_t f = cudaFreeAsync(buf, s);
-        if (e != cudaSuccess)
-            return set_error(ROSEN_ECUDA, "rosen_offlattice_grow: %s", cudaGetErrorString(e));
+        if (st != ROSEN_OK) return st;
         if (f != cudaSuccess)
             return set_error(ROSEN_ECUDA, "rosen_offlattice_grow: freeing the work counter: %s",
                              cudaGetErrorString(f));
         return ROSEN_OK;
     }
     cudaGetLastError();   // clear the failed allocation; grow in one pass
+    const int chains = chains_per_block_for(G, N, LJ);
+    const size_t smem = kTable * sizeof(float) + (size_t)chains * chain_smem_bytes(N, LJ);
+    const int64_t blocks = (a.C + chains - 1) / chains;
     allow_max_smem(offlattice_group_kernel<G, T, LJ>);
-    offlattice_group_kernel<G, T, LJ><<<(unsigned)blocks, threads, smem, s>>>(a, chains);
+    offlattice_group_kernel<G, T, LJ><<<(unsigned)blocks, chains * G, smem, s>>>(a, chains);
     return check_launch("rosen_offlattice_grow");
 }
 
 template <int G, bool LJ>
-int launch_g(const OffArgs &a, int N, int k, cudaStream_t s)
+int launch_g(const OffArgs &a, int N, int k, int64_t c_lo, int64_t c_hi, void *scratch,
+             cudaStream_t s)
 {
     const int T = (k + G - 1) / G;
-    if (T <= 1) return launch_one<G, 1, LJ>(a, N, s);
-    if (T <= 2) return launch_one<G, 2, LJ>(a, N, s);
-    return launch_one<G, 4, LJ>(a, N, s);
+    if (!scratch) {
+        if (T <= 1) return launch_one<G, 1, LJ>(a, N, s);
+        if (T <= 2) return launch_one<G, 2, LJ>(a, N, s);
+        return launch_one<G, 4, LJ>(a, N, s);
+    }
+    if (T <= 1) return launch_range<G, 1, LJ>(a, N, c_lo, c_hi, scratch, s);
+    if (T <= 2) return launch_range<G, 2, LJ>(a, N, c_lo, c_hi, scratch, s);
+    return launch_range<G, 4, LJ>(a, N, c_lo, c_hi, scratch, s);
 }
 
 template <bool LJ>
-int launch_lj(const OffArgs &a, int G, int N, int k, cudaStream_t s)
+int launch_lj(const OffArgs &a, int G, int N, int k, int64_t c_lo, int64_t c_hi, void *scratch,
+              cudaStream_t s)
 {
-    if (G == 8) return launch_g<8, LJ>(a, N, k, s);
-    if (G == 16) return launch_g<16, LJ>(a, N, k, s);
-    return launch_g<32, LJ>(a, N, k, s);
+    if (G == 8) return launch_g<8, LJ>(a, N, k, c_lo, c_hi, scratch, s);
+    if (G == 16) return launch_g<16, LJ>(a, N, k, c_lo, c_hi, scratch, s);
+    return launch_g<32, LJ>(a, N, k, c_lo, c_hi, scratch, s);
 }
 
 // The batch kernel of class (G, T, LJ) through one function pointer type.
@@ -434,7 +474,23 @@ int offlattice_launch(const rosen_offlattice_params *p, const rosen_offlattice_o
     const bool lj = p->potential == ROSEN_LJ;
     const int G =
         p->lanes_per_chain ? p->lanes_per_chain : offlattice_default_lanes(p->k, lj, p->N);
-    return lj ? launch_lj<true>(a, G, p->N, p->k, s) : launch_lj<false>(a, G, p->N, p->k, s);
+    return lj ? launch_lj<true>(a, G, p->N, p->k, 0, p->C, nullptr, s)
+              : launch_lj<false>(a, G, p->N, p->k, 0, p->C, nullptr, s);
+}
+
+size_t offlattice_range_scratch_bytes(int64_t C) { return kScratchHeader + mask_bytes(C); }
+
+int offlattice_grow_range(const rosen_offlattice_params *p, const rosen_offlattice_out *o,
+                          int64_t c_lo, int64_t c_hi, void *scratch, cudaStream_t s)
+{
+    if (c_hi <= c_lo) return ROSEN_OK;
+    OffArgs a;
+    offlattice_make_args(p, o, reinterpret_cast<unsigned long long *>(o->counters), &a);
+    const bool lj = p->potential == ROSEN_LJ;
+    const int G =
+        p->lanes_per_chain ? p->lanes_per_chain : offlattice_default_lanes(p->k, lj, p->N);
+    return lj ? launch_lj<true>(a, G, p->N, p->k, c_lo, c_hi, scratch, s)
+              : launch_lj<false>(a, G, p->N, p->k, c_lo, c_hi, scratch, s);
 }
 
 int offlattice_batch_prepare(int G, int T, bool lj, int Nmax, int *chains_per_block, size_t *smem,

@@ -1,29 +1,50 @@
-// serve.cu -- a request loop over the growth and reduction kernels.
+// serve.cu -- a request loop with continuous admission and time-sliced
+// execution over the single-ensemble kernels.
 //
 // Clients submit ensemble requests (model, N, chain count, trials, beta eps,
-// seed) from any thread.  A scheduler thread admits them in arrival order as
-// soon as a slot and enough of the device-memory budget are free, and enqueues
-// the request's growth and FP64 reduction at once on a stream of its own, so
-// requests that arrive while others are on the GPU run concurrently with them
-// (the block scheduler interleaves the kernels of all active streams).  Output
-// memory comes from a stream-ordered pool; the statistics land in pinned host
-// memory.  With shortest_first the streams carry priorities by the request's
-// work (decades of pair tests): when SMs free up, the blocks of smaller
-// requests are dispatched first, so a small request does not wait behind the
-// waves of a large one (nothing is preempted).  Completion is detected with event queries on the host -- no kernel
-// ever waits -- and waits by clients are bounded condition-variable waits.
-// A request's chains are a pure function of its parameters (stateless Philox
-// keyed by seed, ensemble, chain and step), so its result does not depend on
-// what else is running.
+// seed) from any thread.  One scheduler thread:
+//  - admits waiting requests in arrival order as soon as a slot and enough of
+//    the device-memory budget are free; a request that does not fit may be
+//    passed by later ones that do, for at most kPassLimitNs, after which
+//    nothing behind it is admitted until it fits;
+//  - grows every admitted request in slices, chain ranges of about kSliceNs
+//    of GPU time, on the request's own stream, with the single-ensemble
+//    kernels (lattice_grow_range / offlattice_grow_range; long chains in one
+//    piece through the long-chain entry points);
+//  - chooses the request of each next slice by policy: arrival order, or
+//    (shortest_first) the least estimated remaining GPU time, discounted by
+//    the time the request has waited so that large requests are not starved;
+//  - keeps about kLookaheadNs of slices enqueued so that the GPU does not
+//    idle between slices (the next slice's blocks start as the last ones of
+//    the running slice finish);
+//  - after a request's last slice, enqueues its FP64 reduction, the copy of
+//    its statistics to pinned host memory, the release of its scratch and an
+//    event that marks it done.
+// So a request that arrives while a large one runs starts within about one
+// slice, and requests overlap on the GPU at slice boundaries.  No kernel
+// waits on anything: completion is found with event queries on the host, and
+// every client wait is a bounded condition-variable wait.
+//
+// Every chain of a request is grown by the same kernel, with the same lanes
+// per chain, as rosen_lattice_grow / rosen_offlattice_grow would grow it,
+// and its random numbers are a pure function of (seed, ensemble, chain,
+// step); the reduction is rosen_reduce's.  A request's result is therefore
+// the same, bit for bit, alone, in any mix, and through the single-ensemble
+// entry points.
+//
+// Device memory of a request (outputs, reduction scratch, the real-space
+// chain counters and deferral mask, a long-chain workspace, stored
+// conformations) comes from one stream-ordered pool and is counted against
+// the budget from admission until it is returned.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
-#include <time.h>
 
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -35,6 +56,12 @@
 namespace {
 
 enum State { QUEUED = 0, RUNNING = 1, DONE = 2, FAILED = 3, CANCELLED = 4 };
+
+constexpr int64_t kSliceNs = 4'000'000;        // target GPU time of a slice
+constexpr int64_t kLookaheadNs = 8'000'000;    // estimated work kept enqueued
+constexpr int kMaxInflight = 16;               // slices enqueued at once
+constexpr int64_t kPassLimitNs = 1'000'000'000;   // longest a request may be passed over
+constexpr double kAgingNs = 1e9;               // shortest_first: waiting discount scale
 
 int64_t now_ns()
 {
@@ -51,18 +78,41 @@ struct Request {
     State state = QUEUED;
     int status = ROSEN_OK;
     char message[256] = "";
-    int level = 0;             // stream priority class (0: the least work)
-    size_t work_bytes = 0;     // outputs + reduction workspace (freed at completion)
+    size_t work_bytes = 0;     // outputs + scratch (freed after the reduction)
     size_t coord_bytes = 0;    // stored conformations (freed at release)
     void *work = nullptr;
     void *coords = nullptr;
+    // carved from work at admission
+    rosen_lattice_params lp;
+    rosen_lattice_out lo;
+    rosen_offlattice_params op;
+    rosen_offlattice_out oo;
+    rosen_reduce_in rin;
+    void *rws = nullptr;       // reduction workspace
+    size_t rws_bytes = 0;
+    rosen_stats *dstats = nullptr;
+    void *scratch = nullptr;   // real space: chain counters and deferral mask
+    void *long_ws = nullptr;   // long chains: their workspace
+    size_t long_bytes = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     rosen_stats *host_stats = nullptr;   // pinned
     rosen_stats stats;
     int64_t t_submit = 0, t_admit = 0, t_done = 0;
+    int64_t t_passed = 0;      // first time a later request was admitted past it
+    int64_t next_chain = 0;    // first chain not yet in a slice
+    int inflight = 0;          // slices enqueued and not yet seen complete
+    bool finishing = false;    // the reduction (or, after a failure, the end) is enqueued
+    double ns_per_chain = 0.0; // estimated GPU time per chain
     bool in_queue = false;     // still referenced by the admission queue
     bool released = false;     // the client has let go of the ticket
+};
+
+struct Slice {
+    Request *q = nullptr;
+    int64_t chains = 0;
+    double est_ns = 0.0;
+    cudaEvent_t start = nullptr, end = nullptr;
 };
 
 }  // namespace
@@ -73,15 +123,17 @@ struct rosen_server {
     cudaMemPool_t pool = nullptr;
     std::mutex mu;
     std::condition_variable cv_done;   // a request finished
-    std::condition_variable cv_work;   // new submission or shutdown
+    std::condition_variable cv_work;   // new submission, release or shutdown
     std::deque<Request *> queue;
-    std::vector<Request *> running;
+    std::vector<Request *> active;     // admitted, not yet finished
+    std::vector<Slice> slices;         // enqueued slices, oldest first
     std::unordered_map<uint64_t, Request *> all;
-    std::vector<std::vector<cudaStream_t>> streams;   // idle streams per priority class
-    int prio_greatest = 0;     // CUDA priority of class 0 (numerically lowest)
-    int levels = 1;
-    std::vector<cudaEvent_t> events;
+    std::vector<cudaStream_t> streams;       // idle streams
+    std::vector<cudaEvent_t> done_events;    // idle completion events
+    std::vector<cudaEvent_t> timing_events;  // idle slice events
+    cudaEvent_t last_end = nullptr;    // end of the last slice seen complete
     std::vector<rosen_stats *> pinned;
+    std::map<uint64_t, double> rate;   // GPU ns per chain by request class
     size_t used = 0;
     std::vector<std::pair<void *, size_t>> to_free;   // released conformations
     cudaStream_t free_stream = nullptr;
@@ -121,12 +173,19 @@ size_t long_workspace_bytes(const rosen_request &r)
     return align256(std::max(one, std::min(want, kLongWorkspaceCap)));
 }
 
+// Real-space chain counters and deferral mask (shared-memory kernels).
+size_t scratch_bytes(const rosen_request &r)
+{
+    if (r.model != ROSEN_MODEL_OFFLATTICE || long_request(r)) return 0;
+    return align256(offlattice_range_scratch_bytes(r.C));
+}
+
 // Device bytes a request holds while it runs, and what stored conformations
 // keep after it finishes.
 void request_bytes(const rosen_request &r, size_t *work, size_t *coords)
 {
     const size_t C = (size_t)r.C, N = (size_t)r.N;
-    size_t b = long_workspace_bytes(r);
+    size_t b = long_workspace_bytes(r) + scratch_bytes(r);
     if (r.model == ROSEN_MODEL_LATTICE)
         b += align256(16 * C) + align256(4 * C) + align256(4 * C) + align256(8 * C);
     else
@@ -137,18 +196,24 @@ void request_bytes(const rosen_request &r, size_t *work, size_t *coords)
     *coords = r.store_coords ? align256(12 * N * C) : 0;
 }
 
-// Priority class of a request (shortest_first): decades of its pair tests
-// (chains x (N-1)(N-2)/2 x trials per step), class 0 -- the highest priority,
-// well under a millisecond of GPU time -- below 1e8, up to the last class.
-int work_level(const rosen_request &r, int levels)
+// Class of a request for the GPU-time estimate: model, potential, trials,
+// chain-length bucket of 16.
+uint64_t rate_key(const rosen_request &r)
 {
-    const double n = (double)r.N;
-    const double pairs = (double)r.C * (n - 1.0) * (n - 2.0) * 0.5 *
-                         (r.model == ROSEN_MODEL_LATTICE ? 1.0 : (double)r.k);
-    int level = pairs < 1.0 ? 0 : (int)floor(log10(pairs)) - 7;
-    if (level < 0) level = 0;
-    if (level > levels - 1) level = levels - 1;
-    return level;
+    return ((uint64_t)r.model << 56) | ((uint64_t)(r.potential & 0xFF) << 48) |
+           ((uint64_t)(r.k & 0xFFFF) << 32) | (uint64_t)(r.N / 16);
+}
+
+// First estimate of a class's GPU time per chain (ns), from GB300 timings of
+// the single-ensemble kernels at N = 64 (lattice 1.2 ns, hard spheres 0.55 k,
+// Lennard-Jones 1.8 k per chain) scaled by N^2; refined by measured slices.
+double default_ns_per_chain(const rosen_request &r)
+{
+    const double f = ((double)r.N / 64.0) * ((double)r.N / 64.0);
+    double base;
+    if (r.model == ROSEN_MODEL_LATTICE) base = 1.2;
+    else base = (r.potential == ROSEN_LJ ? 1.8 : 0.55) * (double)r.k;
+    return std::max(0.05, base * f);
 }
 
 int validate_request(const rosen_request &r)
@@ -196,37 +261,24 @@ void fail(Request *q, int status, const char *msg)
     snprintf(q->message, sizeof q->message, "%s", msg);
 }
 
-// Return a failed request's scratch to the pool (stream-ordered).
-void release_work(Request *q)
-{
-    if (q->work) cudaFreeAsync(q->work, q->stream);
-    q->work = nullptr;
-}
-
-// Enqueue a request's whole pass on its stream (scheduler thread, lock held).
-void launch(rosen_server *s, Request *q)
+// Pointers of a request's outputs and scratch inside its work allocation.
+void carve(Request *q)
 {
     const rosen_request &r = q->req;
     const size_t C = (size_t)r.C;
-    cudaError_t e = cudaMallocFromPoolAsync(&q->work, q->work_bytes, s->pool, q->stream);
-    if (e == cudaSuccess && q->coord_bytes)
-        e = cudaMallocFromPoolAsync(&q->coords, q->coord_bytes, s->pool, q->stream);
-    if (e != cudaSuccess) {
-        fail(q, ROSEN_ENOMEM, cudaGetErrorString(e));
-        release_work(q);
-        return;
-    }
     unsigned char *p = static_cast<unsigned char *>(q->work);
-    const size_t long_bytes = long_workspace_bytes(r);
-    void *long_ws = long_bytes ? p : nullptr;   // long chains: their workspace first
-    p += long_bytes;
-    rosen_reduce_in in;
+    q->long_bytes = long_workspace_bytes(r);
+    q->long_ws = q->long_bytes ? p : nullptr;   // long chains: their workspace first
+    p += q->long_bytes;
+    const size_t sb = scratch_bytes(r);
+    q->scratch = sb ? p : nullptr;
+    p += sb;
+    rosen_reduce_in &in = q->rin;
     memset(&in, 0, sizeof in);
     in.N = r.N;
     in.C = r.C;
-    int st;
     if (r.model == ROSEN_MODEL_LATTICE) {
-        rosen_lattice_out o;
+        rosen_lattice_out &o = q->lo;
         memset(&o, 0, sizeof o);
         o.counts = reinterpret_cast<uint16_t *>(p);
         p += align256(16 * C);
@@ -241,7 +293,7 @@ void launch(rosen_server *s, Request *q)
             p += align256(2 * C);
         }
         o.coords = static_cast<int32_t *>(q->coords);
-        rosen_lattice_params lp;
+        rosen_lattice_params &lp = q->lp;
         memset(&lp, 0, sizeof lp);
         lp.seed = r.seed;
         lp.ensemble = r.ensemble;
@@ -250,8 +302,6 @@ void launch(rosen_server *s, Request *q)
         lp.beta_eps = r.beta_eps;
         lp.flags = q->coords ? ROSEN_STORE_COORDS : 0;
         lp.max_attempts = r.max_attempts;
-        st = long_ws ? rosen_lattice_grow_long(&lp, &o, long_ws, long_bytes, q->stream)
-                     : rosen_lattice_grow(&lp, &o, q->stream);
         in.attempts = o.attempts;
         in.kind = ROSEN_REDUCE_LATTICE;
         in.use_counts = r.beta_eps == 0.0;
@@ -260,7 +310,7 @@ void launch(rosen_server *s, Request *q)
         in.r2_i = o.r2;
         in.n2rg2 = o.n2rg2;
     } else {
-        rosen_offlattice_out o;
+        rosen_offlattice_out &o = q->oo;
         memset(&o, 0, sizeof o);
         o.logw = reinterpret_cast<float *>(p);
         p += align256(4 * C);
@@ -275,7 +325,7 @@ void launch(rosen_server *s, Request *q)
             p += align256(2 * C);
         }
         o.coords = static_cast<float *>(q->coords);
-        rosen_offlattice_params op;
+        rosen_offlattice_params &op = q->op;
         memset(&op, 0, sizeof op);
         op.seed = r.seed;
         op.ensemble = r.ensemble;
@@ -288,8 +338,6 @@ void launch(rosen_server *s, Request *q)
         op.beta_eps = r.beta_eps;
         op.flags = q->coords ? ROSEN_STORE_COORDS : 0;
         op.max_attempts = r.max_attempts;
-        st = long_ws ? rosen_offlattice_grow_long(&op, &o, long_ws, long_bytes, q->stream)
-                     : rosen_offlattice_grow(&op, &o, q->stream);
         in.attempts = o.attempts;
         in.kind = ROSEN_REDUCE_OFFLATTICE;
         in.k = r.k;
@@ -297,22 +345,316 @@ void launch(rosen_server *s, Request *q)
         in.r2_f = o.r2;
         in.rg2_f = o.rg2;
     }
-    rosen_stats *dstats = reinterpret_cast<rosen_stats *>(p);
+    q->dstats = reinterpret_cast<rosen_stats *>(p);
     p += align256(sizeof(rosen_stats));
-    const size_t ws = rosen_reduce_workspace_size(r.C);
-    if (st == ROSEN_OK) st = rosen_reduce(&in, dstats, p, ws, q->stream);
+    q->rws = p;
+    q->rws_bytes = rosen_reduce_workspace_size(r.C);
+}
+
+cudaEvent_t take_event(std::vector<cudaEvent_t> &pool, unsigned flags)
+{
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, flags) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Resources of a request that is no longer on the GPU go back to the pools.
+void retire(rosen_server *s, Request *q)
+{
+    if (q->stream) s->streams.push_back(q->stream);
+    if (q->done) s->done_events.push_back(q->done);
+    if (q->host_stats) s->pinned.push_back(q->host_stats);
+    q->stream = nullptr;
+    q->done = nullptr;
+    q->host_stats = nullptr;
+}
+
+// Admit q (lock held): stream, completion event, pinned statistics, device
+// memory from the pool, and the set-up of its scratch.  A request whose
+// memory cannot be had fails at once and gives its reservation back.
+bool admit(rosen_server *s, Request *q)
+{
+    if (s->streams.empty()) {
+        cudaStream_t st = nullptr;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return false;     // stays queued; retried at the next pass
+        }
+        s->streams.push_back(st);
+    }
+    cudaEvent_t done = take_event(s->done_events, cudaEventDisableTiming);
+    if (!done) return false;
+    if (s->pinned.empty()) {
+        rosen_stats *h = nullptr;
+        if (cudaMallocHost(reinterpret_cast<void **>(&h), sizeof(rosen_stats)) != cudaSuccess) {
+            cudaGetLastError();
+            s->done_events.push_back(done);
+            return false;
+        }
+        s->pinned.push_back(h);
+    }
+    q->stream = s->streams.back();
+    s->streams.pop_back();
+    q->done = done;
+    q->host_stats = s->pinned.back();
+    s->pinned.pop_back();
+    q->state = RUNNING;
+    q->t_admit = now_ns();
+    const uint64_t key = rate_key(q->req);
+    auto it = s->rate.find(key);
+    q->ns_per_chain = it != s->rate.end() ? it->second : default_ns_per_chain(q->req);
+
+    cudaError_t e = cudaMallocFromPoolAsync(&q->work, q->work_bytes, s->pool, q->stream);
+    if (e == cudaSuccess && q->coord_bytes)
+        e = cudaMallocFromPoolAsync(&q->coords, q->coord_bytes, s->pool, q->stream);
+    if (e == cudaSuccess) {
+        carve(q);
+        if (q->scratch)
+            e = cudaMemsetAsync(q->scratch, 0, scratch_bytes(q->req), q->stream);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(q, ROSEN_ENOMEM, cudaGetErrorString(e));
+        if (q->work) cudaFreeAsync(q->work, q->stream);
+        if (q->coords) cudaFreeAsync(q->coords, q->stream);
+        q->work = q->coords = nullptr;
+        cudaGetLastError();
+        q->t_done = now_ns();
+        ++s->n_failed;
+        retire(s, q);
+        s->cv_done.notify_all();
+        return true;          // taken off the queue, finished (failed)
+    }
+    s->used += q->work_bytes + q->coord_bytes;
+    s->active.push_back(q);
+    return true;
+}
+
+// Enqueue the end of a request on its stream: the reduction, the copy of the
+// statistics, the release of its scratch and the completion event.  After a
+// failure only the release and the event (so its in-flight slices finish
+// before its memory is reused).
+void finish(Request *q)
+{
+    q->finishing = true;
+    int st = ROSEN_OK;
+    if (q->state != FAILED) {
+        st = rosen_reduce(&q->rin, q->dstats, q->rws, q->rws_bytes, q->stream);
+        if (st == ROSEN_OK &&
+            cudaMemcpyAsync(q->host_stats, q->dstats, sizeof(rosen_stats), cudaMemcpyDeviceToHost,
+                            q->stream) != cudaSuccess)
+            st = set_error(ROSEN_ECUDA, "copying the statistics: %s",
+                           cudaGetErrorString(cudaGetLastError()));
+        if (st != ROSEN_OK) fail(q, st, rosen_last_error());
+    }
+    // The outputs are scratch once the statistics are copied; conformations stay.
+    if (q->work) cudaFreeAsync(q->work, q->stream);
+    q->work = nullptr;
+    if (cudaEventRecord(q->done, q->stream) != cudaSuccess) {
+        // Without the event the stream is synchronised here instead.
+        cudaGetLastError();
+        cudaStreamSynchronize(q->stream);
+        cudaEventRecord(q->done, 0);
+    }
+}
+
+// Enqueue the next slice of q: chains [next_chain, next_chain + n), or the
+// whole request for long chains.  Slices start at multiples of 32 chains
+// (the deferral mask's words).
+void launch_slice(rosen_server *s, Request *q)
+{
+    const int64_t C = q->req.C;
+    int64_t n = C - q->next_chain;
+    if (!q->long_ws) {
+        const double per = std::max(q->ns_per_chain, 1e-3);
+        int64_t want = (int64_t)((double)kSliceNs / per);
+        want = std::max<int64_t>(32, (want + 31) / 32 * 32);
+        if (n - want >= want / 2) n = want;   // else: the remainder in one slice
+    }
+    Slice sl;
+    sl.q = q;
+    sl.chains = n;
+    sl.est_ns = (double)n * q->ns_per_chain;
+    sl.start = take_event(s->timing_events, cudaEventDefault);
+    sl.end = take_event(s->timing_events, cudaEventDefault);
+    int st = ROSEN_OK;
+    if (sl.start) cudaEventRecord(sl.start, q->stream);
+    const int64_t c_lo = q->next_chain, c_hi = c_lo + n;
+    if (q->long_ws) {
+        st = q->req.model == ROSEN_MODEL_LATTICE
+                 ? rosen_lattice_grow_long(&q->lp, &q->lo, q->long_ws, q->long_bytes, q->stream)
+                 : rosen_offlattice_grow_long(&q->op, &q->oo, q->long_ws, q->long_bytes, q->stream);
+    } else if (q->req.model == ROSEN_MODEL_LATTICE) {
+        st = lattice_grow_range(&q->lp, &q->lo, c_lo, c_hi, q->stream);
+    } else {
+        st = offlattice_grow_range(&q->op, &q->oo, c_lo, c_hi, q->scratch, q->stream);
+    }
+    if (sl.end) cudaEventRecord(sl.end, q->stream);
+    q->next_chain = c_hi;
     if (st != ROSEN_OK) {
         fail(q, st, rosen_last_error());
-        release_work(q);
-        return;
+        q->next_chain = C;
     }
-    e = cudaMemcpyAsync(q->host_stats, dstats, sizeof(rosen_stats), cudaMemcpyDeviceToHost,
-                        q->stream);
-    // The outputs are scratch once the statistics are copied; conformations stay.
-    if (e == cudaSuccess) e = cudaFreeAsync(q->work, q->stream);
-    q->work = nullptr;
-    if (e == cudaSuccess) e = cudaEventRecord(q->done, q->stream);
-    if (e != cudaSuccess) fail(q, ROSEN_ECUDA, cudaGetErrorString(e));
+    if (sl.start && sl.end) {
+        ++q->inflight;
+        s->slices.push_back(sl);
+    } else {
+        if (sl.start) s->timing_events.push_back(sl.start);
+        if (sl.end) s->timing_events.push_back(sl.end);
+    }
+    if (q->next_chain >= C) finish(q);
+}
+
+// The request whose slice goes next: the oldest (arrival order), or the one
+// with the least estimated remaining GPU time divided by 1 + its waiting
+// time in seconds (shortest_first).  At most two slices of one request are
+// enqueued at once.
+Request *pick(rosen_server *s, int64_t now)
+{
+    Request *best = nullptr;
+    double best_key = 0.0;
+    for (Request *q : s->active) {
+        if (q->finishing || q->inflight >= 2 || q->next_chain >= q->req.C) continue;
+        double key;
+        if (s->cfg.shortest_first) {
+            const double rem = (double)(q->req.C - q->next_chain) * q->ns_per_chain;
+            key = rem / (1.0 + (double)(now - q->t_submit) / kAgingNs);
+        } else {
+            key = (double)q->t_submit;
+        }
+        if (!best || key < best_key) {
+            best = q;
+            best_key = key;
+        }
+    }
+    return best;
+}
+
+// Completed slices (oldest first): refine the GPU-time estimates.  A slice's
+// own time is measured from the later of its start and the end of the slice
+// completed before it, so the time it spent queued behind another slice is
+// not counted.
+bool reap_slices(rosen_server *s)
+{
+    bool progressed = false;
+    for (size_t i = 0; i < s->slices.size();) {
+        Slice &sl = s->slices[i];
+        const cudaError_t e = cudaEventQuery(sl.end);
+        if (e == cudaErrorNotReady) {
+            ++i;
+            continue;
+        }
+        Request *q = sl.q;
+        if (e == cudaSuccess) {
+            float ms = 0.f, since = -1.f;
+            if (cudaEventElapsedTime(&ms, sl.start, sl.end) != cudaSuccess) ms = -1.f;
+            if (s->last_end && cudaEventElapsedTime(&since, s->last_end, sl.end) != cudaSuccess)
+                since = -1.f;
+            cudaGetLastError();
+            float own = ms;
+            if (since >= 0.f && since < own) own = since;
+            if (own > 0.f && sl.chains > 0) {
+                const double per = (double)own * 1e6 / (double)sl.chains;
+                q->ns_per_chain = 0.5 * q->ns_per_chain + 0.5 * per;
+                const uint64_t key = rate_key(q->req);
+                auto it = s->rate.find(key);
+                s->rate[key] = it == s->rate.end() ? per : 0.8 * it->second + 0.2 * per;
+            }
+            if (s->last_end) s->timing_events.push_back(s->last_end);
+            s->last_end = sl.end;
+            s->timing_events.push_back(sl.start);
+        } else {
+            cudaGetLastError();
+            if (q->state != FAILED) fail(q, ROSEN_ECUDA, cudaGetErrorString(e));
+            s->timing_events.push_back(sl.start);
+            s->timing_events.push_back(sl.end);
+        }
+        --q->inflight;
+        s->slices.erase(s->slices.begin() + (ptrdiff_t)i);
+        progressed = true;
+    }
+    return progressed;
+}
+
+// Requests whose completion event has fired.
+bool reap_requests(rosen_server *s)
+{
+    bool progressed = false;
+    for (size_t i = 0; i < s->active.size();) {
+        Request *q = s->active[i];
+        if (!q->finishing || q->inflight > 0) {
+            ++i;
+            continue;
+        }
+        const cudaError_t e = cudaEventQuery(q->done);
+        if (e == cudaErrorNotReady) {
+            ++i;
+            continue;
+        }
+        if (q->state != FAILED) {
+            if (e == cudaSuccess) {
+                q->stats = *q->host_stats;
+                q->state = DONE;
+                ++s->n_done;
+            } else {
+                cudaGetLastError();
+                fail(q, ROSEN_ECUDA, cudaGetErrorString(e));
+            }
+        }
+        if (q->state == FAILED) {
+            ++s->n_failed;
+            // A failed request gives back everything it reserved.
+            if (q->coords) cudaFreeAsync(q->coords, q->stream);
+            q->coords = nullptr;
+            s->used -= q->coord_bytes;
+        }
+        s->used -= q->work_bytes;
+        q->t_done = now_ns();
+        retire(s, q);
+        s->active[i] = s->active.back();
+        s->active.pop_back();
+        progressed = true;
+    }
+    return progressed;
+}
+
+// Admissions in arrival order; a request that does not fit the budget may be
+// passed by later ones for at most kPassLimitNs, then nothing behind it is
+// admitted until it fits.
+bool admit_waiting(rosen_server *s, int64_t now)
+{
+    bool progressed = false;
+    for (auto it = s->queue.begin();
+         it != s->queue.end() && !s->stop && (int)s->active.size() < s->cfg.max_slots;) {
+        Request *q = *it;
+        if (q->state == CANCELLED) {
+            it = s->queue.erase(it);
+            q->in_queue = false;
+            if (q->released) delete q;
+            progressed = true;
+            continue;
+        }
+        const size_t need = q->work_bytes + q->coord_bytes;
+        if (s->used + need > s->cfg.mem_budget_bytes) {
+            if (q->t_passed == 0) q->t_passed = now;
+            if (now - q->t_passed > kPassLimitNs) break;
+            ++it;
+            continue;
+        }
+        if (!admit(s, q)) break;
+        it = s->queue.erase(it);
+        q->in_queue = false;
+        progressed = true;
+    }
+    return progressed;
 }
 
 void scheduler(rosen_server *s)
@@ -328,87 +670,32 @@ void scheduler(rosen_server *s)
             progressed = true;
         }
         s->to_free.clear();
-        // Completions.
-        for (size_t i = 0; i < s->running.size();) {
-            Request *q = s->running[i];
-            const cudaError_t e = (q->state == FAILED) ? cudaSuccess : cudaEventQuery(q->done);
-            if (e == cudaErrorNotReady) {
-                ++i;
-                continue;
-            }
-            if (q->state != FAILED) {
-                if (e == cudaSuccess) {
-                    q->stats = *q->host_stats;
-                    q->state = DONE;
-                    ++s->n_done;
-                } else {
-                    fail(q, ROSEN_ECUDA, cudaGetErrorString(e));
-                }
-            }
-            if (q->state == FAILED) ++s->n_failed;
-            q->t_done = now_ns();
-            s->used -= q->work_bytes;
-            if (q->state == FAILED) {
-                // A failed request gives back everything it reserved, whether
-                // or not its conformations were ever allocated.
-                if (q->coords) cudaFreeAsync(q->coords, q->stream);
-                q->coords = nullptr;
-                s->used -= q->coord_bytes;
-            }
-            s->streams[q->level].push_back(q->stream);
-            s->events.push_back(q->done);
-            s->pinned.push_back(q->host_stats);
-            q->stream = nullptr;
-            q->done = nullptr;
-            q->host_stats = nullptr;
-            s->running[i] = s->running.back();
-            s->running.pop_back();
+        progressed |= reap_slices(s);
+        if (reap_requests(s)) {
+            progressed = true;
+            s->cv_done.notify_all();
+        }
+        const int64_t now = now_ns();
+        if (admit_waiting(s, now)) {
+            progressed = true;
+            s->cv_done.notify_all();   // requests that failed at admission
+        }
+        // Slices: keep about kLookaheadNs of estimated work enqueued.
+        double queued = 0.0;
+        for (const Slice &sl : s->slices) queued += sl.est_ns;
+        while ((int)s->slices.size() < kMaxInflight && queued < (double)kLookaheadNs) {
+            Request *q = pick(s, now);
+            if (!q) break;
+            const size_t before = s->slices.size();
+            launch_slice(s, q);
+            if (s->slices.size() > before) queued += s->slices.back().est_ns;
             progressed = true;
         }
-        if (progressed) s->cv_done.notify_all();
-        // Admissions, in arrival order.
-        while (!s->stop && !s->queue.empty() && (int)s->running.size() < s->cfg.max_slots) {
-            Request *q = s->queue.front();
-            if (q->state == CANCELLED) {
-                s->queue.pop_front();
-                q->in_queue = false;
-                if (q->released) delete q;
-                continue;
-            }
-            const size_t need = q->work_bytes + q->coord_bytes;
-            if (s->used + need > s->cfg.mem_budget_bytes) break;
-            // A stream of the request's priority class (created on first use;
-            // at most max_slots per class are ever in use).
-            std::vector<cudaStream_t> &idle = s->streams[q->level];
-            if (idle.empty()) {
-                cudaStream_t st;
-                if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking,
-                                                 s->prio_greatest + q->level) != cudaSuccess) {
-                    cudaGetLastError();
-                    break;   // the request stays queued; retried at the next pass
-                }
-                idle.push_back(st);
-            }
-            s->queue.pop_front();
-            q->in_queue = false;
-            s->used += need;
-            q->stream = idle.back();
-            idle.pop_back();
-            q->done = s->events.back();
-            s->events.pop_back();
-            q->host_stats = s->pinned.back();
-            s->pinned.pop_back();
-            q->state = RUNNING;
-            q->t_admit = now_ns();
-            launch(s, q);
-            s->running.push_back(q);
-            progressed = true;
-        }
-        if (s->stop && s->running.empty()) break;
+        if (s->stop && s->active.empty()) break;
         if (!progressed) {
             // Nothing to do right now: sleep until a submission arrives, or
             // briefly while work is on the GPU.
-            if (s->running.empty())
+            if (s->active.empty())
                 s->cv_work.wait_for(lock, std::chrono::milliseconds(50));
             else {
                 lock.unlock();
@@ -432,6 +719,17 @@ void fill_result(const Request *q, rosen_result *out)
     snprintf(out->message, sizeof out->message, "%s", q->message);
 }
 
+void destroy_resources(rosen_server *s)
+{
+    if (s->free_stream) cudaStreamDestroy(s->free_stream);
+    for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : s->done_events) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : s->timing_events) cudaEventDestroy(ev);
+    if (s->last_end) cudaEventDestroy(s->last_end);
+    for (rosen_stats *h : s->pinned) cudaFreeHost(h);
+    if (s->pool) cudaMemPoolDestroy(s->pool);
+}
+
 }  // namespace
 
 extern "C" int rosen_serve_create(const rosen_serve_config *cfg, rosen_server **out)
@@ -450,34 +748,15 @@ extern "C" int rosen_serve_create(const rosen_serve_config *cfg, rosen_server **
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
     props.location.id = s->device;
+    props.maxSize = (size_t)cfg->pool_max_bytes;   // 0: no cap
     if (e == cudaSuccess) e = cudaMemPoolCreate(&s->pool, &props);
     if (e == cudaSuccess) {
         uint64_t keep = cfg->mem_budget_bytes;   // keep freed blocks for reuse up to the budget
         e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->free_stream, cudaStreamNonBlocking);
-    int least = 0, greatest = 0;
-    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-    // Without shortest_first every stream has the default priority.
-    s->prio_greatest = cfg->shortest_first ? greatest : 0;
-    s->levels = cfg->shortest_first ? least - greatest + 1 : 1;
-    if (s->levels < 1) s->levels = 1;
-    s->streams.resize((size_t)s->levels);
-    for (int i = 0; e == cudaSuccess && i < cfg->max_slots; ++i) {
-        cudaEvent_t ev;
-        rosen_stats *h;
-        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void **>(&h), sizeof(rosen_stats));
-        if (e == cudaSuccess) {
-            s->events.push_back(ev);
-            s->pinned.push_back(h);
-        }
-    }
     if (e != cudaSuccess) {
-        if (s->free_stream) cudaStreamDestroy(s->free_stream);
-        for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
-        for (rosen_stats *h : s->pinned) cudaFreeHost(h);
-        if (s->pool) cudaMemPoolDestroy(s->pool);
+        destroy_resources(s);
         delete s;
         return set_error(ROSEN_ECUDA, "rosen_serve_create: %s", cudaGetErrorString(e));
     }
@@ -494,7 +773,6 @@ extern "C" int rosen_serve_submit(rosen_server *s, const rosen_request *r, uint6
     Request *q = new Request();
     q->req = *r;
     request_bytes(*r, &q->work_bytes, &q->coord_bytes);
-    q->level = work_level(*r, s->levels);
     std::lock_guard<std::mutex> lock(s->mu);
     if (s->stop) {
         delete q;
@@ -607,7 +885,7 @@ extern "C" int rosen_serve_info(rosen_server *s, rosen_serve_counters *out)
     out->completed = s->n_done;
     out->failed = s->n_failed;
     out->queued = s->queue.size();
-    out->running = s->running.size();
+    out->running = s->active.size();
     out->bytes_in_use = s->used;
     return ROSEN_OK;
 }
@@ -635,12 +913,7 @@ extern "C" int rosen_serve_destroy(rosen_server *s)
     }
     for (auto &f : s->to_free) cudaFreeAsync(f.first, s->free_stream);
     cudaStreamSynchronize(s->free_stream);
-    cudaStreamDestroy(s->free_stream);
-    for (auto &pool : s->streams)
-        for (cudaStream_t st : pool) cudaStreamDestroy(st);
-    for (cudaEvent_t ev : s->events) cudaEventDestroy(ev);
-    for (rosen_stats *h : s->pinned) cudaFreeHost(h);
-    cudaMemPoolDestroy(s->pool);
+    destroy_resources(s);
     delete s;
     return ROSEN_OK;
 }

@@ -487,7 +487,7 @@ class rosen_stats_t(ctypes.Structure):
 class rosen_serve_config(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
                 ("max_queue", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("shortest_first", ctypes.c_int32)]
+                ("shortest_first", ctypes.c_int32), ("pool_max_bytes", ctypes.c_uint64)]
 
 
 class rosen_request(ctypes.Structure):
@@ -572,10 +572,11 @@ class RosenServer:
     """The request loop (rosen_serve_*): submit, poll/wait, release."""
 
     def __init__(self, mem_budget_bytes, max_slots=32, max_queue=4096, device=0,
-                 shortest_first=False):
+                 shortest_first=False, pool_max_bytes=0):
         cfg = rosen_serve_config(mem_budget_bytes=int(mem_budget_bytes), max_slots=int(max_slots),
                                  max_queue=int(max_queue), device=int(device),
-                                 shortest_first=int(bool(shortest_first)))
+                                 shortest_first=int(bool(shortest_first)),
+                                 pool_max_bytes=int(pool_max_bytes))
         h = _vp()
         _check(_serve_lib().rosen_serve_create(ctypes.byref(cfg), ctypes.byref(h)))
         self.handle = h

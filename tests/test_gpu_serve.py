@@ -218,3 +218,89 @@ def test_served_results_match_the_oracle(rosen):
             assert srv.release(t) == rosen.ROSEN_OK
     finally:
         srv.close()
+
+
+def test_time_slices_let_a_small_request_pass_a_large_one(rosen):
+    # A large request is grown in slices of a few milliseconds; with the
+    # shortest-remaining-work policy a small request submitted while it runs
+    # gets the next slice and finishes first.  Both results equal those of
+    # the requests served alone, bit for bit.
+    L, R = rosen.ROSEN_MODEL_LATTICE, rosen.ROSEN_MODEL_OFFLATTICE
+    big = rosen.request(R, 64, 2_000_000, 31, 0, k=32)
+    small = rosen.request(L, 32, 1000, 32, 1, beta_eps=0.2)
+    srv = rosen.RosenServer(mem_budget_bytes=4 << 30, max_slots=8, shortest_first=True)
+    try:
+        alone = {}
+        for name, r in (("big", big), ("small", small)):
+            st, res = srv.wait(srv.submit(r), 120)
+            assert st == rosen.ROSEN_OK and res["status"] == rosen.ROSEN_OK
+            alone[name] = res["stats"]
+        tb = srv.submit(big)
+        deadline = time.time() + 10
+        while srv.info()["running"] < 1 and time.time() < deadline:
+            time.sleep(0.0005)
+        time.sleep(0.01)                    # the large request is on the GPU
+        ts = srv.submit(small)
+        st_s, rs = srv.wait(ts, 120)
+        st_b, rb = srv.wait(tb, 120)
+        assert st_s == st_b == rosen.ROSEN_OK
+        assert rs["stats"] == alone["small"] and rb["stats"] == alone["big"]
+        assert rs["t_done_ns"] < rb["t_done_ns"]
+        # The small request waited about a slice or two, not the large one's time.
+        assert rs["t_done_ns"] - rs["t_submit_ns"] < 0.5 * (rb["t_done_ns"] - rb["t_admit_ns"])
+    finally:
+        srv.close()
+
+
+def test_admission_passes_a_request_that_does_not_fit(rosen):
+    # A request that does not fit the budget next to a running one may be
+    # passed by a later request that does fit; it is admitted once memory
+    # frees up.
+    L, R = rosen.ROSEN_MODEL_LATTICE, rosen.ROSEN_MODEL_OFFLATTICE
+    a = rosen.request(R, 256, 20_000, 41, 0, k=32, potential=rosen.ROSEN_LJ, beta_eps=0.5,
+                      store_coords=True)                       # ~62 MB, tens of ms
+    b = rosen.request(L, 128, 60_000, 42, 1, store_coords=True)   # ~94 MB
+    c = rosen.request(L, 32, 1000, 43, 2)                          # < 1 MB
+    srv = rosen.RosenServer(mem_budget_bytes=150 << 20, max_slots=8)
+    try:
+        ta = srv.submit(a)
+        deadline = time.time() + 10
+        while srv.info()["running"] < 1 and time.time() < deadline:
+            time.sleep(0.0005)
+        tb = srv.submit(b)
+        tc = srv.submit(c)
+        res = {}
+        for name, t in (("a", ta), ("b", tb), ("c", tc)):
+            st, r = srv.wait(t, 120)
+            assert st == rosen.ROSEN_OK and r["status"] == rosen.ROSEN_OK, r
+            res[name] = r
+        assert res["c"]["t_admit_ns"] < res["b"]["t_admit_ns"]     # c passed b
+        assert res["b"]["t_admit_ns"] >= res["a"]["t_done_ns"] - 2_000_000
+        for t in (ta, tb, tc):
+            srv.release(t)
+        time.sleep(0.05)
+        assert srv.info()["bytes_in_use"] == 0
+    finally:
+        srv.close()
+
+
+def test_pool_failure_returns_the_reservation(rosen):
+    # The server's pool is capped below what a request needs while the budget
+    # admits it: its allocation fails on the host (ROSEN_ENOMEM, no GPU work),
+    # its reservation goes back to the budget, and later requests still run.
+    L = rosen.ROSEN_MODEL_LATTICE
+    srv = rosen.RosenServer(mem_budget_bytes=1 << 30, max_slots=4, pool_max_bytes=32 << 20)
+    try:
+        big = rosen.request(L, 64, 100, 51, 0, store_coords=True)
+        big.C = 200_000                     # 12 B x 64 x 2e5 = 154 MB of conformations
+        for _ in range(3):
+            st, res = srv.wait(srv.submit(big), 60)
+            assert st == rosen.ROSEN_OK and res["status"] == rosen.ROSEN_ENOMEM, res
+        info = srv.info()
+        assert info["failed"] == 3 and info["bytes_in_use"] == 0
+        small = rosen.request(L, 32, 2000, 52, 1)
+        st, res = srv.wait(srv.submit(small), 60)
+        assert st == rosen.ROSEN_OK and res["status"] == rosen.ROSEN_OK
+        assert srv.info()["bytes_in_use"] == 0
+    finally:
+        srv.close()
