@@ -65,6 +65,11 @@ def lib():
         L.orc_reduce_n.restype = None
         L.orc_enumerate.argtypes = [ctypes.c_int, i64p, i64p, i64p]
         L.orc_enumerate.restype = ctypes.c_int
+        L.orc_perm_run.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                   ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
+                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, i64p,
+                                   f64p, f64p, i64p, f64p, i32p, i32p]
+        L.orc_perm_run.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -206,3 +211,39 @@ def enumerate_saw(nmax):
     if rc != 0:
         raise ValueError("nmax out of range")
     return cnt, sr2, sg2
+
+
+def perm_run(seed, N, M0, max_pop=None, beta_eps=0.0, mu=4.684, c_hi=3.0, c_lo=1.0 / 3.0,
+             ensemble=0, positions=False):
+    """Breadth-first PERM on the cubic lattice (pruned-enriched Rosenbluth
+    growth; Grassberger, Phys. Rev. E 56, 3682 (1997)): a population of M0
+    chains grows step by step; after step i a chain with W > c_hi mu^i is
+    enriched (two copies sharing W), one with W < c_lo mu^i is pruned (kept
+    with probability 1/2 with 2W), within a population cap max_pop.
+
+    Returns pop [N] (population after each step), logz [N] (log of Eq. 9's
+    estimate of Z_i from the chains grown at step i), r2 [N] (their
+    W-weighted <R_ee^2>), and the final population: w_m, w_e (W = w_m 2^w_e)
+    and, with positions, pos [n, N, 3].
+    """
+    max_pop = int(max_pop or 4 * M0)
+    pop = np.zeros(N, np.int64)
+    logz = np.zeros(N, np.float64)
+    r2 = np.zeros(N, np.float64)
+    fn = np.zeros(1, np.int64)
+    w_m = np.zeros(max_pop, np.float64)
+    w_e = np.zeros(max_pop, np.int32)
+    pos = np.zeros((max_pop, N, 3), np.int32) if positions else None
+    rc = lib().orc_perm_run(int(seed), int(ensemble), int(N), float(beta_eps), int(M0),
+                            int(max_pop), float(mu), float(c_hi), float(c_lo),
+                            _ptr(pop, ctypes.c_int64), _ptr(logz, ctypes.c_double),
+                            _ptr(r2, ctypes.c_double), _ptr(fn, ctypes.c_int64),
+                            _ptr(w_m, ctypes.c_double), _ptr(w_e, ctypes.c_int32),
+                            _ptr(pos, ctypes.c_int32))
+    if rc != 0:
+        raise ValueError("perm_run: bad arguments")
+    n = int(fn[0])
+    out = {"pop": pop, "logz": logz, "r2": r2, "n": n, "w_m": w_m[:n], "w_e": w_e[:n]}
+    if positions:
+        out["pos"] = pos[:n]
+    return out

@@ -36,6 +36,10 @@
  *                          attempt law, E[W] and <R^2>) and the exact c_n
  *   orc_reduce             pinned against exact rational sums
  *   orc_enumerate          pinned against brute force over all 6^n walks
+ *   orc_perm_run           pinned by exact reduction to orc_lattice_run
+ *                          without thresholds, and by the exact c_n (n <= 12)
+ *                          and Z_n(beta eps) (n <= 10) that its mean estimate
+ *                          must equal with pruning and enrichment active
  */
 #include <math.h>
 #include <pthread.h>
@@ -771,5 +775,271 @@ ORC_EXPORT int orc_enumerate(int nmax, int64_t *cnt, int64_t *sr2, int64_t *sg2)
     dfs(&E, 0, 0, 0, 0, 0, 0);
     free(E.occ);
     free(E.path);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* PERM: pruned-enriched Rosenbluth growth, breadth first.              */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper's conclusion names a GPU PERM; its text is not available, so
+ * this follows the published method (Grassberger, Phys. Rev. E 56, 3682
+ * (1997)): Rosenbluth growth in which a chain whose weight has grown well
+ * above the typical weight of its length is copied (enrichment, the copies
+ * share its weight) and a chain whose weight has fallen well below it is
+ * removed with probability 1/2, its weight doubled if it survives (pruning).
+ * Both keep the expected total weight of every length unchanged, so the
+ * mean weight over the tours started is still an unbiased estimate of Z_n
+ * (Eq. 9) and W-weighted means are still those of Eq. 2.
+ *
+ * Readings (the listing is not available):
+ *  - Breadth first: all chains grow step i together, as one population,
+ *    instead of Grassberger's depth-first recursion.  The expectations are
+ *    the same.
+ *  - Thresholds per step: enrich when W > c_hi mu^i, prune when
+ *    W < c_lo mu^i, with mu a caller-chosen growth constant (a chain's fate
+ *    depends on its own weight only).  c_hi = +inf never enriches,
+ *    c_lo = 0 never prunes; then the method is plain Rosenbluth growth.
+ *  - Two copies per enrichment.  A population cap max_pop bounds memory:
+ *    enrichments are granted in population order while the population stays
+ *    <= max_pop; a chain denied its copy keeps its whole weight.
+ *  - Dead ends (no free neighbour) leave the population.
+ *  - The growth step is the Rosenbluth step of the lattice chains above
+ *    (same free/contact rule, weight, selection and draw); the chain at
+ *    position j of the population before step i draws from the counter
+ *    (j, ens, i, 0), and its pruning coin is the top bit of word 0 of
+ *    (j, ens, i, 1) (kept when set).  Without pruning, enrichment or dead
+ *    ends the chain at position j is chain j of orc_lattice_run.
+ *  - Weights are kept as W = wm 2^we with wm in [1, 2) (FP64 mantissa,
+ *    integer exponent): every update is one correctly rounded product and
+ *    an exact rescaling, and every comparison with a threshold is exact.
+ *    The threshold mu^i is kept the same way, multiplied by mu each step.
+ *
+ * Outputs per length (i = 0 .. N-1, i steps):
+ *   pop[i]   chains in the population after step i (pop[0] = M0);
+ *   logz[i]  log of (1/M0) sum W over the chains grown at step i (Eq. 9);
+ *   r2[i]    W-weighted mean R_ee^2 of those chains (Eq. 2);
+ * and the final population: its size *final_n, weights (fw_m, fw_e) and
+ * positions fpos[c][N][3] (optional).  Returns 0, or -1 on bad arguments.
+ */
+typedef struct perm_chain {
+    double wm;
+    int32_t we;
+    int32_t *pos;      /* [N][3] */
+} perm_chain;
+
+/* x = m 2^e with m in [1, 2); x > 0 finite. */
+static void perm_norm(double x, double *m, int32_t *e)
+{
+    int k = ilogb(x);
+    *m = ldexp(x, -k);
+    *e = k;
+}
+
+/* Is wm 2^we > c tm 2^te ?  (c >= 0; c = +inf is never exceeded.) */
+static int perm_above(double wm, int32_t we, double c, double tm, int32_t te)
+{
+    if (isinf(c)) return 0;
+    double x = c * tm;
+    if (x == 0.0) return 1;
+    double xm;
+    int32_t xe;
+    perm_norm(x, &xm, &xe);
+    xe += te;
+    return we > xe || (we == xe && wm > xm);
+}
+
+/* Is wm 2^we < c tm 2^te ? */
+static int perm_below(double wm, int32_t we, double c, double tm, int32_t te)
+{
+    if (isinf(c)) return 1;
+    double x = c * tm;
+    if (x == 0.0) return 0;
+    double xm;
+    int32_t xe;
+    perm_norm(x, &xm, &xe);
+    xe += te;
+    return we < xe || (we == xe && wm < xm);
+}
+
+ORC_EXPORT int orc_perm_run(uint64_t seed, uint32_t ens, int N, double beta_eps, int64_t M0,
+                            int64_t max_pop, double mu, double c_hi, double c_lo,
+                            int64_t *pop, double *logz, double *r2, int64_t *final_n,
+                            double *fw_m, int32_t *fw_e, int32_t *fpos)
+{
+    if (N < 2 || M0 < 1 || max_pop < M0 || !(mu > 0.0) || !(c_lo >= 0.0) || !(c_hi > c_lo))
+        return -1;
+    perm_chain *cur = calloc((size_t)max_pop, sizeof(perm_chain));
+    perm_chain *nxt = calloc((size_t)max_pop, sizeof(perm_chain));
+    int *grew = calloc((size_t)max_pop, sizeof(int));    /* grown at this step         */
+    int *fate = calloc((size_t)max_pop, sizeof(int));    /* 0 gone, 1 kept, 2 enriched,
+                                                            -1 pruning survivor         */
+    int32_t *posbuf = malloc(sizeof(int32_t) * 3 * (size_t)N * (size_t)max_pop * 2);
+    for (int64_t c = 0; c < max_pop; ++c) {
+        cur[c].pos = posbuf + (size_t)3 * N * (size_t)c;
+        nxt[c].pos = posbuf + (size_t)3 * N * (size_t)(max_pop + c);
+    }
+    double wt[8];
+    for (int c = 0; c < 8; ++c) wt[c] = exp(beta_eps * (double)c);
+    int64_t P = M0;
+    for (int64_t c = 0; c < P; ++c) {
+        cur[c].wm = 1.0;
+        cur[c].we = 0;
+        memset(cur[c].pos, 0, sizeof(int32_t) * 3 * (size_t)N);
+    }
+    pop[0] = M0;
+    logz[0] = 0.0;
+    r2[0] = 0.0;
+    double tm = 1.0;   /* mu^i = tm 2^te */
+    int32_t te = 0;
+    int i = 1;
+    for (; i < N && P > 0; ++i) {
+        double m_;
+        int32_t e_;
+        perm_norm(tm * mu, &m_, &e_);
+        tm = m_;
+        te += e_;
+
+        /* 1. One Rosenbluth step of every chain, in population order. */
+        for (int64_t j = 0; j < P; ++j) {
+            perm_chain *ch = &cur[j];
+            const int32_t *end = &ch->pos[3 * (i - 1)];
+            int free_[6], contact[6], m = 0;
+            for (int d = 0; d < 6; ++d) {
+                int32_t t[3] = {end[0] + DIRS[d][0], end[1] + DIRS[d][1], end[2] + DIRS[d][2]};
+                free_[d] = 1;
+                contact[d] = 0;
+                for (int q = 0; q <= i - 2; ++q) {
+                    int dist = l1(&ch->pos[3 * q], t);
+                    if (dist == 0) free_[d] = 0;
+                    else if (dist == 1) contact[d]++;
+                }
+                m += free_[d];
+            }
+            grew[j] = m > 0;
+            if (m == 0) continue;          /* dead end: leaves the population */
+            uint32_t x[4];
+            draw(seed, ens, (uint32_t)j, (uint32_t)i, 0u, x);
+            int sel = -1;
+            double S;
+            if (beta_eps == 0.0) {
+                S = (double)m;
+                uint32_t idx = (uint32_t)(((uint64_t)x[0] * (uint64_t)m) >> 32);
+                uint32_t seen = 0;
+                for (int d = 0; d < 6; ++d) {
+                    if (!free_[d]) continue;
+                    if (seen == idx) { sel = d; break; }
+                    seen++;
+                }
+            } else {
+                double w[6];
+                S = 0.0;
+                for (int d = 0; d < 6; ++d) {
+                    w[d] = free_[d] ? wt[contact[d]] : 0.0;
+                    S += w[d];
+                }
+                double r = u24(x[0]) * S, Pf = 0.0;
+                for (int d = 0; d < 6; ++d) {
+                    Pf += w[d];
+                    if (Pf > r) { sel = d; break; }
+                }
+                if (sel < 0)
+                    for (int d = 0; d < 6; ++d)
+                        if (w[d] > 0.0) sel = d;
+            }
+            int32_t *p = &ch->pos[3 * i];
+            p[0] = end[0] + DIRS[sel][0];
+            p[1] = end[1] + DIRS[sel][1];
+            p[2] = end[2] + DIRS[sel][2];
+            perm_norm(ch->wm * S, &m_, &e_);
+            ch->wm = m_;
+            ch->we += e_;
+        }
+
+        /* 2. Estimates of length i over the grown chains (Eq. 9, Eq. 2). */
+        int32_t emax = INT32_MIN;
+        for (int64_t j = 0; j < P; ++j)
+            if (grew[j] && cur[j].we > emax) emax = cur[j].we;
+        if (emax == INT32_MIN) {
+            logz[i] = -INFINITY;
+            r2[i] = NAN;
+        } else {
+            double sw = 0.0, swr = 0.0;
+            for (int64_t j = 0; j < P; ++j) {
+                if (!grew[j]) continue;
+                const int32_t *e = &cur[j].pos[3 * i];
+                const double R2 = (double)((int64_t)e[0] * e[0] + (int64_t)e[1] * e[1] +
+                                           (int64_t)e[2] * e[2]);
+                const double w = ldexp(cur[j].wm, cur[j].we - emax);
+                sw += w;
+                swr += w * R2;
+            }
+            logz[i] = log(sw) + (double)emax * log(2.0) - log((double)M0);
+            r2[i] = swr / sw;
+        }
+
+        /* 3. Fate of every grown chain against the thresholds of length i. */
+        int64_t base = 0;
+        for (int64_t j = 0; j < P; ++j) {
+            if (!grew[j]) {
+                fate[j] = 0;
+            } else if (perm_above(cur[j].wm, cur[j].we, c_hi, tm, te)) {
+                fate[j] = 2;
+            } else if (perm_below(cur[j].wm, cur[j].we, c_lo, tm, te)) {
+                uint32_t y[4];
+                draw(seed, ens, (uint32_t)j, (uint32_t)i, 1u, y);
+                fate[j] = (y[0] >> 31) ? -1 : 0;
+            } else {
+                fate[j] = 1;
+            }
+            base += fate[j] != 0;
+        }
+
+        /* 4. The next population, in order; the first max_pop - base
+         *    enrichment requests are granted. */
+        const int64_t G = max_pop - base;
+        int64_t rank = 0, n = 0;
+        for (int64_t j = 0; j < P; ++j) {
+            if (fate[j] == 0) continue;
+            int copies = 1;
+            int32_t we = cur[j].we;
+            if (fate[j] == 2) {
+                if (rank < G) {
+                    copies = 2;
+                    we -= 1;         /* the copies share the weight */
+                }
+                ++rank;
+            } else if (fate[j] == -1) {
+                we += 1;             /* a pruning survivor carries twice the weight */
+            }
+            for (int c = 0; c < copies; ++c) {
+                nxt[n].wm = cur[j].wm;
+                nxt[n].we = we;
+                memcpy(nxt[n].pos, cur[j].pos, sizeof(int32_t) * 3 * (size_t)(i + 1));
+                ++n;
+            }
+        }
+        perm_chain *t = cur;
+        cur = nxt;
+        nxt = t;
+        P = n;
+        pop[i] = P;
+    }
+    for (; i < N; ++i) {             /* the population died out */
+        pop[i] = 0;
+        logz[i] = -INFINITY;
+        r2[i] = NAN;
+    }
+    *final_n = P;
+    for (int64_t c = 0; c < P; ++c) {
+        if (fw_m) fw_m[c] = cur[c].wm;
+        if (fw_e) fw_e[c] = cur[c].we;
+        if (fpos) memcpy(fpos + (size_t)3 * N * (size_t)c, cur[c].pos, sizeof(int32_t) * 3 * (size_t)N);
+    }
+    free(cur);
+    free(nxt);
+    free(grew);
+    free(fate);
+    free(posbuf);
     return 0;
 }
