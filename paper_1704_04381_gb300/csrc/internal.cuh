@@ -16,6 +16,8 @@ size_t lattice_smem_bytes(int N, int B);
 // N <= 512); outputs are those of rosen_lattice_grow, bit for bit.
 int lattice_grow_range(const rosen_lattice_params *p, const rosen_lattice_out *o, int64_t c_lo,
                        int64_t c_hi, cudaStream_t s);
+// Chains the GPU grows at the same time for this ensemble (0 on error).
+int64_t lattice_resident_chains(const rosen_lattice_params *p);
 int lattice_batch_prepare(int B, int Nmax, size_t *smem, int *blocks_per_sm);
 void lattice_batch_launch(const void *dev_args, const BatchItem *items, int n_items, int *head,
                           int B, size_t smem, int grid, cudaStream_t s);
@@ -29,15 +31,21 @@ void offlattice_make_args(const rosen_offlattice_params *p, const rosen_offlatti
                           unsigned long long *counters, void *out);
 int offlattice_default_lanes(int k, bool lj, int N = 0);
 // Local chains [c_lo, c_hi) of a validated ensemble (shared-memory kernels,
-// N <= 1024), with caller-owned scratch of offlattice_range_scratch_bytes(C)
-// bytes (16-byte aligned) whose deferral mask (after a 16-byte header) is
-// zero before the first range of the ensemble; ranges of one ensemble run
-// in stream order and, for hard spheres, start at multiples of 32 chains
-// (any others cost regrowths of shared mask words, same outputs).  Outputs
-// are those of rosen_offlattice_grow, bit for bit.
-size_t offlattice_range_scratch_bytes(int64_t C);
+// N <= 1024), with caller-owned scratch: counters of
+// offlattice_range_counter_bytes() (16-byte aligned, zeroed by the call; one
+// set per range that may run concurrently with another) and the deferral
+// mask of offlattice_range_mask_bytes(C) bytes (4-byte aligned, zero before
+// the first range of the ensemble, shared by all its ranges).  For hard
+// spheres, ranges that run at the same time must not share mask words: start
+// them at multiples of 32 chains.  Outputs are those of
+// rosen_offlattice_grow, bit for bit.
+size_t offlattice_range_counter_bytes();
+size_t offlattice_range_mask_bytes(int64_t C);
 int offlattice_grow_range(const rosen_offlattice_params *p, const rosen_offlattice_out *o,
-                          int64_t c_lo, int64_t c_hi, void *scratch, cudaStream_t s);
+                          int64_t c_lo, int64_t c_hi, void *counters, uint32_t *mask,
+                          cudaStream_t s);
+// Chains the GPU grows at the same time for this ensemble (0 on error).
+int64_t offlattice_resident_chains(const rosen_offlattice_params *p);
 int offlattice_batch_prepare(int G, int T, bool lj, int Nmax, int *chains_per_block, size_t *smem,
                              int *blocks_per_sm);
 void offlattice_batch_launch(int G, int T, bool lj, const void *dev_args, const BatchItem *items,

@@ -853,6 +853,22 @@ int lattice_grow_range(const rosen_lattice_params *p, const rosen_lattice_out *o
     return check_launch("rosen_lattice_grow");
 }
 
+int64_t lattice_resident_chains(const rosen_lattice_params *p)
+{
+    const int B = lattice_block(p->N);
+    const size_t smem = lattice_smem_bytes(p->N, B);
+    auto kern = p->beta_eps != 0.0 ? lattice_lane_kernel<true> : lattice_lane_kernel<false>;
+    int dev = 0, sms = 0, bps = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        allow_max_smem(kern) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, B, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (int64_t)bps * sms * B;
+}
+
 }  // namespace rosen
 
 using namespace rosen;

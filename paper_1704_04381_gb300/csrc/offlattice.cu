@@ -212,10 +212,12 @@ int chains_per_block_for(int G, int N, bool lj)
     return chains;
 }
 
-// Scratch of a range launch: the chain counter (8 bytes), the second pass's
-// word counter (4 bytes, padded to 16), then the deferral mask, one bit per
-// chain of the ensemble.  The counters are zeroed by every launch; the mask
-// must be zero before the first launch over an ensemble's chains.
+// Scratch of a range launch: 16 bytes of counters (the chain counter, 8
+// bytes, and the second pass's word counter, 4 bytes), zeroed by every
+// launch, and the deferral mask, one bit per chain of the ensemble, which
+// must be zero before the first launch over an ensemble's chains.  Launches
+// that may run at the same time need counters of their own; they can share
+// the mask (their chain ranges are disjoint).
 constexpr size_t kScratchHeader = 16;
 
 size_t mask_bytes(int64_t C) { return (size_t)((C + 31) / 32) * sizeof(uint32_t); }
@@ -232,8 +234,8 @@ size_t mask_bytes(int64_t C) { return (size_t)((C + 31) / 32) * sizeof(uint32_t)
 // costs more than the first pass saves, so they grow in one pass.  Every
 // chain's outputs are those of the one-pass kernel, bit for bit.
 template <int G, int T, bool LJ>
-int launch_range(const OffArgs &a, int N, int64_t c_lo, int64_t c_hi, void *scratch,
-                 cudaStream_t s)
+int launch_range(const OffArgs &a, int N, int64_t c_lo, int64_t c_hi, void *counters,
+                 uint32_t *mask, cudaStream_t s)
 {
     const int chains = chains_per_block_for(G, N, LJ);
     const size_t smem = kTable * sizeof(float) + (size_t)chains * chain_smem_bytes(N, LJ);
@@ -241,11 +243,11 @@ int launch_range(const OffArgs &a, int N, int64_t c_lo, int64_t c_hi, void *scra
     const int64_t n = c_hi - c_lo;
     const int64_t blocks = (n + chains - 1) / chains;
     const bool two_pass = !LJ && N <= 128;
-    unsigned char *sc = static_cast<unsigned char *>(scratch);
+    unsigned char *sc = static_cast<unsigned char *>(counters);
     unsigned long long *next = reinterpret_cast<unsigned long long *>(sc);
     unsigned int *wnext = reinterpret_cast<unsigned int *>(sc + 8);
     OffArgs d = a;
-    if (two_pass) d.deferred = reinterpret_cast<uint32_t *>(sc + kScratchHeader);
+    if (two_pass) d.deferred = mask;
     cudaError_t e = cudaMemsetAsync(sc, 0, kScratchHeader, s);
     int dev = 0, sms = 0, bps = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
@@ -295,7 +297,9 @@ int launch_one(const OffArgs &a, int N, cudaStream_t s)
         cudaError_t e = two_pass ? cudaMemsetAsync(static_cast<unsigned char *>(buf) +
                                                        kScratchHeader, 0, bytes - kScratchHeader, s)
                                  : cudaSuccess;
-        int st = e == cudaSuccess ? launch_range<G, T, LJ>(a, N, 0, a.C, buf, s)
+        uint32_t *mask = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(buf) +
+                                                      kScratchHeader);
+        int st = e == cudaSuccess ? launch_range<G, T, LJ>(a, N, 0, a.C, buf, mask, s)
                                   : set_error(ROSEN_ECUDA, "rosen_offlattice_grow: %s",
                                               cudaGetErrorString(e));
         const cudaError_t f = cudaFreeAsync(buf, s);
@@ -314,28 +318,55 @@ int launch_one(const OffArgs &a, int N, cudaStream_t s)
     return check_launch("rosen_offlattice_grow");
 }
 
+// Chains the GPU grows at once with the first-pass (or only) kernel.
+template <int G, int T, bool LJ>
+int64_t resident(int N)
+{
+    const int chains = chains_per_block_for(G, N, LJ);
+    const size_t smem = kTable * sizeof(float) + (size_t)chains * chain_smem_bytes(N, LJ);
+    auto first = (!LJ && N <= 128) ? offlattice_queue_kernel<G, T, LJ, !LJ>
+                                   : offlattice_queue_kernel<G, T, LJ, false>;
+    int dev = 0, sms = 0, bps = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        allow_max_smem(first) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, first, chains * G, smem) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return (int64_t)bps * sms * chains;
+}
+
+// launch_one (counters == nullptr: a whole ensemble, scratch allocated
+// here), launch_range, or the resident chain count (resident_out != nullptr).
 template <int G, bool LJ>
-int launch_g(const OffArgs &a, int N, int k, int64_t c_lo, int64_t c_hi, void *scratch,
-             cudaStream_t s)
+int launch_g(const OffArgs &a, int N, int k, int64_t c_lo, int64_t c_hi, void *counters,
+             uint32_t *mask, cudaStream_t s, int64_t *resident_out = nullptr)
 {
     const int T = (k + G - 1) / G;
-    if (!scratch) {
+    if (resident_out) {
+        *resident_out = T <= 1 ? resident<G, 1, LJ>(N) : T <= 2 ? resident<G, 2, LJ>(N)
+                                                                  : resident<G, 4, LJ>(N);
+        return ROSEN_OK;
+    }
+    if (!counters) {
         if (T <= 1) return launch_one<G, 1, LJ>(a, N, s);
         if (T <= 2) return launch_one<G, 2, LJ>(a, N, s);
         return launch_one<G, 4, LJ>(a, N, s);
     }
-    if (T <= 1) return launch_range<G, 1, LJ>(a, N, c_lo, c_hi, scratch, s);
-    if (T <= 2) return launch_range<G, 2, LJ>(a, N, c_lo, c_hi, scratch, s);
-    return launch_range<G, 4, LJ>(a, N, c_lo, c_hi, scratch, s);
+    if (T <= 1) return launch_range<G, 1, LJ>(a, N, c_lo, c_hi, counters, mask, s);
+    if (T <= 2) return launch_range<G, 2, LJ>(a, N, c_lo, c_hi, counters, mask, s);
+    return launch_range<G, 4, LJ>(a, N, c_lo, c_hi, counters, mask, s);
 }
 
 template <bool LJ>
-int launch_lj(const OffArgs &a, int G, int N, int k, int64_t c_lo, int64_t c_hi, void *scratch,
-              cudaStream_t s)
+int launch_lj(const OffArgs &a, int G, int N, int k, int64_t c_lo, int64_t c_hi, void *counters,
+              uint32_t *mask, cudaStream_t s, int64_t *resident_out = nullptr)
 {
-    if (G == 8) return launch_g<8, LJ>(a, N, k, c_lo, c_hi, scratch, s);
-    if (G == 16) return launch_g<16, LJ>(a, N, k, c_lo, c_hi, scratch, s);
-    return launch_g<32, LJ>(a, N, k, c_lo, c_hi, scratch, s);
+    if (G == 8) return launch_g<8, LJ>(a, N, k, c_lo, c_hi, counters, mask, s, resident_out);
+    if (G == 16) return launch_g<16, LJ>(a, N, k, c_lo, c_hi, counters, mask, s, resident_out);
+    return launch_g<32, LJ>(a, N, k, c_lo, c_hi, counters, mask, s, resident_out);
 }
 
 // The batch kernel of class (G, T, LJ) through one function pointer type.
@@ -474,14 +505,16 @@ int offlattice_launch(const rosen_offlattice_params *p, const rosen_offlattice_o
     const bool lj = p->potential == ROSEN_LJ;
     const int G =
         p->lanes_per_chain ? p->lanes_per_chain : offlattice_default_lanes(p->k, lj, p->N);
-    return lj ? launch_lj<true>(a, G, p->N, p->k, 0, p->C, nullptr, s)
-              : launch_lj<false>(a, G, p->N, p->k, 0, p->C, nullptr, s);
+    return lj ? launch_lj<true>(a, G, p->N, p->k, 0, p->C, nullptr, nullptr, s)
+              : launch_lj<false>(a, G, p->N, p->k, 0, p->C, nullptr, nullptr, s);
 }
 
-size_t offlattice_range_scratch_bytes(int64_t C) { return kScratchHeader + mask_bytes(C); }
+size_t offlattice_range_counter_bytes() { return kScratchHeader; }
+size_t offlattice_range_mask_bytes(int64_t C) { return mask_bytes(C); }
 
 int offlattice_grow_range(const rosen_offlattice_params *p, const rosen_offlattice_out *o,
-                          int64_t c_lo, int64_t c_hi, void *scratch, cudaStream_t s)
+                          int64_t c_lo, int64_t c_hi, void *counters, uint32_t *mask,
+                          cudaStream_t s)
 {
     if (c_hi <= c_lo) return ROSEN_OK;
     OffArgs a;
@@ -489,8 +522,21 @@ int offlattice_grow_range(const rosen_offlattice_params *p, const rosen_offlatti
     const bool lj = p->potential == ROSEN_LJ;
     const int G =
         p->lanes_per_chain ? p->lanes_per_chain : offlattice_default_lanes(p->k, lj, p->N);
-    return lj ? launch_lj<true>(a, G, p->N, p->k, c_lo, c_hi, scratch, s)
-              : launch_lj<false>(a, G, p->N, p->k, c_lo, c_hi, scratch, s);
+    return lj ? launch_lj<true>(a, G, p->N, p->k, c_lo, c_hi, counters, mask, s)
+              : launch_lj<false>(a, G, p->N, p->k, c_lo, c_hi, counters, mask, s);
+}
+
+int64_t offlattice_resident_chains(const rosen_offlattice_params *p)
+{
+    OffArgs a;
+    memset(&a, 0, sizeof a);
+    const bool lj = p->potential == ROSEN_LJ;
+    const int G =
+        p->lanes_per_chain ? p->lanes_per_chain : offlattice_default_lanes(p->k, lj, p->N);
+    int64_t r = 0;
+    if (lj) launch_lj<true>(a, G, p->N, p->k, 0, 0, nullptr, nullptr, nullptr, &r);
+    else launch_lj<false>(a, G, p->N, p->k, 0, 0, nullptr, nullptr, nullptr, &r);
+    return r;
 }
 
 int offlattice_batch_prepare(int G, int T, bool lj, int Nmax, int *chains_per_block, size_t *smem,

@@ -8,12 +8,17 @@
 //    passed by later ones that do, for at most kPassLimitNs, after which
 //    nothing behind it is admitted until it fits;
 //  - grows every admitted request in slices, chain ranges of about kSliceNs
-//    of GPU time, on the request's own stream, with the single-ensemble
-//    kernels (lattice_grow_range / offlattice_grow_range; long chains in one
-//    piece through the long-chain entry points);
+//    of GPU time but at least twice the chains the GPU grows at once (so a
+//    slice fills the GPU), with the single-ensemble kernels
+//    (lattice_grow_range / offlattice_grow_range; long chains in one piece
+//    through the long-chain entry points).  A request's slices alternate
+//    between two streams of its own, so its next slice starts while the
+//    last blocks of the previous one finish;
 //  - chooses the request of each next slice by policy: arrival order, or
 //    (shortest_first) the least estimated remaining GPU time, discounted by
-//    the time the request has waited so that large requests are not starved;
+//    the time the request has waited; under either policy a request that has
+//    been admitted for more than kStarveNs goes first, oldest first, so that
+//    no request starves;
 //  - keeps about kLookaheadNs of slices enqueued so that the GPU does not
 //    idle between slices (the next slice's blocks start as the last ones of
 //    the running slice finish);
@@ -62,6 +67,7 @@ constexpr int64_t kLookaheadNs = 8'000'000;    // estimated work kept enqueued
 constexpr int kMaxInflight = 16;               // slices enqueued at once
 constexpr int64_t kPassLimitNs = 1'000'000'000;   // longest a request may be passed over
 constexpr double kAgingNs = 1e9;               // shortest_first: waiting discount scale
+constexpr int64_t kStarveNs = 1'000'000'000;   // admitted longer: served in arrival order
 
 int64_t now_ns()
 {
@@ -91,11 +97,14 @@ struct Request {
     void *rws = nullptr;       // reduction workspace
     size_t rws_bytes = 0;
     rosen_stats *dstats = nullptr;
-    void *scratch = nullptr;   // real space: chain counters and deferral mask
+    void *scratch = nullptr;   // real space: two sets of chain counters, the deferral mask
     void *long_ws = nullptr;   // long chains: their workspace
     size_t long_bytes = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t streams[2] = {nullptr, nullptr};   // slices alternate between them
     cudaEvent_t done = nullptr;
+    cudaEvent_t join = nullptr;   // orders the two streams (set-up, end)
+    int nslices = 0;
+    int64_t resident = 0;      // chains the GPU grows at once for this request
     rosen_stats *host_stats = nullptr;   // pinned
     rosen_stats stats;
     int64_t t_submit = 0, t_admit = 0, t_done = 0;
@@ -173,11 +182,12 @@ size_t long_workspace_bytes(const rosen_request &r)
     return align256(std::max(one, std::min(want, kLongWorkspaceCap)));
 }
 
-// Real-space chain counters and deferral mask (shared-memory kernels).
+// Real-space chain counters (one set per stream) and deferral mask
+// (shared-memory kernels).
 size_t scratch_bytes(const rosen_request &r)
 {
     if (r.model != ROSEN_MODEL_OFFLATTICE || long_request(r)) return 0;
-    return align256(offlattice_range_scratch_bytes(r.C));
+    return align256(2 * offlattice_range_counter_bytes() + offlattice_range_mask_bytes(r.C));
 }
 
 // Device bytes a request holds while it runs, and what stored conformations
@@ -369,11 +379,15 @@ cudaEvent_t take_event(std::vector<cudaEvent_t> &pool, unsigned flags)
 // Resources of a request that is no longer on the GPU go back to the pools.
 void retire(rosen_server *s, Request *q)
 {
-    if (q->stream) s->streams.push_back(q->stream);
+    for (cudaStream_t &st : q->streams) {
+        if (st) s->streams.push_back(st);
+        st = nullptr;
+    }
     if (q->done) s->done_events.push_back(q->done);
+    if (q->join) s->done_events.push_back(q->join);
     if (q->host_stats) s->pinned.push_back(q->host_stats);
-    q->stream = nullptr;
     q->done = nullptr;
+    q->join = nullptr;
     q->host_stats = nullptr;
 }
 
@@ -382,7 +396,7 @@ void retire(rosen_server *s, Request *q)
 // memory cannot be had fails at once and gives its reservation back.
 bool admit(rosen_server *s, Request *q)
 {
-    if (s->streams.empty()) {
+    while (s->streams.size() < 2) {
         cudaStream_t st = nullptr;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
             cudaGetLastError();
@@ -392,18 +406,27 @@ bool admit(rosen_server *s, Request *q)
     }
     cudaEvent_t done = take_event(s->done_events, cudaEventDisableTiming);
     if (!done) return false;
+    cudaEvent_t join = take_event(s->done_events, cudaEventDisableTiming);
+    if (!join) {
+        s->done_events.push_back(done);
+        return false;
+    }
     if (s->pinned.empty()) {
         rosen_stats *h = nullptr;
         if (cudaMallocHost(reinterpret_cast<void **>(&h), sizeof(rosen_stats)) != cudaSuccess) {
             cudaGetLastError();
             s->done_events.push_back(done);
+            s->done_events.push_back(join);
             return false;
         }
         s->pinned.push_back(h);
     }
-    q->stream = s->streams.back();
-    s->streams.pop_back();
+    for (cudaStream_t &st : q->streams) {
+        st = s->streams.back();
+        s->streams.pop_back();
+    }
     q->done = done;
+    q->join = join;
     q->host_stats = s->pinned.back();
     s->pinned.pop_back();
     q->state = RUNNING;
@@ -412,19 +435,26 @@ bool admit(rosen_server *s, Request *q)
     auto it = s->rate.find(key);
     q->ns_per_chain = it != s->rate.end() ? it->second : default_ns_per_chain(q->req);
 
-    cudaError_t e = cudaMallocFromPoolAsync(&q->work, q->work_bytes, s->pool, q->stream);
+    cudaStream_t s0 = q->streams[0];
+    cudaError_t e = cudaMallocFromPoolAsync(&q->work, q->work_bytes, s->pool, s0);
     if (e == cudaSuccess && q->coord_bytes)
-        e = cudaMallocFromPoolAsync(&q->coords, q->coord_bytes, s->pool, q->stream);
+        e = cudaMallocFromPoolAsync(&q->coords, q->coord_bytes, s->pool, s0);
     if (e == cudaSuccess) {
         carve(q);
-        if (q->scratch)
-            e = cudaMemsetAsync(q->scratch, 0, scratch_bytes(q->req), q->stream);
+        if (q->scratch) e = cudaMemsetAsync(q->scratch, 0, scratch_bytes(q->req), s0);
+    }
+    // The second stream starts after the allocation and the set-up.
+    if (e == cudaSuccess) e = cudaEventRecord(q->join, s0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(q->streams[1], q->join, 0);
+    if (e == cudaSuccess && !q->long_ws) {
+        q->resident = q->req.model == ROSEN_MODEL_LATTICE ? lattice_resident_chains(&q->lp)
+                                                          : offlattice_resident_chains(&q->op);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
         fail(q, ROSEN_ENOMEM, cudaGetErrorString(e));
-        if (q->work) cudaFreeAsync(q->work, q->stream);
-        if (q->coords) cudaFreeAsync(q->coords, q->stream);
+        if (q->work) cudaFreeAsync(q->work, s0);
+        if (q->coords) cudaFreeAsync(q->coords, s0);
         q->work = q->coords = nullptr;
         cudaGetLastError();
         q->t_done = now_ns();
@@ -445,40 +475,52 @@ bool admit(rosen_server *s, Request *q)
 void finish(Request *q)
 {
     q->finishing = true;
+    cudaStream_t s0 = q->streams[0];
+    // The end runs on the first stream once the second has drained.
+    if (cudaEventRecord(q->join, q->streams[1]) != cudaSuccess ||
+        cudaStreamWaitEvent(s0, q->join, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamSynchronize(q->streams[1]);
+    }
     int st = ROSEN_OK;
     if (q->state != FAILED) {
-        st = rosen_reduce(&q->rin, q->dstats, q->rws, q->rws_bytes, q->stream);
+        st = rosen_reduce(&q->rin, q->dstats, q->rws, q->rws_bytes, s0);
         if (st == ROSEN_OK &&
             cudaMemcpyAsync(q->host_stats, q->dstats, sizeof(rosen_stats), cudaMemcpyDeviceToHost,
-                            q->stream) != cudaSuccess)
+                            s0) != cudaSuccess)
             st = set_error(ROSEN_ECUDA, "copying the statistics: %s",
                            cudaGetErrorString(cudaGetLastError()));
         if (st != ROSEN_OK) fail(q, st, rosen_last_error());
     }
     // The outputs are scratch once the statistics are copied; conformations stay.
-    if (q->work) cudaFreeAsync(q->work, q->stream);
+    if (q->work) cudaFreeAsync(q->work, s0);
     q->work = nullptr;
-    if (cudaEventRecord(q->done, q->stream) != cudaSuccess) {
+    if (cudaEventRecord(q->done, s0) != cudaSuccess) {
         // Without the event the stream is synchronised here instead.
         cudaGetLastError();
-        cudaStreamSynchronize(q->stream);
+        cudaStreamSynchronize(s0);
         cudaEventRecord(q->done, 0);
     }
 }
 
-// Enqueue the next slice of q: chains [next_chain, next_chain + n), or the
-// whole request for long chains.  Slices start at multiples of 32 chains
-// (the deferral mask's words).
+// Enqueue the next slice of q on the stream after the last one's:
+// chains [next_chain, next_chain + n), or the whole request for long chains.
+// A slice holds about kSliceNs of estimated GPU time but at least twice the
+// chains the GPU grows at once, and starts at a multiple of 32 chains (the
+// deferral mask's words).
 void launch_slice(rosen_server *s, Request *q)
 {
     const int64_t C = q->req.C;
     int64_t n = C - q->next_chain;
     if (!q->long_ws) {
         const double per = std::max(q->ns_per_chain, 1e-3);
-        int64_t want = (int64_t)((double)kSliceNs / per);
+        int64_t want = std::max<int64_t>((int64_t)((double)kSliceNs / per), 2 * q->resident);
         want = std::max<int64_t>(32, (want + 31) / 32 * 32);
         if (n - want >= want / 2) n = want;   // else: the remainder in one slice
     }
+    const int lane = q->nslices & 1;
+    cudaStream_t st_q = q->streams[lane];
+    ++q->nslices;
     Slice sl;
     sl.q = q;
     sl.chains = n;
@@ -486,18 +528,21 @@ void launch_slice(rosen_server *s, Request *q)
     sl.start = take_event(s->timing_events, cudaEventDefault);
     sl.end = take_event(s->timing_events, cudaEventDefault);
     int st = ROSEN_OK;
-    if (sl.start) cudaEventRecord(sl.start, q->stream);
+    if (sl.start) cudaEventRecord(sl.start, st_q);
     const int64_t c_lo = q->next_chain, c_hi = c_lo + n;
     if (q->long_ws) {
         st = q->req.model == ROSEN_MODEL_LATTICE
-                 ? rosen_lattice_grow_long(&q->lp, &q->lo, q->long_ws, q->long_bytes, q->stream)
-                 : rosen_offlattice_grow_long(&q->op, &q->oo, q->long_ws, q->long_bytes, q->stream);
+                 ? rosen_lattice_grow_long(&q->lp, &q->lo, q->long_ws, q->long_bytes, st_q)
+                 : rosen_offlattice_grow_long(&q->op, &q->oo, q->long_ws, q->long_bytes, st_q);
     } else if (q->req.model == ROSEN_MODEL_LATTICE) {
-        st = lattice_grow_range(&q->lp, &q->lo, c_lo, c_hi, q->stream);
+        st = lattice_grow_range(&q->lp, &q->lo, c_lo, c_hi, st_q);
     } else {
-        st = offlattice_grow_range(&q->op, &q->oo, c_lo, c_hi, q->scratch, q->stream);
+        unsigned char *sc = static_cast<unsigned char *>(q->scratch);
+        const size_t cb = offlattice_range_counter_bytes();
+        st = offlattice_grow_range(&q->op, &q->oo, c_lo, c_hi, sc + lane * cb,
+                                   reinterpret_cast<uint32_t *>(sc + 2 * cb), st_q);
     }
-    if (sl.end) cudaEventRecord(sl.end, q->stream);
+    if (sl.end) cudaEventRecord(sl.end, st_q);
     q->next_chain = c_hi;
     if (st != ROSEN_OK) {
         fail(q, st, rosen_last_error());
@@ -515,16 +560,22 @@ void launch_slice(rosen_server *s, Request *q)
 
 // The request whose slice goes next: the oldest (arrival order), or the one
 // with the least estimated remaining GPU time divided by 1 + its waiting
-// time in seconds (shortest_first).  At most two slices of one request are
-// enqueued at once.
+// time in seconds (shortest_first); requests admitted more than kStarveNs
+// ago come first, oldest first.  At most two slices of one request (one per
+// stream) are enqueued at once.
 Request *pick(rosen_server *s, int64_t now)
 {
     Request *best = nullptr;
     double best_key = 0.0;
+    bool best_old = false;
     for (Request *q : s->active) {
         if (q->finishing || q->inflight >= 2 || q->next_chain >= q->req.C) continue;
+        const bool old = now - q->t_admit > kStarveNs;
+        if (best_old && !old) continue;
+        if (old && !best_old) best = nullptr;
+        best_old = best_old || old;
         double key;
-        if (s->cfg.shortest_first) {
+        if (s->cfg.shortest_first && !old) {
             const double rem = (double)(q->req.C - q->next_chain) * q->ns_per_chain;
             key = rem / (1.0 + (double)(now - q->t_submit) / kAgingNs);
         } else {
@@ -612,7 +663,7 @@ bool reap_requests(rosen_server *s)
         if (q->state == FAILED) {
             ++s->n_failed;
             // A failed request gives back everything it reserved.
-            if (q->coords) cudaFreeAsync(q->coords, q->stream);
+            if (q->coords) cudaFreeAsync(q->coords, q->streams[0]);
             q->coords = nullptr;
             s->used -= q->coord_bytes;
         }

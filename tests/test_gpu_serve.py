@@ -261,7 +261,7 @@ def test_admission_passes_a_request_that_does_not_fit(rosen):
                       store_coords=True)                       # ~62 MB, tens of ms
     b = rosen.request(L, 128, 60_000, 42, 1, store_coords=True)   # ~94 MB
     c = rosen.request(L, 32, 1000, 43, 2)                          # < 1 MB
-    srv = rosen.RosenServer(mem_budget_bytes=150 << 20, max_slots=8)
+    srv = rosen.RosenServer(mem_budget_bytes=140 << 20, max_slots=8)   # 146.8 MB
     try:
         ta = srv.submit(a)
         deadline = time.time() + 10
