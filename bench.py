@@ -345,10 +345,14 @@ def run_ours(args):
     # The batched and served configurations and the conformation-store run
     # (one GPU only): the metric's latency half and the batched/served
     # throughput next to the single-ensemble path.
-    batched = served5 = served_ok = stored = None
-    if world == 1 and not (args.no_served and args.no_batched and args.no_store_coords):
+    batched = served5 = served_ok = stored = perm = None
+    if world == 1 and not (args.no_served and args.no_batched and args.no_store_coords and
+                           args.no_perm):
         del ens
         torch.cuda.empty_cache()
+        if not args.no_perm:
+            perm = perm_leg(rosen, torch)
+            torch.cuda.empty_cache()
         if not args.no_store_coords:
             stored = store_coords_leg(rosen, torch)
         if not args.no_batched:
@@ -382,6 +386,7 @@ def run_ours(args):
         "served_config5": served5,
         "served_sustainable": served_ok,
         "store_coords": stored,
+        "perm": perm,
         "small_config": n16,
     }
     if not args.no_cpu_baseline:
@@ -645,6 +650,66 @@ def batched_leg(rosen, torch, scale=1.0, steps=3, warmup=1):
             "batched_over_single": single_ms / batch_ms, "tune_s": tune_s,
             "fp64_redecided_steps_total": cnt[0], "classes": len(classes),
             "clocks": clocks.summary()}
+
+
+PERM_CFG = dict(N=64, M0=1_000_000, cap=4_000_000, mu=4.684, c_hi=3.0, c_lo=1.0 / 3.0, seed=9)
+
+
+def perm_leg(rosen, torch, steps=3, warmup=1):
+    """PERM (breadth first) on the cubic lattice: athermal N = 64, 10^6 chains
+    started, population cap 4x10^6, thresholds 3 mu^i and mu^i / 3 with
+    mu = 4.684.  value = chain steps grown per second (every chain of the
+    population before step i makes one step).  Algorithmic bytes per step of
+    a chain: the scan of its earlier monomers of matching parity (4 B each),
+    then the copy of its i + 1 keys into the next population (read and
+    write, per copy), against the measured HBM bandwidth."""
+    c = PERM_CFG
+    N, M0, cap = c["N"], c["M0"], c["cap"]
+    p = rosen.perm_params(c["seed"], N, M0, cap, mu=c["mu"], c_hi=c["c_hi"], c_lo=c["c_lo"])
+    out = rosen.perm_outputs(N, cap)
+    ws = rosen.perm_workspace(N, cap)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(1, warmup)):
+        rosen.rosen_perm_run(p, out, ws, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        rosen.rosen_perm_run(p, out, ws, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    pop = out["population"].cpu().tolist()
+    logz = out["logz"].cpu().tolist()
+    grown = sum(pop[i - 1] for i in range(1, N))
+    nbytes = sum(pop[i - 1] * 4 * (i // 2) + pop[i] * 8 * (i + 1) + pop[i] * 24
+                 for i in range(1, N))
+    peak = measured_peak("hbm_gbs", 6800.0)
+    gbs = nbytes / (ms / 1e3) / 1e9
+    return {"workload": "PERM athermal N=64, M0=1e6 chains started, cap 4e6, mu=4.684, "
+                        "c_hi=3, c_lo=1/3, seed 9",
+            "ms": ms, "chain_steps": grown, "chain_steps_per_s": grown / (ms / 1e3),
+            "population_final": pop[-1], "population_max": max(pop),
+            "logZ_N": logz[-1], "launches_per_run": 4 * (N - 1) + 2,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "traffic": None,
+                         "basis": "per chain step: 4 B per scanned key (parity), 8 B per copied "
+                                  "key (read + write) and 24 B of weights, per copy"}}
+
+
+def run_perm(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1704_04381_gb300 import rosen
+    torch.cuda.set_device(0)
+    r = perm_leg(rosen, torch, steps=args.steps, warmup=args.warmup)
+    line = {"metric": "PERM chain steps/s (breadth first, cubic lattice)",
+            "value": r["chain_steps_per_s"], "unit": "chain steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"],
+            "higher_is_better": True, "dtype": "int32+fp64", "data": "synthetic",
+            "config": {"workload": r["workload"]}, "perm": r}
+    print(json.dumps(line), flush=True)
 
 
 def run_batched(args):
@@ -991,6 +1056,7 @@ def main():
                     help="step: skip the batched configuration (one graph launch)")
     ap.add_argument("--no-store-coords", action="store_true",
                     help="step: skip the hard-sphere launch that stores conformations")
+    ap.add_argument("--no-perm", action="store_true", help="step: skip the PERM run")
     ap.add_argument("--served-duration", type=float, default=60.0,
                     help="step: seconds of arrivals in each served run")
     ap.add_argument("--served-policy", default="shortest_first",
@@ -999,7 +1065,8 @@ def main():
     ap.add_argument("--lattice-only", action="store_true")
     ap.add_argument("--chains", type=int, default=None,
                     help="chains per ensemble (default 10^7); smaller values are for profiling")
-    ap.add_argument("--workload", default="step", choices=["step", "batched", "served", "long"])
+    ap.add_argument("--workload", default="step",
+                    choices=["step", "batched", "served", "long", "perm"])
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="scale of the chain counts in the batched/served modes")
     ap.add_argument("--rate", type=float, default=2000.0, help="served: arrivals per second")
@@ -1032,6 +1099,8 @@ def main():
         return run_batched(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "perm":
+        return run_perm(args)
     if args.chains:
         global C
         C = args.chains

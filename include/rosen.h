@@ -358,6 +358,74 @@ ROSEN_API int rosen_reduce(const rosen_reduce_in *in, rosen_stats *out, void *wo
 ROSEN_API int rosen_stats_merge(const rosen_stats *parts, int32_t n, int32_t N, int32_t k,
                                 rosen_stats *out);
 
+/* ---- PERM: pruned-enriched Rosenbluth growth (cubic lattice) ---------- */
+/*
+ * The paper's conclusion names a GPU implementation of PERM (Grassberger,
+ * Phys. Rev. E 56, 3682 (1997)) whose text is not available; this is that
+ * method, breadth first.  A population of M0 chains grows one step at a time
+ * with the Rosenbluth step of rosen_lattice_grow (Section 3.3.2, Eq. 3).
+ * After step i a chain with W > c_hi mu^i is enriched: it and a copy go on,
+ * each with W/2.  A chain with W < c_lo mu^i is pruned: it is removed with
+ * probability 1/2 and otherwise goes on with 2W.  Chains at a dead end leave.
+ * Both operations keep the expected total weight, so logz[i] estimates
+ * log Z_i (Eq. 9: the mean weight per chain started) and mean_r2[i] the
+ * W-weighted <R_ee^2> (Eq. 2), for every length at once.
+ * Readings: thresholds c mu^i with a caller-chosen growth constant mu
+ * (c_hi = +inf: no enrichment, c_lo = 0: no pruning, which is plain
+ * Rosenbluth growth); two copies per enrichment; at most max_population
+ * chains -- enrichments are granted in population order while the cap
+ * allows, and a chain denied its copy keeps its weight.  Random numbers: the
+ * chain at position j of the population before step i draws its step from
+ * the Philox counter (j, ensemble, i, 0), as chain j of rosen_lattice_grow
+ * would, and its pruning coin from the top bit of word 0 of (j, ensemble,
+ * i, 1) (kept when set).  Weights are FP64 mantissas in [1, 2) with int32
+ * exponents, so every fate decision is exact and the run is deterministic.
+ */
+#define ROSEN_PERM_MAX_POP (1 << 24)
+
+typedef struct rosen_perm_params {
+    uint64_t seed;
+    uint32_t ensemble;
+    int32_t N;                /* monomers per chain, 2 <= N <= 512           */
+    int64_t M0;               /* chains started, >= 1                        */
+    int64_t max_population;   /* cap, M0 <= max_population <= 2^24            */
+    double beta_eps;          /* contact attraction (0: athermal), >= 0       */
+    double mu;                /* threshold growth per step, > 0               */
+    double c_hi, c_lo;        /* enrichment / pruning factors, 0 <= c_lo < c_hi
+                                 (c_hi may be +inf)                           */
+    uint32_t flags;           /* ROSEN_STORE_COORDS: the final conformations  */
+    int32_t reserved;         /* set to 0                                     */
+} rosen_perm_params;
+
+typedef struct rosen_perm_out {
+    int64_t *population;      /* [N]: chains after step i (population[0] = M0) */
+    double *logz;             /* [N]: log((1/M0) sum W) over the chains grown at
+                                 step i, -inf if none (logz[0] = 0)            */
+    double *mean_r2;          /* [N] optional: their W-weighted <R_ee^2>       */
+    int64_t *final_n;         /* [1]: chains in the final population            */
+    double *w_m;              /* [max_population] optional: final weights       */
+    int32_t *w_e;             /*   W = w_m 2^w_e, w_m in [1, 2)                  */
+    int32_t *coords;          /* [N][3][max_population] optional (needs
+                                 ROSEN_STORE_COORDS): final chain c, monomer q,
+                                 axis a at [q][a][c]                             */
+} rosen_perm_out;
+
+/* Bytes of workspace rosen_perm_run needs (two populations of packed keys,
+ * weights, scan arrays): about 8 N + 45 bytes per chain of the cap; 0 for
+ * arguments out of range. */
+ROSEN_API size_t rosen_perm_workspace_size(int32_t N, int64_t max_population);
+/*
+ * Run PERM on the stream: all outputs are DEVICE pointers owned by the
+ * caller; workspace: device, 256-byte aligned, at least
+ * rosen_perm_workspace_size bytes, contents need not be initialised.  The
+ * population size stays on the device (no host synchronisation); about
+ * 4 N kernel launches.  Errors: EINVAL (N, M0, cap, beta_eps, mu, c_hi,
+ * c_lo or flags out of range, a required output missing), ENOMEM (workspace
+ * too small), ECUDA.
+ */
+ROSEN_API int rosen_perm_run(const rosen_perm_params *p, const rosen_perm_out *o,
+                             void *workspace, size_t workspace_bytes, void *stream);
+
 /* ---- batched growth: many ensembles, one graph launch ---------------- */
 #define ROSEN_MODEL_LATTICE 0
 #define ROSEN_MODEL_OFFLATTICE 1

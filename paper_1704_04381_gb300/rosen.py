@@ -77,6 +77,19 @@ class rosen_reduce_in(ctypes.Structure):
 
 ROSEN_MODEL_LATTICE = 0
 ROSEN_MODEL_OFFLATTICE = 1
+ROSEN_PERM_MAX_POP = 1 << 24
+
+
+class rosen_perm_params(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("ensemble", ctypes.c_uint32), ("N", ctypes.c_int32),
+                ("M0", ctypes.c_int64), ("max_population", ctypes.c_int64),
+                ("beta_eps", ctypes.c_double), ("mu", ctypes.c_double), ("c_hi", ctypes.c_double),
+                ("c_lo", ctypes.c_double), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_int32)]
+
+
+class rosen_perm_out(ctypes.Structure):
+    _fields_ = [("population", _vp), ("logz", _vp), ("mean_r2", _vp), ("final_n", _vp),
+                ("w_m", _vp), ("w_e", _vp), ("coords", _vp)]
 
 
 class rosen_ensemble(ctypes.Structure):
@@ -163,6 +176,11 @@ def load():
     L.rosen_reduce_noalloc.restype = ctypes.c_int
     L.rosen_stats_merge.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp]
     L.rosen_stats_merge.restype = ctypes.c_int
+    L.rosen_perm_workspace_size.argtypes = [ctypes.c_int32, ctypes.c_int64]
+    L.rosen_perm_workspace_size.restype = ctypes.c_size_t
+    L.rosen_perm_run.argtypes = [ctypes.POINTER(rosen_perm_params), ctypes.POINTER(rosen_perm_out),
+                                 _vp, ctypes.c_size_t, _vp]
+    L.rosen_perm_run.restype = ctypes.c_int
     _LIB = L
     return L
 
@@ -391,6 +409,46 @@ def rosen_stats_merge(parts, N, k=0):
     _check(load().rosen_stats_merge(ctypes.cast(arr, _vp), int(n), int(N), int(k),
                                     ctypes.cast(out, _vp)))
     return dict(zip(STAT_KEYS, list(out)))
+
+
+def perm_params(seed, N, M0, max_population=None, beta_eps=0.0, mu=4.684, c_hi=3.0,
+                c_lo=1.0 / 3.0, ensemble=0, flags=0):
+    return rosen_perm_params(seed=int(seed), ensemble=int(ensemble), N=int(N), M0=int(M0),
+                             max_population=int(max_population or 4 * M0),
+                             beta_eps=float(beta_eps), mu=float(mu), c_hi=float(c_hi),
+                             c_lo=float(c_lo), flags=int(flags), reserved=0)
+
+
+def perm_outputs(N, max_population, device="cuda", coords=False):
+    """Allocate the outputs of rosen_perm_run (final weights always)."""
+    out = {
+        "population": torch.empty(N, dtype=torch.int64, device=device),
+        "logz": torch.empty(N, dtype=torch.float64, device=device),
+        "mean_r2": torch.empty(N, dtype=torch.float64, device=device),
+        "final_n": torch.empty(1, dtype=torch.int64, device=device),
+        "w_m": torch.empty(max_population, dtype=torch.float64, device=device),
+        "w_e": torch.empty(max_population, dtype=torch.int32, device=device),
+    }
+    if coords:
+        out["coords"] = torch.empty((N, 3, max_population), dtype=torch.int32, device=device)
+    return out
+
+
+def perm_workspace(N, max_population, device="cuda"):
+    nbytes = int(load().rosen_perm_workspace_size(int(N), int(max_population)))
+    if nbytes == 0:
+        raise RosenError(ROSEN_EINVAL, "PERM sizes out of range")
+    return torch.empty((nbytes + 255) // 256 * 32, dtype=torch.float64, device=device)
+
+
+def rosen_perm_run(params, out, workspace, stream=None):
+    """PERM on the cubic lattice (breadth first); out from perm_outputs."""
+    o = rosen_perm_out(population=_ptr(out["population"]), logz=_ptr(out["logz"]),
+                       mean_r2=_ptr(out.get("mean_r2")), final_n=_ptr(out["final_n"]),
+                       w_m=_ptr(out.get("w_m")), w_e=_ptr(out.get("w_e")),
+                       coords=_ptr(out.get("coords")))
+    _check(load().rosen_perm_run(ctypes.byref(params), ctypes.byref(o), _ptr(workspace),
+                                 workspace.numel() * workspace.element_size(), _stream(stream)))
 
 
 def stats_tensor(device="cuda"):

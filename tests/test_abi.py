@@ -63,6 +63,8 @@ def test_struct_layout_matches_c(rosen, tmp_path):
         "rosen_request": rosen.rosen_request,
         "rosen_result": rosen.rosen_result,
         "rosen_serve_counters": rosen.rosen_serve_counters,
+        "rosen_perm_params": rosen.rosen_perm_params,
+        "rosen_perm_out": rosen.rosen_perm_out,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rosen.h"', "int main(void){"]
     for name, cls in structs.items():
@@ -228,3 +230,38 @@ def test_batch_rejects_bad_ensembles(rosen, bad):
     h = ctypes.c_void_p()
     assert rosen.load().rosen_batch_create(arr, 2, ctypes.byref(h)) == rosen.ROSEN_EINVAL
     assert "ensemble 1" in rosen.last_error()
+
+
+def _perm(rosen, ws=4096, nbytes=None, out=None, **kw):
+    p = rosen.perm_params(**{**dict(seed=1, N=16, M0=100, max_population=400), **kw})
+    o = out or rosen.rosen_perm_out(population=4096, logz=8192, final_n=12288)
+    if nbytes is None:
+        nbytes = rosen.load().rosen_perm_workspace_size(p.N, p.max_population)
+    return rosen.load().rosen_perm_run(ctypes.byref(p), ctypes.byref(o), ws, nbytes, None)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(N=1), dict(N=513), dict(M0=0), dict(max_population=50), dict(max_population=(1 << 24) + 1),
+    dict(beta_eps=-0.5), dict(beta_eps=float("nan")), dict(mu=0.0), dict(mu=float("inf")),
+    dict(c_hi=0.5, c_lo=0.5), dict(c_lo=-1.0), dict(c_lo=float("inf"), c_hi=float("inf")),
+    dict(flags=1), dict(flags=2),
+])
+def test_perm_rejects_bad_parameters(rosen, kw):
+    # Host-side validation before any CUDA call (flags=2 asks for coordinates
+    # without an array).
+    assert _perm(rosen, **kw) == rosen.ROSEN_EINVAL
+    assert "rosen_perm_run" in rosen.last_error()
+
+
+def test_perm_workspace_and_outputs(rosen):
+    L = rosen.load()
+    assert L.rosen_perm_workspace_size(1, 100) == 0
+    assert L.rosen_perm_workspace_size(16, 0) == 0
+    assert L.rosen_perm_workspace_size(16, (1 << 24) + 1) == 0
+    n = L.rosen_perm_workspace_size(64, 10 ** 6)
+    # two populations of keys (8 N bytes per chain) plus weights and scans
+    assert 8 * 64 * 10 ** 6 < n < (8 * 64 + 64) * 10 ** 6
+    assert _perm(rosen, nbytes=L.rosen_perm_workspace_size(16, 400) - 1) == rosen.ROSEN_ENOMEM
+    assert _perm(rosen, ws=4096 + 16) == rosen.ROSEN_EINVAL          # 256-byte alignment
+    missing = rosen.rosen_perm_out(population=4096, logz=None, final_n=12288)
+    assert _perm(rosen, out=missing) == rosen.ROSEN_EINVAL
