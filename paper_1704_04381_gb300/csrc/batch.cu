@@ -8,9 +8,13 @@
 // decreasing cost (N^2 k per chain), so long and short chains, large and small
 // ensembles share the GPU without tail effects.  The shape of every class
 // (lattice: chains per block; real space: lanes per chain) is picked by timing
-// the candidates on a sample of the class.  Growth of all classes (on forked
-// streams, so they overlap) and the FP64 reduction of every ensemble are
-// captured once into a CUDA graph; each run is one graph launch.
+// the candidates on a sample of the class.  A member with at least
+// kOwnLaunchWaves times the chains its single-ensemble kernel grows at once
+// fills the GPU by itself: it runs as that kernel's own launch (a persistent
+// grid over its chains) on the class's stream, before the class kernel, and
+// the class kernel serves the smaller members.  Growth of all classes (on
+// forked streams, so they overlap) and the FP64 reduction of every ensemble
+// are captured once into a CUDA graph; each run is one graph launch.
 //
 // Every chain is grown by the same device code as the single-ensemble entry
 // points and every ensemble is reduced by the same tile and merge code as
@@ -35,9 +39,17 @@ struct rosen_batch;
 namespace rosen {
 namespace {
 
+// A member is grown by its own single-ensemble launch from this many waves of
+// resident chains up.
+constexpr int64_t kOwnLaunchWaves = 4;
+
 struct ClassPlan {
     bool lattice;
     bool lj;
+    std::vector<char> own;      // per member: grown by its own single-ensemble launch
+    std::vector<size_t> own_off;   // real space: offset of its counters and mask in d_own
+    void *d_own = nullptr;      // real space: scratch of the members with their own launch
+    size_t own_bytes = 0;
     bool longc = false; // long chains: members grown one after another by the
                         // hash-table / cell-grid kernels in one class workspace
     void *d_ws = nullptr;
@@ -156,6 +168,7 @@ std::vector<BatchItem> make_items(const rosen_batch *b, const ClassPlan &c, doub
     std::vector<BatchItem> items;
     std::vector<double> cost;
     for (size_t m = 0; m < c.members.size(); ++m) {
+        if (!c.own.empty() && c.own[m]) continue;
         const rosen_ensemble &e = b->ens[c.members[m]];
         int64_t limit = e.C;
         if (fraction < 1.0)
@@ -231,8 +244,38 @@ int upload_items(ClassPlan &c, const std::vector<BatchItem> &items)
     return ROSEN_OK;
 }
 
-int launch_class(const rosen_batch *b, const ClassPlan &c, cudaStream_t s)
+// Members with their own launch, largest first, through the single-ensemble
+// range launches (default lanes per chain, as rosen_*_grow would grow them).
+int launch_own(const rosen_batch *b, const ClassPlan &c, cudaStream_t s)
 {
+    if (c.d_own && cudaMemsetAsync(c.d_own, 0, c.own_bytes, s) != cudaSuccess)
+        return set_error(ROSEN_ECUDA, "batch: clearing the members' scratch");
+    for (size_t m = 0; m < c.members.size(); ++m) {
+        if (!c.own[m]) continue;
+        const int e = c.members[m];
+        int st;
+        if (c.lattice) {
+            const rosen_lattice_params p = lat_params(b->ens[e]);
+            st = lattice_grow_range(&p, &b->lat_out[e], 0, p.C, s);
+        } else {
+            const rosen_offlattice_params p = off_params(b->ens[e], 0);
+            unsigned char *sc = static_cast<unsigned char *>(c.d_own) + c.own_off[m];
+            st = offlattice_grow_range(&p, &b->off_out[e], 0, p.C, sc,
+                                       reinterpret_cast<uint32_t *>(
+                                           sc + offlattice_range_counter_bytes()),
+                                       s);
+        }
+        if (st != ROSEN_OK) return st;
+    }
+    return ROSEN_OK;
+}
+
+int launch_class(const rosen_batch *b, const ClassPlan &c, cudaStream_t s, bool shared_only = false)
+{
+    if (!c.longc && !shared_only) {
+        const int st = launch_own(b, c, s);
+        if (st != ROSEN_OK) return st;
+    }
     if (c.longc) {
         for (int e : c.members) {
             int st;
@@ -260,6 +303,7 @@ int launch_class(const rosen_batch *b, const ClassPlan &c, cudaStream_t s)
 // the fastest per unit of work.
 int tune_class(rosen_batch *b, ClassPlan &c)
 {
+    if (make_items(b, c, 1.0).empty()) return ROSEN_OK;   // every member has its own launch
     std::vector<int> cands;
     if (c.lattice) {
         for (int B : {64, 128, 256})
@@ -297,7 +341,7 @@ int tune_class(rosen_batch *b, ClassPlan &c)
         for (int rep = 0; rep < 2; ++rep) {
             CK(cudaMemsetAsync(c.d_head, 0, sizeof(int), b->s0));
             CK(cudaEventRecord(e0, b->s0));
-            launch_class(b, c, b->s0);
+            launch_class(b, c, b->s0, true);
             CK(cudaEventRecord(e1, b->s0));
             CK(cudaStreamSynchronize(b->s0));
             CK(cudaGetLastError());
@@ -402,6 +446,7 @@ void free_batch(rosen_batch *b)
         if (c.d_args) cudaFree(c.d_args);
         if (c.d_head) cudaFree(c.d_head);
         if (c.d_ws) cudaFree(c.d_ws);
+        if (c.d_own) cudaFree(c.d_own);
         if (c.stream) cudaStreamDestroy(c.stream);
         if (c.done) cudaEventDestroy(c.done);
     }
@@ -549,6 +594,30 @@ int create(rosen_batch *b, const rosen_ensemble *ens, int n)
             CK(cudaMalloc(&c.d_ws, c.ws_bytes));
             continue;
         }
+        // Members that fill the GPU by themselves get their own launch
+        // (real space: with their own chain counters and deferral mask).
+        c.own.assign(c.members.size(), 0);
+        c.own_off.assign(c.members.size(), 0);
+        for (size_t m = 0; m < c.members.size(); ++m) {
+            const rosen_ensemble &x = b->ens[c.members[m]];
+            int64_t res;
+            if (c.lattice) {
+                const rosen_lattice_params p = lat_params(x);
+                res = lattice_resident_chains(&p);
+            } else {
+                const rosen_offlattice_params p = off_params(x, 0);
+                res = offlattice_resident_chains(&p);
+            }
+            if (res > 0 && x.C >= kOwnLaunchWaves * res) {
+                c.own[m] = 1;
+                if (!c.lattice) {
+                    c.own_off[m] = c.own_bytes;
+                    c.own_bytes += align256(offlattice_range_counter_bytes() +
+                                            offlattice_range_mask_bytes(x.C));
+                }
+            }
+        }
+        if (c.own_bytes) CK(cudaMalloc(&c.d_own, c.own_bytes));
         // Untuned default shape: 128 chains per block (fewer if the keys of
         // the longest chain would not fit), or the default lanes per chain.
         if (c.lattice) {
@@ -651,6 +720,20 @@ extern "C" int rosen_batch_describe(rosen_batch *b, char *buf, size_t len)
         s += line;
         for (size_t m = 0; m < c.members.size(); ++m)
             s += (m ? "," : "") + std::to_string(c.members[m]);
+        // Lanes per chain each member is grown with: the class's, or (own
+        // launch) the single-ensemble default.
+        s += "],\"own_launch\":[";
+        for (size_t m = 0; m < c.members.size(); ++m)
+            s += std::string(m ? "," : "") + ((!c.own.empty() && c.own[m]) ? "1" : "0");
+        s += "],\"member_lanes\":[";
+        for (size_t m = 0; m < c.members.size(); ++m) {
+            const rosen_ensemble &x = b->ens[c.members[m]];
+            int lanes = c.lattice ? 1 : c.G;
+            if (!c.lattice && !c.own.empty() && c.own[m])
+                lanes = offlattice_default_lanes(x.k, x.potential == ROSEN_LJ, x.N);
+            if (c.longc) lanes = 0;      // the long-chain kernel's own default
+            s += (m ? "," : "") + std::to_string(lanes);
+        }
         s += "]}";
     }
     s += "]";

@@ -72,7 +72,7 @@ def test_alone_and_in_the_mix_are_identical(rosen):
     torch.cuda.synchronize()
     classes = json.loads(b.describe())
     assert sum(c["ensembles"] for c in classes) == len(ens)
-    lanes = {m: c["lanes_per_chain"] for c in classes for m in c["members"]}
+    lanes = {m: l for c in classes for m, l in zip(c["members"], c["member_lanes"])}
     for i, e in enumerate(ens):
         lattice = e.model == rosen.ROSEN_MODEL_LATTICE
         out, st = single(rosen, e, 0 if lattice else lanes[i])
@@ -125,6 +125,38 @@ def test_repeated_runs_are_identical_and_match_the_oracle(rosen):
     b.close()
 
 
+def test_large_members_get_their_own_launch(rosen):
+    # A member with several waves of resident chains runs as its own
+    # single-ensemble launch inside the graph; its outputs are those of
+    # rosen_*_grow with the default lanes, bit for bit, and the small members
+    # of its class still share the class kernel.
+    L, R = rosen.ROSEN_MODEL_LATTICE, rosen.ROSEN_MODEL_OFFLATTICE
+    ens = [rosen.ensemble(R, 60, 300_000, 21, 0, k=32, potential=rosen.ROSEN_LJ, beta_eps=0.6),
+           rosen.ensemble(R, 50, 700, 22, 1, k=32, potential=rosen.ROSEN_LJ, beta_eps=0.3),
+           rosen.ensemble(R, 64, 400_000, 23, 2, k=32),
+           rosen.ensemble(L, 64, 3_000_000, 24, 3, beta_eps=0.2),
+           rosen.ensemble(L, 60, 2_000, 25, 4, beta_eps=0.1)]
+    b = rosen.RosenBatch(ens)
+    b.tune()
+    b.run()
+    b.run()
+    got = b.stats()
+    torch.cuda.synchronize()
+    classes = json.loads(b.describe())
+    own = {m: o for c in classes for m, o in zip(c["members"], c["own_launch"])}
+    assert own[0] == own[2] == own[3] == 1 and own[1] == own[4] == 0
+    lanes = {m: l for c in classes for m, l in zip(c["members"], c["member_lanes"])}
+    for i, e in enumerate(ens):
+        lattice = e.model == rosen.ROSEN_MODEL_LATTICE
+        out, st = single(rosen, e, 0 if (lattice or own[i]) else lanes[i])
+        mine = b.lattice_outputs(i) if lattice else b.offlattice_outputs(i)
+        torch.cuda.synchronize()
+        assert torch.equal(got[i], st), i
+        for key, v in mine.items():
+            assert torch.equal(v, out[key]), (i, key)
+    b.close()
+
+
 def test_config_like_batch_runs(rosen):
     # A scaled-down draw of the batched configuration: N uniform in [8, 256],
     # chain counts log-uniform, half lattice ISAW, half LJ with k in {16,32,64}.
@@ -145,7 +177,8 @@ def test_config_like_batch_runs(rosen):
     st = b.stats().cpu().numpy()
     assert np.isfinite(st[:, 11]).all()          # logZ
     assert (st[:, 1] > 0).all()                   # live chains in every ensemble
-    lanes = {m: c["lanes_per_chain"] for c in json.loads(b.describe()) for m in c["members"]}
+    lanes = {m: l for c in json.loads(b.describe())
+             for m, l in zip(c["members"], c["member_lanes"])}
     for i in (0, 1, 7):
         lat = ens[i].model == rosen.ROSEN_MODEL_LATTICE
         _, s1 = single(rosen, ens[i], 0 if lat else lanes[i])
