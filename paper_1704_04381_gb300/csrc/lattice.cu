@@ -12,11 +12,10 @@
 // with one integer add: t is the packed displacement (dx+2, dy+2, dz+2) and
 // it fits three 3-bit fields exactly when the monomer lies in the 5x5x5 box
 // around the end (|d| <= 511 on every axis keeps the fields from borrowing
-// into each other).  One multiply by 1 + 2^7 + 2^14 gathers the three fields
-// into bits 14..22 without carries (the partial products below bit 14 sum to
-// less than 2^13), giving a 9-bit index into a 512-entry table that turns
-// the displacement into "occupies neighbour d" bits and "touches neighbour
-// d" contact increments.  Monomers outside the box read the all-zero entry
+// into each other).  One multiply gathers the three fields into the byte
+// offset of an entry of a 512-entry table (lattice_step.cuh) that turns the
+// displacement into "occupies neighbour d" bits and "touches neighbour d"
+// contact increments.  Monomers outside the box read the all-zero entry
 // 511, so the scan has no branch; the entries are simply added (a site holds
 // one monomer, so the occupancy bits never carry).  Parity halves the
 // athermal scan: only monomers j with j = i (mod 2) can sit on a neighbour
@@ -47,12 +46,14 @@ namespace {
 // attempt is allowed (restart mode): the caller grows the chain again with
 // att + 1 (the outputs then hold nothing final for it).  Otherwise the
 // chain's outputs are written and false is returned.
-template <bool kIsaw>
+// kB > 0 fixes the stride at compile time (immediate load offsets).
+template <bool kIsaw, int kB = 0>
 __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c, uint32_t att,
-                                                uint32_t *my, int B, const uint32_t *lut,
+                                                uint32_t *my, int B_, const uint32_t *lut,
                                                 const uint8_t *seltab, const float *wt32,
                                                 const double *wt64)
 {
+    const int B = kB > 0 ? kB : B_;
     const uint32_t chain = a.chain0 + (uint32_t)c;
     const int N = a.N;
     const int64_t C = a.C;
@@ -82,14 +83,10 @@ __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c,
             const uint32_t kb = kNearBias - key;
             if (kIsaw) {
 #pragma unroll 4
-                for (int j = 0; j <= i - 2; ++j) {
-                    acc += lut[lut_slot(my[j * B] + kb)];
-                }
+                for (int j = 0; j <= i - 2; ++j) acc += lut_at(lut, lut_off(my[j * B] + kb));
             } else {
 #pragma unroll 4
-                for (int j = i & 1; j <= i - 2; j += 2) {
-                    acc += lut[lut_slot(my[j * B] + kb)];
-                }
+                for (int j = i & 1; j <= i - 2; j += 2) acc += lut_at(lut, lut_off(my[j * B] + kb));
             }
             const uint32_t freem = ~acc & 63u;
             const int m = __popc(freem);
@@ -156,19 +153,20 @@ __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c,
 }
 
 // Every growth of chain c in this lane (restart mode regrows in place).
-template <bool kIsaw>
+template <bool kIsaw, int kB = 0>
 __device__ __forceinline__ void lattice_chain(const LatticeArgs &a, int64_t c, uint32_t *my, int B,
                                               const uint32_t *lut, const uint8_t *seltab,
                                               const float *wt32, const double *wt64)
 {
     uint32_t att = 0;
-    while (lattice_attempt<kIsaw>(a, c, att, my, B, lut, seltab, wt32, wt64)) ++att;
+    while (lattice_attempt<kIsaw, kB>(a, c, att, my, B, lut, seltab, wt32, wt64)) ++att;
 }
 
 
 // Local chains [c_lo, c_hi) of the ensemble, one per lane (a call grows
-// [0, C); the server grows a request in slices of chain ranges).
-template <bool kIsaw>
+// [0, C); the server grows a request in slices of chain ranges).  kB > 0:
+// blocks of exactly kB threads (the key stride known at compile time).
+template <bool kIsaw, int kB = 0>
 __global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a, int64_t c_lo,
                                                            int64_t c_hi)
 {
@@ -186,10 +184,10 @@ __global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a, 
     }
     __syncthreads();
 
-    const int B = blockDim.x;
+    const int B = kB > 0 ? kB : (int)blockDim.x;
     const int64_t c = c_lo + (int64_t)blockIdx.x * B + threadIdx.x;
     if (c >= c_hi) return;
-    lattice_chain<kIsaw>(a, c, keys + threadIdx.x, B, lut, seltab, wt32, wt64);
+    lattice_chain<kIsaw, kB>(a, c, keys + threadIdx.x, B, lut, seltab, wt32, wt64);
 }
 
 // Restart mode, single ensemble: a persistent kernel in which every warp owns
@@ -239,7 +237,8 @@ __global__ void __launch_bounds__(256) lattice_retry_kernel(const LatticeArgs a,
         next += fresh;
         __syncwarp();
         const bool retry =
-            c >= 0 && lattice_attempt<kIsaw>(a, c, att, keys + lane, 32, lut, seltab, wt32, wt64);
+            c >= 0 && lattice_attempt<kIsaw, 32>(a, c, att, keys + lane, 32, lut, seltab, wt32,
+                                                 wt64);
         const unsigned m = __ballot_sync(0xffffffffu, retry);
         if (retry) {
             const int pos = __popc(m & ((1u << lane) - 1u));
@@ -705,13 +704,12 @@ int lattice_grow_range(const rosen_lattice_params *p, const rosen_lattice_out *o
     if (a.max_att > 1) return lattice_retry_launch(a, p->N, B, c_lo, c_hi, s);
     const size_t smem = lattice_smem_bytes(p->N, B);
     const int64_t blocks = (c_hi - c_lo + B - 1) / B;
-    if (p->beta_eps == 0.0) {
-        allow_max_smem(lattice_lane_kernel<false>);
-        lattice_lane_kernel<false><<<(unsigned)blocks, B, smem, s>>>(a, c_lo, c_hi);
-    } else {
-        allow_max_smem(lattice_lane_kernel<true>);
-        lattice_lane_kernel<true><<<(unsigned)blocks, B, smem, s>>>(a, c_lo, c_hi);
-    }
+    // Blocks of 256 (N up to about 100) with the stride fixed at compile time.
+    auto kern = p->beta_eps == 0.0
+                    ? (B == 256 ? lattice_lane_kernel<false, 256> : lattice_lane_kernel<false, 0>)
+                    : (B == 256 ? lattice_lane_kernel<true, 256> : lattice_lane_kernel<true, 0>);
+    allow_max_smem(kern);
+    kern<<<(unsigned)blocks, B, smem, s>>>(a, c_lo, c_hi);
     return check_launch("rosen_lattice_grow");
 }
 
@@ -719,7 +717,9 @@ int64_t lattice_resident_chains(const rosen_lattice_params *p)
 {
     const int B = lattice_block(p->N);
     const size_t smem = lattice_smem_bytes(p->N, B);
-    auto kern = p->beta_eps != 0.0 ? lattice_lane_kernel<true> : lattice_lane_kernel<false>;
+    auto kern = p->beta_eps != 0.0
+                    ? (B == 256 ? lattice_lane_kernel<true, 256> : lattice_lane_kernel<true, 0>)
+                    : (B == 256 ? lattice_lane_kernel<false, 256> : lattice_lane_kernel<false, 0>);
     int dev = 0, sms = 0, bps = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||

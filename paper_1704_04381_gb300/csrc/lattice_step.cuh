@@ -19,15 +19,26 @@ constexpr uint32_t kOriginKey = 512u | (512u << 10) | (512u << 20);
 constexpr int kLutWords = 512;
 constexpr int kSelBytes = 512;
 
-constexpr uint32_t kGather = (1u << 14) | (1u << 7) | 1u;
-constexpr uint32_t kZeroSlot = 511u;   // fields (7,7,7): outside the box, entry 0
+// One multiply gathers the three 3-bit fields of an in-box displacement into
+// bits 23..31 of the product -- y at 23..25, z at 26..28, x at 29..31 -- and
+// a shift by 21 leaves them at bits 2..10: the byte offset of table entry
+// y + 8 z + 64 x.  The other partial products (x 2^13, x 2^6, y 2^6; the
+// rest overflow past bit 31) sum to less than 2^19, so nothing carries into
+// bits 19 and up.
+constexpr uint32_t kGather = (1u << 29) | (1u << 13) | (1u << 6);
+constexpr uint32_t kZeroOff = 511u * 4u;   // fields (7,7,7): outside the box, entry 0
 
-// Table slot of displacement t: its three 3-bit fields as a 9-bit index if
-// the monomer lies in the 5x5x5 box around the end, else the zero entry.
-__device__ __forceinline__ uint32_t lut_slot(uint32_t t)
+// Byte offset of displacement t's table entry if the monomer lies in the
+// 5x5x5 box around the end, else of the zero entry.
+__device__ __forceinline__ uint32_t lut_off(uint32_t t)
 {
-    const uint32_t idx = ((t * kGather) >> 14) & 0x1FFu;
-    return ((t & ~kFieldMask) == 0u) ? idx : kZeroSlot;
+    const uint32_t off = (t * kGather) >> 21;
+    return ((t & ~kFieldMask) == 0u) ? off : kZeroOff;
+}
+
+__device__ __forceinline__ uint32_t lut_at(const uint32_t *lut, uint32_t off)
+{
+    return *reinterpret_cast<const uint32_t *>(reinterpret_cast<const unsigned char *>(lut) + off);
 }
 
 // Table entry for an earlier monomer at displacement d from the chain end.
@@ -36,7 +47,7 @@ __device__ __forceinline__ uint32_t lut_slot(uint32_t t)
 // (one non-bonded contact for a monomer placed there).
 __device__ uint32_t lut_entry(int idx)
 {
-    const int dx = (idx & 7) - 2, dy = ((idx >> 3) & 7) - 2, dz = ((idx >> 6) & 7) - 2;
+    const int dy = (idx & 7) - 2, dz = ((idx >> 3) & 7) - 2, dx = ((idx >> 6) & 7) - 2;
     if (dx > 2 || dy > 2 || dz > 2) return 0u;
     if (dx == 0 && dy == 0 && dz == 0) return 0u;
     uint32_t e = 0u;

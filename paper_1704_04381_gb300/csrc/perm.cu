@@ -184,9 +184,9 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
         const uint32_t kb = kNearBias - key;
         uint32_t acc = 0u;
         if (kIsaw) {
-            for (int q = 0; q <= i - 2; ++q) acc += lut[lut_slot(col[(int64_t)q * MP] + kb)];
+            for (int q = 0; q <= i - 2; ++q) acc += lut_at(lut, lut_off(col[(int64_t)q * MP] + kb));
         } else {
-            for (int q = i & 1; q <= i - 2; q += 2) acc += lut[lut_slot(col[(int64_t)q * MP] + kb)];
+            for (int q = i & 1; q <= i - 2; q += 2) acc += lut_at(lut, lut_off(col[(int64_t)q * MP] + kb));
         }
         const uint32_t freem = ~acc & 63u;
         const int m = __popc(freem);
