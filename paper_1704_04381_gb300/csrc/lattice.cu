@@ -41,8 +41,11 @@ namespace {
 
 
 // Growth number att of chain c (local index) of the ensemble described by a,
-// in this lane.  my points at the lane's column of the [monomer][lane] key
-// array (stride B).  Returns true when the growth was trapped and another
+// in this lane.  The keys sit in groups of four monomers per lane, key j at
+// word j % 4 of the lane's 16-byte group j / 4, and the groups of one lane are
+// B groups apart ([j / 4][lane][j % 4]), so one 128-bit load brings four keys
+// and the 32 lanes of a warp read 512 contiguous bytes (no bank conflict).
+// my points at the lane's first group.  Returns true when the growth was trapped and another
 // attempt is allowed (restart mode): the caller grows the chain again with
 // att + 1 (the outputs then hold nothing final for it).  Otherwise the
 // chain's outputs are written and false is returned.
@@ -72,6 +75,7 @@ __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c,
     {
         key = kOriginKey;
         my[0] = key;
+        const uint4 *m4 = reinterpret_cast<const uint4 *>(my);
         sx = sy = sz = sq = 0;
         ex = ey = ez = 0;
         cnt = 0;
@@ -81,12 +85,42 @@ __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c,
         for (int i = 1; i < N; ++i) {
             uint32_t acc = 0u;
             const uint32_t kb = kNearBias - key;
+            // Monomers 0 .. i-2: `full` whole groups, then `rem` of the next.
+            const int full = (i - 1) >> 2, rem = (i - 1) & 3;
             if (kIsaw) {
-#pragma unroll 4
-                for (int j = 0; j <= i - 2; ++j) acc += lut_at(lut, lut_off(my[j * B] + kb));
+#pragma unroll 2
+                for (int g = 0; g < full; ++g) {
+                    const uint4 q = m4[g * B];
+                    acc += lut_at(lut, lut_off(q.x + kb)) + lut_at(lut, lut_off(q.y + kb)) +
+                           lut_at(lut, lut_off(q.z + kb)) + lut_at(lut, lut_off(q.w + kb));
+                }
+                if (rem) {
+                    const uint4 q = m4[full * B];
+                    acc += lut_at(lut, lut_off(q.x + kb));
+                    if (rem > 1) acc += lut_at(lut, lut_off(q.y + kb));
+                    if (rem > 2) acc += lut_at(lut, lut_off(q.z + kb));
+                }
+            } else if (i & 1) {
+                // Only monomers j = i (mod 2) can sit on a neighbour of the
+                // end: words 1 and 3 of each group.
+#pragma unroll 2
+                for (int g = 0; g < full; ++g) {
+                    const uint4 q = m4[g * B];
+                    acc += lut_at(lut, lut_off(q.y + kb)) + lut_at(lut, lut_off(q.w + kb));
+                }
+                if (rem > 1) acc += lut_at(lut, lut_off(m4[full * B].y + kb));
             } else {
-#pragma unroll 4
-                for (int j = i & 1; j <= i - 2; j += 2) acc += lut_at(lut, lut_off(my[j * B] + kb));
+                // Words 0 and 2.
+#pragma unroll 2
+                for (int g = 0; g < full; ++g) {
+                    const uint4 q = m4[g * B];
+                    acc += lut_at(lut, lut_off(q.x + kb)) + lut_at(lut, lut_off(q.z + kb));
+                }
+                if (rem) {
+                    const uint4 q = m4[full * B];
+                    acc += lut_at(lut, lut_off(q.x + kb));
+                    if (rem > 2) acc += lut_at(lut, lut_off(q.z + kb));
+                }
             }
             const uint32_t freem = ~acc & 63u;
             const int m = __popc(freem);
@@ -99,7 +133,7 @@ __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c,
             cnt += 1ull << (9 * m);
             const uint32_t axis_step = 1u << (10 * (sel >> 1));
             key = (sel & 1) ? key - axis_step : key + axis_step;
-            my[i * B] = key;
+            my[(i >> 2) * 4 * B + (i & 3)] = key;
             ex = (int)(key & 1023u) - 512;
             ey = (int)((key >> 10) & 1023u) - 512;
             ez = (int)(key >> 20) - 512;
@@ -187,7 +221,7 @@ __global__ void __launch_bounds__(256) lattice_lane_kernel(const LatticeArgs a, 
     const int B = kB > 0 ? kB : (int)blockDim.x;
     const int64_t c = c_lo + (int64_t)blockIdx.x * B + threadIdx.x;
     if (c >= c_hi) return;
-    lattice_chain<kIsaw, kB>(a, c, keys + threadIdx.x, B, lut, seltab, wt32, wt64);
+    lattice_chain<kIsaw, kB>(a, c, keys + 4 * threadIdx.x, B, lut, seltab, wt32, wt64);
 }
 
 // Restart mode, single ensemble: a persistent kernel in which every warp owns
@@ -208,7 +242,7 @@ __global__ void __launch_bounds__(256) lattice_retry_kernel(const LatticeArgs a,
     const int wpb = blockDim.x / 32, wib = threadIdx.x / 32, lane = threadIdx.x & 31;
     uint32_t *rq = smem + kLutWords + kSelBytes / 4 + 8 + 16 + (size_t)wib * 64;   // [2][32]
     uint32_t *keys = smem + kLutWords + kSelBytes / 4 + 8 + 16 + (size_t)wpb * 64 +
-                     (size_t)wib * a.N * 32;
+                     (size_t)wib * ((a.N + 3) & ~3) * 32;
 
     fill_tables(lut, seltab);
     if (threadIdx.x < 8) {
@@ -237,8 +271,8 @@ __global__ void __launch_bounds__(256) lattice_retry_kernel(const LatticeArgs a,
         next += fresh;
         __syncwarp();
         const bool retry =
-            c >= 0 && lattice_attempt<kIsaw, 32>(a, c, att, keys + lane, 32, lut, seltab, wt32,
-                                                 wt64);
+            c >= 0 && lattice_attempt<kIsaw, 32>(a, c, att, keys + 4 * lane, 32, lut, seltab,
+                                                 wt32, wt64);
         const unsigned m = __ballot_sync(0xffffffffu, retry);
         if (retry) {
             const int pos = __popc(m & ((1u << lane) - 1u));
@@ -285,10 +319,10 @@ __global__ void __launch_bounds__(256) lattice_batch_kernel(const LatticeArgs *_
         __syncthreads();
         if (threadIdx.x < (int)bi.n) {
             if (sa.isaw)
-                lattice_chain<true>(sa, bi.c0 + threadIdx.x, keys + threadIdx.x, B, lut, seltab,
+                lattice_chain<true>(sa, bi.c0 + threadIdx.x, keys + 4 * threadIdx.x, B, lut, seltab,
                                     wt32, wt64);
             else
-                lattice_chain<false>(sa, bi.c0 + threadIdx.x, keys + threadIdx.x, B, lut, seltab,
+                lattice_chain<false>(sa, bi.c0 + threadIdx.x, keys + 4 * threadIdx.x, B, lut, seltab,
                                      wt32, wt64);
         }
         __syncthreads();
@@ -576,7 +610,8 @@ __global__ void __launch_bounds__(256) lattice_long_kernel(const LatticeArgs a, 
 
 size_t lattice_smem_bytes(int N, int B)
 {
-    return (size_t)(kLutWords + kSelBytes / 4 + 8 + 16) * 4 + (size_t)N * B * 4;
+    // Tables, then the keys in groups of four monomers per lane.
+    return (size_t)(kLutWords + kSelBytes / 4 + 8 + 16) * 4 + (size_t)((N + 3) & ~3) * B * 4;
 }
 
 // Block size: the largest multiple of 32 (at most 256) whose coordinate
@@ -673,7 +708,7 @@ int lattice_retry_launch(const LatticeArgs &a, int N, int B, int64_t c_lo, int64
 {
     const int wpb = B / 32;
     const size_t smem = (size_t)(kLutWords + kSelBytes / 4 + 8 + 16) * 4 +
-                        (size_t)wpb * (64 * 4 + (size_t)N * 32 * 4);
+                        (size_t)wpb * (64 * 4 + (size_t)((N + 3) & ~3) * 32 * 4);
     auto kern = a.isaw ? lattice_retry_kernel<true> : lattice_retry_kernel<false>;
     cudaError_t e = allow_max_smem(kern);
     int bps = 0, dev = 0, sms = 0;
