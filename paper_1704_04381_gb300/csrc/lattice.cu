@@ -39,13 +39,18 @@
 namespace rosen {
 namespace {
 
+// 16-byte key groups per parity and lane: ceil(ceil(N / 2) / 4).
+__host__ __device__ __forceinline__ int key_groups(int N) { return ((N + 1) / 2 + 3) / 4; }
+
 
 // Growth number att of chain c (local index) of the ensemble described by a,
-// in this lane.  The keys sit in groups of four monomers per lane, key j at
-// word j % 4 of the lane's 16-byte group j / 4, and the groups of one lane are
-// B groups apart ([j / 4][lane][j % 4]), so one 128-bit load brings four keys
-// and the 32 lanes of a warp read 512 contiguous bytes (no bank conflict).
-// my points at the lane's first group.  Returns true when the growth was trapped and another
+// in this lane.  The keys sit in 16-byte groups of four monomers of one
+// parity: key j (parity p = j % 2, h = j / 2) is word h % 4 of group h / 4 of
+// parity p, the lane's groups are B apart, and the parities lie kGroups(N)
+// groups apart ([p][h / 4][lane][h % 4]).  One 128-bit load brings four keys
+// of one parity, and the 32 lanes of a warp read 512 contiguous bytes (no
+// bank conflict).  The athermal scan reads one parity, the interacting scan
+// both.  my points at the lane's first group.  Returns true when the growth was trapped and another
 // attempt is allowed (restart mode): the caller grows the chain again with
 // att + 1 (the outputs then hold nothing final for it).  Otherwise the
 // chain's outputs are written and false is returned.
@@ -76,6 +81,7 @@ __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c,
         key = kOriginKey;
         my[0] = key;
         const uint4 *m4 = reinterpret_cast<const uint4 *>(my);
+        const int pstride = key_groups(N) * B;   // groups between the parities
         sx = sy = sz = sq = 0;
         ex = ey = ez = 0;
         cnt = 0;
@@ -85,41 +91,26 @@ __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c,
         for (int i = 1; i < N; ++i) {
             uint32_t acc = 0u;
             const uint32_t kb = kNearBias - key;
-            // Monomers 0 .. i-2: `full` whole groups, then `rem` of the next.
-            const int full = (i - 1) >> 2, rem = (i - 1) & 3;
-            if (kIsaw) {
+            // Monomers j = i (mod 2) can sit on a neighbour of the end (the
+            // athermal scan needs only them); j = i + 1 (mod 2) can touch one.
+            // Of parity q, monomers 0 .. i-2 hold (i - q) / 2 keys.
+#pragma unroll
+            for (int pass = 0; pass < (kIsaw ? 2 : 1); ++pass) {
+                const int q = (i + pass) & 1;
+                const int n = (i - q) >> 1;
+                const uint4 *src = m4 + q * pstride;
+                const int full = n >> 2, rem = n & 3;
 #pragma unroll 2
                 for (int g = 0; g < full; ++g) {
-                    const uint4 q = m4[g * B];
-                    acc += lut_at(lut, lut_off(q.x + kb)) + lut_at(lut, lut_off(q.y + kb)) +
-                           lut_at(lut, lut_off(q.z + kb)) + lut_at(lut, lut_off(q.w + kb));
+                    const uint4 v = src[g * B];
+                    acc += lut_at(lut, lut_off(v.x + kb)) + lut_at(lut, lut_off(v.y + kb)) +
+                           lut_at(lut, lut_off(v.z + kb)) + lut_at(lut, lut_off(v.w + kb));
                 }
                 if (rem) {
-                    const uint4 q = m4[full * B];
-                    acc += lut_at(lut, lut_off(q.x + kb));
-                    if (rem > 1) acc += lut_at(lut, lut_off(q.y + kb));
-                    if (rem > 2) acc += lut_at(lut, lut_off(q.z + kb));
-                }
-            } else if (i & 1) {
-                // Only monomers j = i (mod 2) can sit on a neighbour of the
-                // end: words 1 and 3 of each group.
-#pragma unroll 2
-                for (int g = 0; g < full; ++g) {
-                    const uint4 q = m4[g * B];
-                    acc += lut_at(lut, lut_off(q.y + kb)) + lut_at(lut, lut_off(q.w + kb));
-                }
-                if (rem > 1) acc += lut_at(lut, lut_off(m4[full * B].y + kb));
-            } else {
-                // Words 0 and 2.
-#pragma unroll 2
-                for (int g = 0; g < full; ++g) {
-                    const uint4 q = m4[g * B];
-                    acc += lut_at(lut, lut_off(q.x + kb)) + lut_at(lut, lut_off(q.z + kb));
-                }
-                if (rem) {
-                    const uint4 q = m4[full * B];
-                    acc += lut_at(lut, lut_off(q.x + kb));
-                    if (rem > 2) acc += lut_at(lut, lut_off(q.z + kb));
+                    const uint4 v = src[full * B];
+                    acc += lut_at(lut, lut_off(v.x + kb));
+                    if (rem > 1) acc += lut_at(lut, lut_off(v.y + kb));
+                    if (rem > 2) acc += lut_at(lut, lut_off(v.z + kb));
                 }
             }
             const uint32_t freem = ~acc & 63u;
@@ -133,7 +124,7 @@ __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c,
             cnt += 1ull << (9 * m);
             const uint32_t axis_step = 1u << (10 * (sel >> 1));
             key = (sel & 1) ? key - axis_step : key + axis_step;
-            my[(i >> 2) * 4 * B + (i & 3)] = key;
+            my[((i & 1) * pstride + (i >> 3) * B) * 4 + ((i >> 1) & 3)] = key;
             ex = (int)(key & 1023u) - 512;
             ey = (int)((key >> 10) & 1023u) - 512;
             ez = (int)(key >> 20) - 512;
@@ -242,7 +233,7 @@ __global__ void __launch_bounds__(256) lattice_retry_kernel(const LatticeArgs a,
     const int wpb = blockDim.x / 32, wib = threadIdx.x / 32, lane = threadIdx.x & 31;
     uint32_t *rq = smem + kLutWords + kSelBytes / 4 + 8 + 16 + (size_t)wib * 64;   // [2][32]
     uint32_t *keys = smem + kLutWords + kSelBytes / 4 + 8 + 16 + (size_t)wpb * 64 +
-                     (size_t)wib * ((a.N + 3) & ~3) * 32;
+                     (size_t)wib * key_groups(a.N) * 2 * 4 * 32;
 
     fill_tables(lut, seltab);
     if (threadIdx.x < 8) {
@@ -610,8 +601,8 @@ __global__ void __launch_bounds__(256) lattice_long_kernel(const LatticeArgs a, 
 
 size_t lattice_smem_bytes(int N, int B)
 {
-    // Tables, then the keys in groups of four monomers per lane.
-    return (size_t)(kLutWords + kSelBytes / 4 + 8 + 16) * 4 + (size_t)((N + 3) & ~3) * B * 4;
+    // Tables, then the keys: two parities of key_groups(N) 16-byte groups per lane.
+    return (size_t)(kLutWords + kSelBytes / 4 + 8 + 16) * 4 + (size_t)key_groups(N) * 2 * 16 * B;
 }
 
 // Block size: the largest multiple of 32 (at most 256) whose coordinate
@@ -708,7 +699,7 @@ int lattice_retry_launch(const LatticeArgs &a, int N, int B, int64_t c_lo, int64
 {
     const int wpb = B / 32;
     const size_t smem = (size_t)(kLutWords + kSelBytes / 4 + 8 + 16) * 4 +
-                        (size_t)wpb * (64 * 4 + (size_t)((N + 3) & ~3) * 32 * 4);
+                        (size_t)wpb * (64 * 4 + (size_t)key_groups(N) * 2 * 16 * 32);
     auto kern = a.isaw ? lattice_retry_kernel<true> : lattice_retry_kernel<false>;
     cudaError_t e = allow_max_smem(kern);
     int bps = 0, dev = 0, sms = 0;
