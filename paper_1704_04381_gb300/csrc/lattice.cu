@@ -44,13 +44,14 @@ __host__ __device__ __forceinline__ int key_groups(int N) { return ((N + 1) / 2 
 
 
 // Growth number att of chain c (local index) of the ensemble described by a,
-// in this lane.  The keys sit in 16-byte groups of four monomers of one
-// parity: key j (parity p = j % 2, h = j / 2) is word h % 4 of group h / 4 of
-// parity p, the lane's groups are B apart, and the parities lie kGroups(N)
-// groups apart ([p][h / 4][lane][h % 4]).  One 128-bit load brings four keys
-// of one parity, and the 32 lanes of a warp read 512 contiguous bytes (no
-// bank conflict).  The athermal scan reads one parity, the interacting scan
-// both.  my points at the lane's first group.  Returns true when the growth was trapped and another
+// in this lane.  The keys sit in 16-byte groups of four monomers, the lane's
+// groups B apart, so one 128-bit load brings four keys and the 32 lanes of a
+// warp read 512 contiguous bytes (no bank conflict).  The interacting scan
+// reads every monomer: key j is word j % 4 of group j / 4 ([j / 4][lane]
+// [j % 4]).  The athermal scan reads one parity: key j (p = j % 2, h = j / 2)
+// is word h % 4 of group h / 4 of parity p, the parities key_groups(N)
+// groups apart ([p][h / 4][lane][h % 4]).  my points at the lane's first
+// group.  Returns true when the growth was trapped and another
 // attempt is allowed (restart mode): the caller grows the chain again with
 // att + 1 (the outputs then hold nothing final for it).  Otherwise the
 // chain's outputs are written and false is returned.
@@ -91,27 +92,24 @@ __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c,
         for (int i = 1; i < N; ++i) {
             uint32_t acc = 0u;
             const uint32_t kb = kNearBias - key;
-            // Monomers j = i (mod 2) can sit on a neighbour of the end (the
-            // athermal scan needs only them); j = i + 1 (mod 2) can touch one.
-            // Of parity q, monomers 0 .. i-2 hold (i - q) / 2 keys.
-#pragma unroll
-            for (int pass = 0; pass < (kIsaw ? 2 : 1); ++pass) {
-                const int q = (i + pass) & 1;
-                const int n = (i - q) >> 1;
-                const uint4 *src = m4 + q * pstride;
-                const int full = n >> 2, rem = n & 3;
+            // Interacting: monomers 0 .. i-2.  Athermal: only monomers
+            // j = i (mod 2) can sit on a neighbour of the end; of that parity
+            // q, monomers 0 .. i-2 hold (i - q) / 2 keys.
+            const int q = i & 1;
+            const int n = kIsaw ? i - 1 : (i - q) >> 1;
+            const uint4 *src = kIsaw ? m4 : m4 + q * pstride;
+            const int full = n >> 2, rem = n & 3;
 #pragma unroll 2
-                for (int g = 0; g < full; ++g) {
-                    const uint4 v = src[g * B];
-                    acc += lut_at(lut, lut_off(v.x + kb)) + lut_at(lut, lut_off(v.y + kb)) +
-                           lut_at(lut, lut_off(v.z + kb)) + lut_at(lut, lut_off(v.w + kb));
-                }
-                if (rem) {
-                    const uint4 v = src[full * B];
-                    acc += lut_at(lut, lut_off(v.x + kb));
-                    if (rem > 1) acc += lut_at(lut, lut_off(v.y + kb));
-                    if (rem > 2) acc += lut_at(lut, lut_off(v.z + kb));
-                }
+            for (int g = 0; g < full; ++g) {
+                const uint4 v = src[g * B];
+                acc += lut_at(lut, lut_off(v.x + kb)) + lut_at(lut, lut_off(v.y + kb)) +
+                       lut_at(lut, lut_off(v.z + kb)) + lut_at(lut, lut_off(v.w + kb));
+            }
+            if (rem) {
+                const uint4 v = src[full * B];
+                acc += lut_at(lut, lut_off(v.x + kb));
+                if (rem > 1) acc += lut_at(lut, lut_off(v.y + kb));
+                if (rem > 2) acc += lut_at(lut, lut_off(v.z + kb));
             }
             const uint32_t freem = ~acc & 63u;
             const int m = __popc(freem);
@@ -124,7 +122,8 @@ __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c,
             cnt += 1ull << (9 * m);
             const uint32_t axis_step = 1u << (10 * (sel >> 1));
             key = (sel & 1) ? key - axis_step : key + axis_step;
-            my[((i & 1) * pstride + (i >> 3) * B) * 4 + ((i >> 1) & 3)] = key;
+            if (kIsaw) my[(i >> 2) * 4 * B + (i & 3)] = key;
+            else my[((i & 1) * pstride + (i >> 3) * B) * 4 + ((i >> 1) & 3)] = key;
             ex = (int)(key & 1023u) - 512;
             ey = (int)((key >> 10) & 1023u) - 512;
             ez = (int)(key >> 20) - 512;
