@@ -712,6 +712,22 @@ def run_perm(args):
     print(json.dumps(line), flush=True)
 
 
+def run_store(args):
+    """Config 3 with conformations written out (chains from --chains)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1704_04381_gb300 import rosen
+    torch.cuda.set_device(0)
+    r = store_coords_leg(rosen, torch, steps=args.steps)
+    line = {"metric": "real-space hard spheres N=64 k=32 with conformations stored: write GB/s",
+            "value": r["write_gb_per_s"], "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+            "ms_per_step": r["ms"], "higher_is_better": True, "dtype": "fp32",
+            "data": "synthetic", "config": {"workload": r["workload"], "chains": C},
+            "store_coords": r}
+    print(json.dumps(line), flush=True)
+
+
 def run_batched(args):
     import torch
     import __graft_entry__
@@ -756,7 +772,7 @@ def store_coords_leg(rosen, torch, steps=2):
     written = 12 * N * C
     peak = measured_peak("hbm_gbs", 6800.0)
     gbs = written / (res["coords"] / 1e3) / 1e9
-    return {"workload": "real-space hard spheres N=64 k=32, 1e7 chains, conformations stored",
+    return {"workload": "real-space hard spheres N=64 k=32, %d chains, conformations stored" % C,
             "ms": res["coords"], "ms_without_coords": res["no_coords"],
             "coords_bytes_per_launch": written,
             "write_gb_per_s": gbs, "hbm_peak_gb_per_s": peak,
@@ -1066,7 +1082,7 @@ def main():
     ap.add_argument("--chains", type=int, default=None,
                     help="chains per ensemble (default 10^7); smaller values are for profiling")
     ap.add_argument("--workload", default="step",
-                    choices=["step", "batched", "served", "long", "perm"])
+                    choices=["step", "batched", "served", "long", "perm", "store"])
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="scale of the chain counts in the batched/served modes")
     ap.add_argument("--rate", type=float, default=2000.0, help="served: arrivals per second")
@@ -1104,6 +1120,8 @@ def main():
     if args.chains:
         global C
         C = args.chains
+    if args.workload == "store":
+        return run_store(args)
     if args.impl == "reference":
         run_reference(args)
     else:
