@@ -51,6 +51,13 @@ UNIT = "insertions/s"
 BRUTE_LAT_PAIR, BRUTE_LAT_STEP = 7, 100
 BRUTE_OFF_PAIR, BRUTE_OFF_TRIAL = 8, 90
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant growth -- hard spheres, N = 64, k = 32, 10^7 chains, both
+# passes -- from one ncu capture of that launch: first pass 23,213,312 +
+# 78,660,864, second pass 18,835,968 + 17,702,912.  Reported as the
+# roofline's traffic for that configuration only.
+HS_TRAFFIC_BYTES = 23213312 + 78660864 + 18835968 + 17702912
+
 
 def brute_lattice_ops(N):
     return BRUTE_LAT_PAIR * (N - 1) * (N - 2) // 2 + BRUTE_LAT_STEP * (N - 1)
@@ -375,7 +382,11 @@ def run_ours(args):
         "parts": parts,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                      "unit": "Tops/s (32-bit lane ops)", "frac": achieved / peak,
-                     "traffic": None, "kernel": kname, "ops_per_chain": sops / C,
+                     "traffic": (HS_TRAFFIC_BYTES if (REAL_POT == "hard_sphere" and C == 10_000_000
+                                                      and K_TRIALS == 32 and args.max_attempts <= 1
+                                                      and "hard sphere" in kname) else None),
+                     "traffic_unit": "DRAM bytes per launch (ncu, both passes)",
+                     "kernel": kname, "ops_per_chain": sops / C,
                      "ops_basis": "brute-force work: every earlier monomer tested against every trial",
                      "executed_ops_per_chain": ops / C, "executed_frac": executed / peak,
                      "peak_basis": "%d SMs x 128 lanes x %.0f MHz (max SM clock)" % (sms, mhz)},

@@ -102,9 +102,19 @@ __device__ __forceinline__ uint64_t cell_key(int cx, int cy, int cz)
 
 __device__ __forceinline__ int cell_coord(float x, float inv) { return (int)floorf(x * inv); }
 
+// First probe of a cell: the low bits of its three coordinates side by side
+// (x fastest), so the 27 cells around the end sit in 9 runs of 3 adjacent
+// entries and a moving end reuses the entries it read at the last steps.
+// Distant cells whose low bits agree share a probe sequence; the table holds
+// at most half as many cells as entries, so every sequence ends at an empty
+// entry.
 __device__ __forceinline__ uint32_t cell_slot(uint64_t key, int logH)
 {
-    return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - logH));
+    const int bx = (logH + 2) / 3, by = (logH + 1) / 3, bz = logH - bx - by;
+    const uint32_t x = (uint32_t)key & ((1u << bx) - 1u);
+    const uint32_t y = (uint32_t)(key >> 16) & ((1u << by) - 1u);
+    const uint32_t z = (uint32_t)(key >> 32) & ((1u << bz) - 1u);
+    return x | (y << bx) | (z << (bx + by));
 }
 
 // First bead of the cell whose tagged key is `want` (-1: no bead there).
