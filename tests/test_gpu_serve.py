@@ -311,3 +311,48 @@ def test_pool_failure_returns_the_reservation(rosen):
         assert srv.info()["bytes_in_use"] == 0
     finally:
         srv.close()
+
+
+def test_sliced_requests_equal_the_single_ensemble_path(rosen):
+    # Requests large enough for several slices (chain ranges on two streams
+    # per request) equal the single-ensemble entry points bit for bit:
+    # lattice in restart mode (the retry kernel over ranges that start above
+    # chain 0), two-pass hard spheres (the deferral mask shared by the
+    # slices), and real space in restart mode.
+    L, R = rosen.ROSEN_MODEL_LATTICE, rosen.ROSEN_MODEL_OFFLATTICE
+    cases = [
+        rosen.request(L, 64, 12_000_000, 61, 0, beta_eps=0.3, max_attempts=8),
+        rosen.request(R, 64, 1_500_000, 62, 1, k=32),
+        rosen.request(R, 48, 600_000, 63, 2, k=16, sigma=1.2, max_attempts=4),
+    ]
+    srv = rosen.RosenServer(mem_budget_bytes=8 << 30, max_slots=4)
+    try:
+        tickets = [srv.submit(r) for r in cases]
+        got = []
+        for t in tickets:
+            st, res = srv.wait(t, 300)
+            assert st == rosen.ROSEN_OK and res["status"] == rosen.ROSEN_OK, res
+            got.append(res["stats"])
+    finally:
+        srv.close()
+    for r, g in zip(cases, got):
+        st = rosen.stats_tensor()
+        ws = rosen.reduce_workspace(r.C)
+        if r.model == L:
+            out = rosen.lattice_outputs(r.N, r.C, attempts=True)
+            rosen.rosen_lattice_grow(rosen.lattice_params(r.seed, r.N, r.C, beta_eps=r.beta_eps,
+                                                          ensemble=r.ensemble,
+                                                          max_attempts=r.max_attempts), out)
+            rosen.rosen_reduce(rosen.lattice_reduce_in(out, r.N, 0), st, ws)
+        else:
+            out = rosen.offlattice_outputs(r.N, r.C, attempts=r.max_attempts > 1)
+            rosen.rosen_offlattice_grow(
+                rosen.offlattice_params(r.seed, r.N, r.C, r.k, potential=r.potential,
+                                        sigma=r.sigma, ensemble=r.ensemble,
+                                        max_attempts=r.max_attempts), out)
+            rosen.rosen_reduce(rosen.offlattice_reduce_in(out, r.N, r.k), st, ws)
+        ref = rosen.stats_dict(st)
+        for key in rosen.STAT_KEYS:
+            assert g[key] == ref[key] or (np.isnan(g[key]) and np.isnan(ref[key])), (r.N, key)
+        del out
+        torch.cuda.empty_cache()
