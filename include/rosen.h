@@ -92,9 +92,11 @@ typedef struct rosen_lattice_params {
     int32_t N;                /* monomers per chain, 2 <= N <= 512          */
     int64_t C;                /* chains, C >= 0                             */
     int64_t chain0;           /* global index of chain 0; chain0+C <= 2^32  */
-    double beta_eps;          /* >= 0, finite.  0: athermal SAW.  > 0: each
-                                 non-bonded nearest-neighbour contact has
-                                 energy -eps (interacting SAW)              */
+    double beta_eps;          /* 0 <= beta_eps <= 16.  0: athermal SAW.  > 0:
+                                 each non-bonded nearest-neighbour contact has
+                                 energy -eps (interacting SAW); the bound
+                                 keeps the FP32 factor exp(5 beta_eps) of a
+                                 site with five contacts finite             */
     uint32_t flags;           /* ROSEN_STORE_TRACE | ROSEN_STORE_COORDS     */
     int32_t lanes_per_chain;  /* 0 = automatic; else 1 (one chain per lane) */
     int32_t max_attempts;     /* 0 or 1: a trapped chain keeps W = 0.  2 ..
@@ -138,7 +140,7 @@ typedef struct rosen_lattice_out {
  * sequential implementation of the same rule in FP64 (the FP32 selection
  * falls back to FP64 whenever rounding could change the choice).
  * Errors: EINVAL for N outside [2, 512], C < 0, chain0 + C > 2^32,
- * beta_eps < 0 or not finite, unknown flags or lanes_per_chain,
+ * beta_eps outside [0, 16], unknown flags or lanes_per_chain,
  * max_attempts outside [0, ROSEN_MAX_ATTEMPTS].
  */
 ROSEN_API int rosen_lattice_grow(const rosen_lattice_params *p, const rosen_lattice_out *o,
@@ -389,7 +391,7 @@ typedef struct rosen_perm_params {
     int32_t N;                /* monomers per chain, 2 <= N <= 512           */
     int64_t M0;               /* chains started, >= 1                        */
     int64_t max_population;   /* cap, M0 <= max_population <= 2^24            */
-    double beta_eps;          /* contact attraction (0: athermal), >= 0       */
+    double beta_eps;          /* contact attraction (0: athermal), [0, 16]    */
     double mu;                /* threshold growth per step, > 0               */
     double c_hi, c_lo;        /* enrichment / pruning factors, 0 <= c_lo < c_hi
                                  (c_hi may be +inf)                           */

@@ -71,7 +71,7 @@ __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c,
     int sx, sy, sz, sq;
     int ex, ey, ez;
     uint64_t cnt;      // 9-bit field m holds the number of steps with m free sites
-    float lw;
+    LogW lw;      // interacting: product of the step factors
     int dead_at;
     if (a.coords && att == 0) {
         a.coords[(0 * 3 + 0) * C + c] = 0;
@@ -86,7 +86,7 @@ __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c,
         sx = sy = sz = sq = 0;
         ex = ey = ez = 0;
         cnt = 0;
-        lw = 0.f;
+        lw = LogW();
         dead_at = 0;
 
         for (int i = 1; i < N; ++i) {
@@ -163,12 +163,15 @@ __device__ __forceinline__ bool lattice_attempt(const LatticeArgs &a, int64_t c,
                 for (int q = 0; q < 3; ++q) a.coords[((int64_t)i * 3 + q) * C + c] = 0;
         return false;
     }
+    float logw;
     if (!kIsaw) {
-        lw = 0.f;
+        logw = 0.f;
 #pragma unroll
-        for (int q = 2; q <= 6; ++q) lw += (float)cm[q] * a.logm[q];
+        for (int q = 2; q <= 6; ++q) logw += (float)cm[q] * a.logm[q];
+    } else {
+        logw = lw.value();
     }
-    if (a.logw) a.logw[c] = lw;
+    if (a.logw) a.logw[c] = logw;
     if (a.r2) a.r2[c] = ex * ex + ey * ey + ez * ez;
     if (a.n2rg2)
         a.n2rg2[c] = (int64_t)N * sq -
@@ -415,7 +418,7 @@ __device__ __forceinline__ bool long_attempt(const LatticeArgs &a, int64_t c, ui
     int ex = 0, ey = 0, ez = 0;
     int64_t sx = 0, sy = 0, sz = 0, sq = 0;
     uint64_t cnt_lo = 0ull, cnt_hi = 0ull;   // 16-bit fields: m = 0..3 | 4..7
-    float lw = 0.f;
+    LogW lw;      // interacting: product of the step factors
     int dead_at = 0;
 
     for (int i = 1; i < N; ++i) {
@@ -552,15 +555,18 @@ __device__ __forceinline__ bool long_attempt(const LatticeArgs &a, int64_t c, ui
                 for (int q = 0; q < 3; ++q) a.coords[((int64_t)i * 3 + q) * C + c] = 0;
         return false;
     }
+    float logw;
     if (!kIsaw) {
-        lw = 0.f;
+        logw = 0.f;
 #pragma unroll
         for (int q = 2; q <= 6; ++q) {
             const uint32_t cm = (uint32_t)(((q < 4 ? cnt_lo : cnt_hi) >> (16 * (q & 3))) & 0xFFFFu);
-            lw += (float)cm * a.logm[q];
+            logw += (float)cm * a.logm[q];
         }
+    } else {
+        logw = lw.value();
     }
-    if (a.logw) a.logw[c] = lw;
+    if (a.logw) a.logw[c] = logw;
     if (a.r2) a.r2[c] = ex * ex + ey * ey + ez * ez;
     if (a.n2rg2) a.n2rg2[c] = (int64_t)N * sq - (sx * sx + sy * sy + sz * sz);
     return false;
@@ -625,8 +631,9 @@ int lattice_validate(const rosen_lattice_params *p, const rosen_lattice_out *o, 
     if (p->C < 0 || p->chain0 < 0 || p->chain0 + p->C > (int64_t(1) << 32))
         return set_error(ROSEN_EINVAL, "%s: chains [%lld, %lld) outside [0, 2^32)", fn,
                          (long long)p->chain0, (long long)(p->chain0 + p->C));
-    if (!(p->beta_eps >= 0.0) || !isfinite(p->beta_eps))
-        return set_error(ROSEN_EINVAL, "%s: beta_eps must be finite and >= 0", fn);
+    if (!(p->beta_eps >= 0.0) || !(p->beta_eps <= 16.0))
+        return set_error(ROSEN_EINVAL, "%s: beta_eps must lie in [0, 16] (the FP32 Boltzmann "
+                                       "factor of five contacts must be finite)", fn);
     if (p->flags & ~(ROSEN_STORE_TRACE | ROSEN_STORE_COORDS))
         return set_error(ROSEN_EINVAL, "%s: unknown flags 0x%x", fn, p->flags);
     if (p->lanes_per_chain != 0 && p->lanes_per_chain != 1)

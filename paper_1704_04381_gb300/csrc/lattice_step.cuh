@@ -126,16 +126,41 @@ __device__ __noinline__ int select_fp64(uint32_t freem, uint32_t acc, uint32_t x
     return sel;
 }
 
+// log W of an interacting chain: the running product of its step factors S
+// (each >= 1, finite: beta_eps <= 16) as an FP32 mantissa in [1, 2) and an
+// integer exponent, so that a step costs a multiply and an exact rescale
+// instead of a logarithm; log W = log(mantissa) + exponent ln 2 once, at the
+// end.  Each product rounds by at most 2^-24, so log W is within
+// (N - 1) 6e-8 of the exact sum of the logarithms, plus the final rounding.
+struct LogW {
+    float m = 1.f;
+    int e = 0;
+    __device__ __forceinline__ void mul(float S)
+    {
+        const int b = __float_as_int(m * S);
+        const int k = ((b >> 23) & 0xFF) - 127;
+        m = __int_as_float(b - (k << 23));
+        e += k;
+    }
+    __device__ __forceinline__ float value() const
+    {
+        constexpr float kLn2Hi = 0.693145751953125f;        // ln 2 to 16 bits
+        constexpr float kLn2Lo = 1.428606820309417e-6f;     // ln 2 - kLn2Hi
+        const float E = (float)e;
+        return fmaf(E, kLn2Hi, fmaf(E, kLn2Lo, logf(m)));
+    }
+};
+
 // The neighbour taken at one step, in slot order, from the free mask, the
 // contact fields of acc (bits 8+3d..10+3d: contacts of neighbour d) and the
 // step's draw x.  Athermal: the idx-th free neighbour, idx = floor(x m / 2^32).
 // Interacting: the smallest slot whose FP32 prefix sum of exp(beta_eps c_d)
 // exceeds r = u24(x) S, re-taken in FP64 when r lies within 2^-18 S of the
-// slot's bounds; log S is added to lw.
+// slot's bounds; S goes into the chain's weight product lw.
 template <bool kIsaw>
 __device__ __forceinline__ int choose(uint32_t freem, int m, uint32_t acc, uint32_t x,
                                       const uint8_t *seltab, const float *wt32,
-                                      const double *wt64, float &lw)
+                                      const double *wt64, LogW &lw)
 {
     if (!kIsaw) return seltab[(freem << 3) | __umulhi(x, (uint32_t)m)];
     float w[6], S = 0.f;
@@ -160,7 +185,7 @@ __device__ __forceinline__ int choose(uint32_t freem, int m, uint32_t acc, uint3
     }
     const float tol = S * 0x1p-18f;
     if (sel < 0 || !(r - lo > tol) || !(hi - r > tol)) sel = select_fp64(freem, acc, x, wt64);
-    lw += logf(S);
+    lw.mul(S);
     return sel;
 }
 

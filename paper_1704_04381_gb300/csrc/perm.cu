@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
         if (m > 0) {
             const uint32_t x =
                 philox(make_uint4((uint32_t)j, a.ens, (uint32_t)i, 0u), a.key).x;
-            float lw_unused = 0.f;
+            LogW lw_unused;
             const int sel = choose<kIsaw>(freem, m, acc, x, seltab, wt32, wt64, lw_unused);
             // The step's weight factor in FP64: m, or the sum of the free
             // neighbours' Boltzmann factors in slot order.
@@ -497,8 +497,8 @@ int perm_validate(const rosen_perm_params *p, const rosen_perm_out *o)
     if (p->M0 < 1 || p->max_population < p->M0 || p->max_population > ROSEN_PERM_MAX_POP)
         return set_error(ROSEN_EINVAL, "rosen_perm_run: need 1 <= M0 <= max_population <= %d",
                          (int)ROSEN_PERM_MAX_POP);
-    if (!(p->beta_eps >= 0.0) || !isfinite(p->beta_eps))
-        return set_error(ROSEN_EINVAL, "rosen_perm_run: beta_eps must be finite and >= 0");
+    if (!(p->beta_eps >= 0.0) || !(p->beta_eps <= 16.0))
+        return set_error(ROSEN_EINVAL, "rosen_perm_run: beta_eps must lie in [0, 16]");
     if (!(p->mu > 0.0) || !isfinite(p->mu))
         return set_error(ROSEN_EINVAL, "rosen_perm_run: mu must be finite and > 0");
     if (!(p->c_lo >= 0.0) || !(p->c_hi > p->c_lo) || isinf(p->c_lo))

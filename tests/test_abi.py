@@ -95,6 +95,7 @@ def _grow(rosen, **kw):
 @pytest.mark.parametrize("kw", [
     dict(N=1), dict(N=513), dict(C=-1), dict(chain0=-5), dict(chain0=2 ** 32 - 5, C=10),
     dict(beta_eps=-0.1), dict(beta_eps=float("nan")), dict(beta_eps=float("inf")),
+    dict(beta_eps=16.5),
     dict(flags=8), dict(flags=1), dict(flags=2), dict(lanes_per_chain=3),
     dict(max_attempts=-1), dict(max_attempts=65536),
 ])
