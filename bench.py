@@ -368,11 +368,17 @@ def run_ours(args):
             sf = args.served_policy == "shortest_first"
             served5 = served_run(rosen, 2000.0, args.served_duration, 40.0, 256, 1.0,
                                  shortest_first=sf, replay_every=5, torch=torch)
-            # The sustainable rate: 0.7 x the completion rate under saturation.
-            cap = served5["completed"] / served5["wall_s"]
+            # The sustainable rate: 0.7 x the GPU's capacity for the offered
+            # mix (requests completed under saturation are the smaller ones,
+            # so their rate overstates it).
+            cap, ncap = offered_capacity(rosen, torch)
             served_ok = served_run(rosen, max(1.0, 0.7 * cap), args.served_duration, 40.0, 256,
-                                   1.0, shortest_first=sf)
+                                   1.0, shortest_first=sf, replay_every=5, torch=torch)
             served_ok["capacity_requests_per_s"] = cap
+            served_ok["capacity_basis"] = ("1 / mean time alone of %d requests of the offered "
+                                           "mix (every 16th of the arrival pool)" % ncap)
+            served_ok["completed_per_s_under_saturation"] = (served5["completed"] /
+                                                             served5["wall_s"])
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -672,8 +678,11 @@ def perm_leg(rosen, torch, steps=3, warmup=1):
     mu = 4.684.  value = chain steps grown per second (every chain of the
     population before step i makes one step).  Algorithmic bytes per step of
     a chain: the scan of its earlier monomers of matching parity (4 B each),
-    then the copy of its i + 1 keys into the next population (read and
-    write, per copy), against the measured HBM bandwidth."""
+    the new monomer's key (4 B), its weight read and written (24 B) and its
+    place in the population read and written (8 B), against the measured HBM
+    bandwidth.  The keys an enrichment copy takes are not counted (the
+    outputs do not say how many copies were made), so the figure is a lower
+    bound."""
     c = PERM_CFG
     N, M0, cap = c["N"], c["M0"], c["cap"]
     p = rosen.perm_params(c["seed"], N, M0, cap, mu=c["mu"], c_hi=c["c_hi"], c_lo=c["c_lo"])
@@ -693,19 +702,19 @@ def perm_leg(rosen, torch, steps=3, warmup=1):
     pop = out["population"].cpu().tolist()
     logz = out["logz"].cpu().tolist()
     grown = sum(pop[i - 1] for i in range(1, N))
-    nbytes = sum(pop[i - 1] * 4 * (i // 2) + pop[i] * 8 * (i + 1) + pop[i] * 24
-                 for i in range(1, N))
+    nbytes = sum(pop[i - 1] * (4 * (i // 2) + 4 + 24 + 8) for i in range(1, N))
     peak = measured_peak("hbm_gbs", 6800.0)
     gbs = nbytes / (ms / 1e3) / 1e9
     return {"workload": "PERM athermal N=64, M0=1e6 chains started, cap 4e6, mu=4.684, "
                         "c_hi=3, c_lo=1/3, seed 9",
             "ms": ms, "chain_steps": grown, "chain_steps_per_s": grown / (ms / 1e3),
             "population_final": pop[-1], "population_max": max(pop),
-            "logZ_N": logz[-1], "launches_per_run": 4 * (N - 1) + 2,
+            "logZ_N": logz[-1], "launches_per_run": 3 * (N - 1) + 2,
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                          "frac": gbs / peak, "traffic": None,
-                         "basis": "per chain step: 4 B per scanned key (parity), 8 B per copied "
-                                  "key (read + write) and 24 B of weights, per copy"}}
+                         "basis": "per chain step: 4 B per scanned key (parity), 4 B new key, "
+                                  "24 B weight (read + write), 8 B slot number (read + write); "
+                                  "enrichment copies not counted (lower bound)"}}
 
 
 def run_perm(args):
@@ -993,12 +1002,29 @@ def served_run(rosen, rate, duration, budget_gb, max_queue, scale, shortest_firs
            "duration_s": duration, "budget_gb": budget_gb, "max_queue": max_queue,
            "store_coords_fraction": 0.2, "shortest_first": bool(shortest_first)}
     if replay_every and ok:
-        order = sorted(r["ticket"] for r in ok)
-        sample = [reqs[t] for t in order[::replay_every]]
-        ms = replay_single(rosen, torch, sample)
+        by_ticket = {r["ticket"]: r for r in ok}
+        order = sorted(by_ticket)
+        picked = order[::replay_every]
+        sample = [reqs[t] for t in picked]
+        ms, each = replay_single(rosen, torch, sample)
         w_all = sum(request_cost(reqs[t]) for t in order)
         w_smp = sum(request_cost(e) for e in sample)
         est = ms / 1e3 * w_all / w_smp
+        # Slowdown: a sampled request's served latency over its own time on
+        # an idle GPU (grow + reduce alone); latency by that time.
+        alone = np.array(each)
+        lat_s = np.array([(by_ticket[t]["t_done_ns"] - by_ticket[t]["t_submit_ns"]) / 1e6
+                          for t in picked])
+        slow = lat_s / np.maximum(alone, 1e-3)
+        bins = {}
+        for name, lo_ms, hi_ms in (("alone_lt_10ms", 0.0, 10.0), ("alone_10_100ms", 10.0, 100.0),
+                                   ("alone_ge_100ms", 100.0, float("inf"))):
+            sel = (alone >= lo_ms) & (alone < hi_ms)
+            if sel.any():
+                bins[name] = {"requests": int(sel.sum()),
+                              "p50": float(np.percentile(lat_s[sel], 50)),
+                              "p99": float(np.percentile(lat_s[sel], 99)),
+                              "max": float(lat_s[sel].max())}
         out["single_path"] = {
             "replayed_requests": len(sample), "replayed_ms": ms,
             "estimated_s_for_all_completed": est,
@@ -1006,12 +1032,26 @@ def served_run(rosen, rate, duration, budget_gb, max_queue, scale, shortest_firs
             "basis": "every %d-th completed request grown and reduced alone through "
                      "rosen_*_grow + rosen_reduce, scaled to all completed requests by "
                      "C N^2 (x 8k for real space)" % replay_every}
+        out["slowdown"] = {"p50": float(np.percentile(slow, 50)),
+                           "p99": float(np.percentile(slow, 99)), "max": float(slow.max()),
+                           "basis": "served latency / time alone, over the replayed sample"}
+        out["latency_ms_by_time_alone"] = bins
     return out
+
+
+def offered_capacity(rosen, torch, every=16):
+    """Requests/s one GPU serves from the offered mix: 1 / the mean time of a
+    request grown and reduced alone, over every `every`-th request of the
+    arrival pool (the mix as offered, not as completed)."""
+    pool = batch_config(rosen, n_ens=4096, seed=5, scale=1.0)
+    sample = pool[::every]
+    ms, _ = replay_single(rosen, torch, sample)
+    return 1e3 * len(sample) / ms, len(sample)
 
 
 def replay_single(rosen, torch, reqs):
     """Grow and reduce the requests one after another through the
-    single-ensemble entry points (CUDA events; ms)."""
+    single-ensemble entry points (CUDA events): total ms and ms per request."""
     stream = torch.cuda.current_stream()
     ws = rosen.reduce_workspace(max(r.C for r in reqs))
     st = rosen.stats_tensor()
@@ -1035,16 +1075,16 @@ def replay_single(rosen, torch, reqs):
     torch.cuda.synchronize()
     del keep
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    total = 0.0
+    each = []
     for r in reqs:
         o = None
         e0.record(stream)
         o = one(r)
         e1.record(stream)
         torch.cuda.synchronize()
-        total += e0.elapsed_time(e1)
+        each.append(e0.elapsed_time(e1))
         del o
-    return total
+    return sum(each), each
 
 
 def run_served(args):

@@ -412,8 +412,9 @@ typedef struct rosen_perm_out {
                                  axis a at [q][a][c]                             */
 } rosen_perm_out;
 
-/* Bytes of workspace rosen_perm_run needs (two populations of packed keys,
- * weights, scan arrays): about 8 N + 45 bytes per chain of the cap; 0 for
+/* Bytes of workspace rosen_perm_run needs (a storage slot of packed keys per
+ * chain of the cap, the population as slot numbers, weights, a stack of free
+ * slots, scan counts): about 4 N + 45 bytes per chain of the cap; 0 for
  * arguments out of range. */
 ROSEN_API size_t rosen_perm_workspace_size(int32_t N, int64_t max_population);
 /*
@@ -421,7 +422,7 @@ ROSEN_API size_t rosen_perm_workspace_size(int32_t N, int64_t max_population);
  * caller; workspace: device, 256-byte aligned, at least
  * rosen_perm_workspace_size bytes, contents need not be initialised.  The
  * population size stays on the device (no host synchronisation); about
- * 4 N kernel launches.  Errors: EINVAL (N, M0, cap, beta_eps, mu, c_hi,
+ * 3 N kernel launches.  Errors: EINVAL (N, M0, cap, beta_eps, mu, c_hi,
  * c_lo or flags out of range, a required output missing), ENOMEM (workspace
  * too small), ECUDA.
  */

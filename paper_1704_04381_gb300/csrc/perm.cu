@@ -10,25 +10,35 @@
 // Eq. 2.  The paper's conclusion names a GPU PERM whose text is not
 // available; the readings taken here are stated at rosen_perm_run.
 //
-// GB300 mapping.  The population lives in device memory as packed monomer
-// keys [monomer][chain] (two buffers: the population of this step and the
-// next), with each chain's weight as an FP64 mantissa in [1, 2) and an int32
-// exponent, so every update is one correctly rounded product and every
-// threshold comparison is exact.  A step is four launches, with no host
-// synchronisation (the population size stays on the device):
-//  1. perm_grow_kernel: one lane per chain (grid-stride over the
-//     population) scans the chain's earlier keys with the displacement
-//     table of the lattice kernels, takes the step (same draw, selection
-//     and weight as rosen_lattice_grow), and decides its fate; per-block
-//     partial sums of W and W R^2 for Eq. 9 / Eq. 2;
-//  2. perm_tiles_kernel: an exclusive scan, per tile of 1024 chains, of the
-//     packed counts (chains kept, enrichment requests);
-//  3. perm_top_kernel (one block): the scan of the tile totals, the
-//     population cap (the first max_pop - kept enrichment requests in
-//     population order are granted), the next population size, and the
-//     step's estimates from the partial sums;
-//  4. perm_scatter_kernel: every kept chain (and its copy) is written to its
-//     place in the next population, in order.
+// GB300 mapping.  A chain's packed monomer keys stay in one storage slot of
+// device memory for as long as the chain lives: a slot holds the keys of
+// even monomers, then those of odd monomers, 4 to a 16-byte word, so a lane
+// reads the keys its step scans with 16-byte loads of its own slot.  The
+// population is an array of slot numbers in population order (two buffers:
+// this step's and the next), beside each chain's end key and its weight as
+// an FP64 mantissa in [1, 2) and an int32 exponent, so every update is one
+// correctly rounded product and every threshold comparison is exact.  (The
+// end key sits beside the population, not only in the slot: a step then
+// reads one half of the slot, of the parity it scans.)  A chain that leaves
+// returns its slot to a stack of free slots, and an enrichment copy takes a
+// slot from it and copies the keys there: only copies move keys, not the
+// chains that stay.  A step is three launches, with no host synchronisation
+// (the population size stays on the device):
+//  1. perm_grow_kernel: one lane per chain (whole blocks step through the
+//     population in chunks of 256 chains) scans the chain's earlier keys
+//     with the displacement table of the lattice kernels, takes the step
+//     (same draw, selection and weight as rosen_lattice_grow), appends the
+//     new key to its slot and decides its fate; the slots of chains that
+//     leave go to the free stack; per chunk the chains kept and the
+//     enrichment requests; per-block partial sums of W and W R^2 for
+//     Eq. 9 / Eq. 2;
+//  2. perm_top_kernel (one block): the exclusive scan of the chunk counts,
+//     the population cap (the first max_pop - kept enrichment requests in
+//     population order are granted), the next population size, the free
+//     slots the copies take, and the step's estimates from the partial sums;
+//  3. perm_scatter_kernel: per chunk, a block scan of the fates places
+//     every kept chain's slot, end key and weight (and its copy's) in the
+//     next population, in order; a copy's keys go to a free slot.
 #include <limits.h>
 #include <math.h>
 #include <string.h>
@@ -42,8 +52,8 @@
 namespace rosen {
 namespace {
 
-constexpr int kPermThreads = 256;
-constexpr int kScanTile = 1024;          // chains per scan tile (4 per thread)
+constexpr int kPermThreads = 256;        // also the chains of a scan chunk
+constexpr int kPermWarps = kPermThreads / 32;
 constexpr int kTopThreads = 1024;
 constexpr int kMaxParts = 8192;          // grow-kernel blocks (partial sums)
 
@@ -73,18 +83,23 @@ struct PermPartial {
 };
 
 struct PermWs {
-    uint32_t *keys[2];          // [N][max_pop]
+    uint32_t *keys;             // [max_pop slots][2][H]: key q of a slot at [q & 1][q >> 1]
+    int32_t *ord[2];            // population position -> slot (this step's, the next)
+    uint32_t *endk[2];          // the end key of the chain at each position
     double *wm[2];
     int32_t *we[2];
+    int32_t *free_slots;        // stack of the slots no chain holds
     int8_t *fate;               // 0 gone, 1 kept, 2 enrichment request, -1 pruning survivor
-    unsigned long long *packed; // kept | enrichment request << 32
-    unsigned long long *excl;   // in-tile exclusive prefix of packed
-    unsigned long long *tiles;  // per tile: total, then exclusive offset
+    unsigned long long *chunks; // per chunk: kept | requests << 32, then the exclusive offset
     PermPartial *parts;
-    long long *ctl;             // [0], [1]: population of the two buffers; [2]: grants
+    long long *ctl;             // [0], [1]: population of the two buffers; [2]: grants;
+                                // [3]: free slots; [4]: free slots after the step's returns
 };
 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Words per half slot: the keys of one parity, rounded up to 16-byte words.
+__host__ __device__ inline int perm_half_words(int N) { return (((N + 1) / 2) + 3) & ~3; }
 
 // Carve the workspace (or, with base == nullptr, measure it).
 size_t perm_carve(void *base, int N, int64_t max_pop, PermWs *w)
@@ -97,17 +112,18 @@ size_t perm_carve(void *base, int N, int64_t max_pop, PermWs *w)
         return r;
     };
     const size_t P = (size_t)max_pop;
-    const size_t tiles = (P + kScanTile - 1) / kScanTile;
+    const size_t chunks = (P + kPermThreads - 1) / kPermThreads;
     PermWs t;
-    for (int b = 0; b < 2; ++b) t.keys[b] = static_cast<uint32_t *>(take(4 * (size_t)N * P));
+    t.keys = static_cast<uint32_t *>(take(4 * 2 * (size_t)perm_half_words(N) * P));
+    for (int b = 0; b < 2; ++b) t.ord[b] = static_cast<int32_t *>(take(4 * P));
+    for (int b = 0; b < 2; ++b) t.endk[b] = static_cast<uint32_t *>(take(4 * P));
     for (int b = 0; b < 2; ++b) t.wm[b] = static_cast<double *>(take(8 * P));
     for (int b = 0; b < 2; ++b) t.we[b] = static_cast<int32_t *>(take(4 * P));
+    t.free_slots = static_cast<int32_t *>(take(4 * P));
     t.fate = static_cast<int8_t *>(take(P));
-    t.packed = static_cast<unsigned long long *>(take(8 * P));
-    t.excl = static_cast<unsigned long long *>(take(8 * P));
-    t.tiles = static_cast<unsigned long long *>(take(8 * tiles));
+    t.chunks = static_cast<unsigned long long *>(take(8 * chunks));
     t.parts = static_cast<PermPartial *>(take(sizeof(PermPartial) * kMaxParts));
-    t.ctl = static_cast<long long *>(take(8 * 4));
+    t.ctl = static_cast<long long *>(take(8 * 8));
     if (w) *w = t;
     return off;
 }
@@ -133,33 +149,72 @@ __device__ __forceinline__ bool below(double wm, int32_t we, const Threshold &t)
     return we < t.e || (we == t.e && wm < t.m);
 }
 
-__global__ void perm_init_kernel(int64_t M0, int64_t max_pop, uint32_t *keys, double *wm,
-                                 int32_t *we, long long *ctl, long long *population,
+// Chain j of the first population in slot j, at the origin; the other
+// slots on the free stack.
+__global__ void perm_init_kernel(int64_t M0, int64_t max_pop, int H, uint32_t *keys,
+                                 int32_t *ord, uint32_t *endk, double *wm, int32_t *we,
+                                 int32_t *free_slots, long long *ctl, long long *population,
                                  double *logz, double *mean_r2)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < M0; j += stride) {
-        keys[j] = kOriginKey;
-        wm[j] = 1.0;
-        we[j] = 0;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < max_pop; j += stride) {
+        if (j < M0) {
+            ord[j] = (int32_t)j;
+            endk[j] = kOriginKey;
+            keys[j * 2 * H] = kOriginKey;
+            wm[j] = 1.0;
+            we[j] = 0;
+        } else {
+            free_slots[j - M0] = (int32_t)j;
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         ctl[0] = M0;
         ctl[1] = 0;
         ctl[2] = 0;
+        ctl[3] = max_pop - M0;
+        ctl[4] = 0;
         population[0] = M0;
         logz[0] = 0.0;
         if (mean_r2) mean_r2[0] = 0.0;
     }
-    (void)max_pop;
 }
 
-// Step i of every chain of the population (keys / wm / we of this step's
-// buffer, population *pcount): growth, weight, fate, partial sums.
+// Sum of the table entries of the first n keys at ks (16-byte aligned) for
+// the end whose bias is kb; the entries' fields never carry into one
+// another, so the order of the sum does not matter.
+__device__ __forceinline__ uint32_t scan_keys(const uint32_t *lut, const uint32_t *ks, int n,
+                                              uint32_t kb)
+{
+    const uint4 *g = reinterpret_cast<const uint4 *>(ks);
+    uint32_t acc = 0u;
+    const int full = n >> 2;
+#pragma unroll 4
+    for (int t = 0; t < full; ++t) {
+        const uint4 v = g[t];
+        acc += lut_at(lut, lut_off(v.x + kb)) + lut_at(lut, lut_off(v.y + kb)) +
+               lut_at(lut, lut_off(v.z + kb)) + lut_at(lut, lut_off(v.w + kb));
+    }
+    const int r = n & 3;
+    if (r) {
+        const uint4 v = g[full];
+        acc += lut_at(lut, lut_off(v.x + kb));
+        if (r > 1) acc += lut_at(lut, lut_off(v.y + kb));
+        if (r > 2) acc += lut_at(lut, lut_off(v.z + kb));
+    }
+    return acc;
+}
+
+// Step i of every chain of the population (ord / endk / wm / we of this
+// step's buffer, population *pcount): growth, weight, fate, chunk counts,
+// partial sums; the slots of chains that leave go to the free stack (*nfree
+// entries).
 template <bool kIsaw>
 __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
-    const PermArgs a, int i, Threshold hi, Threshold lo, uint32_t *keys, double *wm, int32_t *we,
-    int8_t *fate, unsigned long long *packed, const long long *pcount, PermPartial *parts)
+    const PermArgs a, int i, Threshold hi, Threshold lo, uint32_t *keys, int H,
+    const int32_t *ord, uint32_t *endk, double *wm, int32_t *we, int8_t *fate,
+    unsigned long long *chunks, const long long *pcount, PermPartial *parts,
+    int32_t *free_slots, long long *nfree)
 {
     __shared__ uint32_t lut[kLutWords];
     __shared__ uint8_t seltab[kSelBytes];
@@ -167,6 +222,7 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
     __shared__ double wt64[8];
     __shared__ double red_s[kPermThreads / 32], red_r[kPermThreads / 32], red_g[kPermThreads / 32];
     __shared__ int32_t red_e[kPermThreads / 32];
+    __shared__ unsigned wk[kPermWarps], wr[kPermWarps];
     fill_tables(lut, seltab);
     if (threadIdx.x < 8) {
         wt32[threadIdx.x] = a.wt32[threadIdx.x];
@@ -175,78 +231,117 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
     __syncthreads();
     const int64_t P = *pcount;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t MP = a.max_pop;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t emax = INT_MIN;     // running largest exponent of this lane's grown chains
     double s = 0.0, sr = 0.0, grown = 0.0;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P; j += stride) {
-        uint32_t *col = keys + j;
-        const uint32_t key = col[(int64_t)(i - 1) * MP];
-        const uint32_t kb = kNearBias - key;
-        uint32_t acc = 0u;
-        if (kIsaw) {
-            for (int q = 0; q <= i - 2; ++q) acc += lut_at(lut, lut_off(col[(int64_t)q * MP] + kb));
-        } else {
-            for (int q = i & 1; q <= i - 2; q += 2) acc += lut_at(lut, lut_off(col[(int64_t)q * MP] + kb));
-        }
-        const uint32_t freem = ~acc & 63u;
-        const int m = __popc(freem);
+    // Whole blocks step through the population together, one chunk of
+    // kPermThreads chains at a time.
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < P; j0 += stride) {
+        const int64_t j = j0 + threadIdx.x;
+        const bool valid = j < P;
         int8_t f = 0;
-        if (m > 0) {
-            const uint32_t x =
-                philox(make_uint4((uint32_t)j, a.ens, (uint32_t)i, 0u), a.key).x;
-            LogW lw_unused;
-            const int sel = choose<kIsaw>(freem, m, acc, x, seltab, wt32, wt64, lw_unused);
-            // The step's weight factor in FP64: m, or the sum of the free
-            // neighbours' Boltzmann factors in slot order.
-            double S;
+        int32_t slot = 0;
+        if (valid) {
+            slot = ord[j];
+            uint32_t *ks = keys + (int64_t)slot * (2 * H);
+            const uint32_t key = endk[j];
+            const uint32_t kb = kNearBias - key;
+            // Monomers 0 .. i-2 (ISAW), or those of the parity of i, the only
+            // ones that can be neighbours of the new site (athermal).
+            uint32_t acc;
             if (kIsaw) {
-                S = 0.0;
+                acc = scan_keys(lut, ks, i / 2, kb) + scan_keys(lut, ks + H, (i - 1) / 2, kb);
+            } else {
+                const int p = i & 1;
+                acc = scan_keys(lut, ks + p * H, (i - p) / 2, kb);
+            }
+            const uint32_t freem = ~acc & 63u;
+            const int m = __popc(freem);
+            if (m > 0) {
+                const uint32_t x =
+                    philox(make_uint4((uint32_t)j, a.ens, (uint32_t)i, 0u), a.key).x;
+                LogW lw_unused;
+                const int sel = choose<kIsaw>(freem, m, acc, x, seltab, wt32, wt64, lw_unused);
+                // The step's weight factor in FP64: m, or the sum of the free
+                // neighbours' Boltzmann factors in slot order.
+                double S;
+                if (kIsaw) {
+                    S = 0.0;
 #pragma unroll
-                for (int d = 0; d < 6; ++d) {
-                    const uint32_t cd = (acc >> (8 + 3 * d)) & 7u;
-                    S = __dadd_rn(S, ((freem >> d) & 1u) ? wt64[cd] : 0.0);
+                    for (int d = 0; d < 6; ++d) {
+                        const uint32_t cd = (acc >> (8 + 3 * d)) & 7u;
+                        S = __dadd_rn(S, ((freem >> d) & 1u) ? wt64[cd] : 0.0);
+                    }
+                } else {
+                    S = (double)m;
                 }
-            } else {
-                S = (double)m;
+                const uint32_t axis_step = 1u << (10 * (sel >> 1));
+                const uint32_t nk = (sel & 1) ? key - axis_step : key + axis_step;
+                ks[(i & 1) * H + (i >> 1)] = nk;
+                endk[j] = nk;
+                double m_;
+                int32_t e_;
+                norm_weight(__dmul_rn(wm[j], S), m_, e_);
+                const int32_t e_new = we[j] + e_;
+                wm[j] = m_;
+                we[j] = e_new;
+                if (above(m_, e_new, hi)) {
+                    f = 2;
+                } else if (below(m_, e_new, lo)) {
+                    const uint32_t y =
+                        philox(make_uint4((uint32_t)j, a.ens, (uint32_t)i, 1u), a.key).x;
+                    f = (y >> 31) ? -1 : 0;
+                } else {
+                    f = 1;
+                }
+                // Partial sums of W and W R^2, relative to 2^emax.
+                const int ex = (int)(nk & 1023u) - 512, ey = (int)((nk >> 10) & 1023u) - 512,
+                          ez = (int)(nk >> 20) - 512;
+                const double R2 = (double)(ex * ex + ey * ey + ez * ez);
+                if (e_new > emax) {
+                    const double sc = emax == INT_MIN ? 0.0 : ldexp(1.0, emax - e_new);
+                    s *= sc;
+                    sr *= sc;
+                    emax = e_new;
+                }
+                const double w = ldexp(m_, e_new - emax);
+                s += w;
+                sr += w * R2;
+                grown += 1.0;
             }
-            const uint32_t axis_step = 1u << (10 * (sel >> 1));
-            const uint32_t nk = (sel & 1) ? key - axis_step : key + axis_step;
-            col[(int64_t)i * MP] = nk;
-            double m_;
-            int32_t e_;
-            norm_weight(__dmul_rn(wm[j], S), m_, e_);
-            const int32_t e_new = we[j] + e_;
-            wm[j] = m_;
-            we[j] = e_new;
-            if (above(m_, e_new, hi)) {
-                f = 2;
-            } else if (below(m_, e_new, lo)) {
-                const uint32_t y =
-                    philox(make_uint4((uint32_t)j, a.ens, (uint32_t)i, 1u), a.key).x;
-                f = (y >> 31) ? -1 : 0;
-            } else {
-                f = 1;
-            }
-            // Partial sums of W and W R^2, relative to 2^emax.
-            const int ex = (int)(nk & 1023u) - 512, ey = (int)((nk >> 10) & 1023u) - 512,
-                      ez = (int)(nk >> 20) - 512;
-            const double R2 = (double)(ex * ex + ey * ey + ez * ez);
-            if (e_new > emax) {
-                const double sc = emax == INT_MIN ? 0.0 : ldexp(1.0, emax - e_new);
-                s *= sc;
-                sr *= sc;
-                emax = e_new;
-            }
-            const double w = ldexp(m_, e_new - emax);
-            s += w;
-            sr += w * R2;
-            grown += 1.0;
+            fate[j] = f;
         }
-        fate[j] = f;
-        packed[j] = (unsigned long long)(f != 0) | ((unsigned long long)(f == 2) << 32);
+        // The slots of the chains that leave, back to the free stack (one
+        // atomic per warp; the stack's order does not matter).
+        const bool leaves = valid && f == 0;
+        const unsigned gone = __ballot_sync(0xffffffffu, leaves);
+        if (gone) {
+            unsigned long long at = 0;
+            if (lane == 0)
+                at = atomicAdd(reinterpret_cast<unsigned long long *>(nfree),
+                               (unsigned long long)__popc(gone));
+            at = __shfl_sync(0xffffffffu, at, 0);
+            if (leaves) free_slots[at + __popc(gone & ((1u << lane) - 1u))] = slot;
+        }
+        // The chunk's counts: chains kept, enrichment requests.
+        const unsigned kept_m = __ballot_sync(0xffffffffu, valid && f != 0);
+        const unsigned req_m = __ballot_sync(0xffffffffu, valid && f == 2);
+        if (lane == 0) {
+            wk[warp] = __popc(kept_m);
+            wr[warp] = __popc(req_m);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long kept = 0, req = 0;
+            for (int q = 0; q < kPermWarps; ++q) {
+                kept += wk[q];
+                req += wr[q];
+            }
+            chunks[j0 / kPermThreads] = kept | (req << 32);
+        }
+        __syncthreads();
     }
     // Block partial: the largest exponent, then the sums rescaled to it.
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t bm = emax;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) bm = max(bm, __shfl_xor_sync(0xffffffffu, bm, o));
@@ -283,63 +378,24 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
     }
 }
 
-// Exclusive scan of the packed counts inside tile blockIdx.x (1024 chains,
-// 4 per thread); the tile's total goes to tiles[tile].
-__global__ void __launch_bounds__(kPermThreads) perm_tiles_kernel(
-    const unsigned long long *packed, const long long *pcount, unsigned long long *excl,
-    unsigned long long *tiles)
-{
-    __shared__ unsigned long long wsum[kPermThreads / 32];
-    const int64_t P = *pcount;
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    if (base >= P) return;
-    const int64_t j0 = base + 4 * (int64_t)threadIdx.x;
-    unsigned long long v[4], run = 0;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        v[r] = (j0 + r < P) ? packed[j0 + r] : 0ull;
-        const unsigned long long t = v[r];
-        v[r] = run;               // exclusive within the thread
-        run += t;
-    }
-    // Exclusive scan of the threads' totals.
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long incl = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    unsigned long long woff = 0, total = 0;
-    for (int q = 0; q < kPermThreads / 32; ++q) {
-        if (q < warp) woff += wsum[q];
-        total += wsum[q];
-    }
-    const unsigned long long off = woff + incl - run;
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-        if (j0 + r < P) excl[j0 + r] = off + v[r];
-    if (threadIdx.x == 0) tiles[blockIdx.x] = total;
-}
-
-// One block: the tiles' offsets, the cap, the next population size, and the
-// estimates of length i from the grow kernel's partials.
+// One block: the chunks' offsets, the cap, the next population size, the
+// free slots the copies take, and the estimates of length i from the grow
+// kernel's partials.
 __global__ void __launch_bounds__(kTopThreads) perm_top_kernel(
-    int i, int64_t max_pop, double log_m0, unsigned long long *tiles, const long long *pcount,
-    long long *pnext, long long *grants, const PermPartial *parts, int nparts,
-    long long *population, double *logz, double *mean_r2)
+    int i, int64_t max_pop, double log_m0, unsigned long long *chunks, const long long *pcount,
+    long long *pnext, long long *grants, long long *nfree, long long *pop_top,
+    const PermPartial *parts, int nparts, long long *population, double *logz,
+    double *mean_r2)
 {
     __shared__ unsigned long long wsum[kTopThreads / 32];
     __shared__ double rs[kTopThreads / 32], rr[kTopThreads / 32], rg[kTopThreads / 32];
     __shared__ int32_t re[kTopThreads / 32];
     const int64_t P = *pcount;
-    const int64_t ntiles = (P + kScanTile - 1) / kScanTile;
-    const int64_t per = (ntiles + kTopThreads - 1) / kTopThreads;
+    const int64_t nchunks = (P + kPermThreads - 1) / kPermThreads;
+    const int64_t per = (nchunks + kTopThreads - 1) / kTopThreads;
     const int64_t t0 = (int64_t)threadIdx.x * per;
     unsigned long long run = 0;
-    for (int64_t t = t0; t < t0 + per && t < ntiles; ++t) run += tiles[t];
+    for (int64_t t = t0; t < t0 + per && t < nchunks; ++t) run += chunks[t];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long incl = run;
 #pragma unroll
@@ -355,9 +411,9 @@ __global__ void __launch_bounds__(kTopThreads) perm_top_kernel(
         total += wsum[q];
     }
     unsigned long long off = woff + incl - run;
-    for (int64_t t = t0; t < t0 + per && t < ntiles; ++t) {
-        const unsigned long long v = tiles[t];
-        tiles[t] = off;
+    for (int64_t t = t0; t < t0 + per && t < nchunks; ++t) {
+        const unsigned long long v = chunks[t];
+        chunks[t] = off;
         off += v;
     }
     // Estimates: the largest exponent over the partials, then the sums.
@@ -405,6 +461,10 @@ __global__ void __launch_bounds__(kTopThreads) perm_top_kernel(
         const long long Pn = base + (extra < G ? extra : G);
         *pnext = Pn;
         *grants = G;
+        // The granted copies take the top Pn - base slots of the free stack.
+        const long long top = *nfree;
+        *pop_top = top;
+        *nfree = top - (Pn - base);
         population[i] = Pn;
         if (g > 0.0) {
             logz[i] = log(s) + (double)E * 0.69314718055994530942 - log_m0;
@@ -416,40 +476,76 @@ __global__ void __launch_bounds__(kTopThreads) perm_top_kernel(
     }
 }
 
-// Kept chains, in population order, to their places in the next buffer.
+// Kept chains, in population order, to their places in the next buffer
+// (per chunk: the chunk's offset from the top kernel plus a block scan of
+// its fates); the copy granted to the enrichment request of rank r takes
+// free slot free_slots[top - 1 - r] and the keys 0..i of its original.
 __global__ void __launch_bounds__(kPermThreads) perm_scatter_kernel(
-    int i, int64_t max_pop, const uint32_t *keys, uint32_t *keys_n, const double *wm,
-    const int32_t *we, double *wm_n, int32_t *we_n, const int8_t *fate,
-    const unsigned long long *excl, const unsigned long long *tiles, const long long *pcount,
-    const long long *grants)
+    int i, int H, uint32_t *keys, const int32_t *ord, int32_t *ord_n, const uint32_t *endk,
+    uint32_t *endk_n, const double *wm, const int32_t *we, double *wm_n, int32_t *we_n,
+    const int8_t *fate, const unsigned long long *chunks, const long long *pcount,
+    const long long *grants, const int32_t *free_slots, const long long *pop_top)
 {
+    __shared__ unsigned wk[kPermWarps], wr[kPermWarps];
     const int64_t P = *pcount;
     const long long G = *grants;
+    const long long top = *pop_top;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < P; j += stride) {
-        const int f = fate[j];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned below_me = (1u << lane) - 1u;
+    for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < P; j0 += stride) {
+        const int64_t j = j0 + threadIdx.x;
+        const int f = j < P ? fate[j] : 0;
+        const unsigned kept_m = __ballot_sync(0xffffffffu, f != 0);
+        const unsigned req_m = __ballot_sync(0xffffffffu, f == 2);
+        if (lane == 0) {
+            wk[warp] = __popc(kept_m);
+            wr[warp] = __popc(req_m);
+        }
+        __syncthreads();
+        unsigned kb = 0, rb = 0;
+        for (int q = 0; q < warp; ++q) {
+            kb += wk[q];
+            rb += wr[q];
+        }
+        __syncthreads();
         if (f == 0) continue;
-        const unsigned long long e = excl[j] + tiles[j / kScanTile];
-        const long long kept_before = (long long)(e & 0xFFFFFFFFull);
-        const long long rank = (long long)(e >> 32);
+        const unsigned long long c = chunks[j0 / kPermThreads];
+        const long long kept_before =
+            (long long)(c & 0xFFFFFFFFull) + kb + __popc(kept_m & below_me);
+        const long long rank = (long long)(c >> 32) + rb + __popc(req_m & below_me);
         const long long dst = kept_before + (rank < G ? rank : G);
         const int copies = (f == 2 && rank < G) ? 2 : 1;
         const int32_t w_e = we[j] + (copies == 2 ? -1 : (f == -1 ? 1 : 0));
-        for (int c = 0; c < copies; ++c) {
-            wm_n[dst + c] = wm[j];
-            we_n[dst + c] = w_e;
-        }
-        for (int q = 0; q <= i; ++q) {
-            const uint32_t k = keys[(int64_t)q * max_pop + j];
-            for (int c = 0; c < copies; ++c) keys_n[(int64_t)q * max_pop + dst + c] = k;
+        const int32_t slot = ord[j];
+        const uint32_t ek = endk[j];
+        const double w_m = wm[j];
+        ord_n[dst] = slot;
+        endk_n[dst] = ek;
+        wm_n[dst] = w_m;
+        we_n[dst] = w_e;
+        if (copies == 2) {
+            const int32_t s2 = free_slots[top - 1 - rank];
+            ord_n[dst + 1] = s2;
+            endk_n[dst + 1] = ek;
+            wm_n[dst + 1] = w_m;
+            we_n[dst + 1] = w_e;
+            // Keys 0..i: i/2 + 1 even and (i + 1)/2 odd monomers, whole
+            // 16-byte words (the words past them are never read unmasked).
+            const uint4 *src = reinterpret_cast<const uint4 *>(keys + (int64_t)slot * (2 * H));
+            uint4 *dstk = reinterpret_cast<uint4 *>(keys + (int64_t)s2 * (2 * H));
+            const int g0 = (i / 2 + 4) >> 2, g1 = ((i + 1) / 2 + 3) >> 2, h4 = H >> 2;
+            for (int t = 0; t < g0; ++t) dstk[t] = src[t];
+            for (int t = 0; t < g1; ++t) dstk[h4 + t] = src[h4 + t];
         }
     }
 }
 
 // The final population to the caller's arrays.
-__global__ void perm_final_kernel(int N, int64_t max_pop, const uint32_t *keys, const double *wm,
-                                  const int32_t *we, const long long *pcount, long long *final_n,
-                                  double *w_m, int32_t *w_e, int32_t *coords)
+__global__ void perm_final_kernel(int N, int64_t max_pop, int H, const uint32_t *keys,
+                                  const int32_t *ord, const double *wm, const int32_t *we,
+                                  const long long *pcount, long long *final_n, double *w_m,
+                                  int32_t *w_e, int32_t *coords)
 {
     const int64_t P = *pcount;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -457,13 +553,15 @@ __global__ void perm_final_kernel(int N, int64_t max_pop, const uint32_t *keys, 
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < P; c += stride) {
         if (w_m) w_m[c] = wm[c];
         if (w_e) w_e[c] = we[c];
-        if (coords)
+        if (coords) {
+            const uint32_t *ks = keys + (int64_t)ord[c] * (2 * H);
             for (int q = 0; q < N; ++q) {
-                const uint32_t k = keys[(int64_t)q * max_pop + c];
+                const uint32_t k = ks[(q & 1) * H + (q >> 1)];
                 coords[((int64_t)q * 3 + 0) * max_pop + c] = (int32_t)(k & 1023u) - 512;
                 coords[((int64_t)q * 3 + 1) * max_pop + c] = (int32_t)((k >> 10) & 1023u) - 512;
                 coords[((int64_t)q * 3 + 2) * max_pop + c] = (int32_t)(k >> 20) - 512;
             }
+        }
     }
 }
 
@@ -556,11 +654,21 @@ extern "C" int rosen_perm_run(const rosen_perm_params *p, const rosen_perm_out *
     if (e != cudaSuccess)
         return set_error(ROSEN_ECUDA, "rosen_perm_run: %s", cudaGetErrorString(e));
     const int64_t MP = p->max_population;
-    const int grid = (int)std::min<int64_t>(std::min<int64_t>((int64_t)sms * 8, kMaxParts),
-                                            (MP + kPermThreads - 1) / kPermThreads);
-    const unsigned tiles = (unsigned)((MP + kScanTile - 1) / kScanTile);
+    const int H = perm_half_words(p->N);
+    // Grid-stride kernels: the blocks the GPU holds at once.
+    int resident = 0;
+    e = a.isaw ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, perm_grow_kernel<true>,
+                                                               kPermThreads, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, perm_grow_kernel<false>,
+                                                               kPermThreads, 0);
+    if (e != cudaSuccess)
+        return set_error(ROSEN_ECUDA, "rosen_perm_run: %s", cudaGetErrorString(e));
+    const int grid = (int)std::min<int64_t>(
+        std::min<int64_t>((int64_t)sms * std::max(resident, 1), kMaxParts),
+        (MP + kPermThreads - 1) / kPermThreads);
     long long *population = reinterpret_cast<long long *>(o->population);
-    perm_init_kernel<<<grid, kPermThreads, 0, s>>>(p->M0, MP, w.keys[0], w.wm[0], w.we[0], w.ctl,
+    perm_init_kernel<<<grid, kPermThreads, 0, s>>>(p->M0, MP, H, w.keys, w.ord[0], w.endk[0],
+                                                   w.wm[0], w.we[0], w.free_slots, w.ctl,
                                                    population, o->logz, o->mean_r2);
     const double log_m0 = log((double)p->M0);
     double tm = 1.0;   // mu^i = tm 2^te
@@ -577,21 +685,24 @@ extern "C" int rosen_perm_run(const rosen_perm_params *p, const rosen_perm_out *
         const int b = (i - 1) & 1;      // this step's buffer; the next one is b ^ 1
         if (a.isaw)
             perm_grow_kernel<true><<<grid, kPermThreads, 0, s>>>(
-                a, i, hi, lo, w.keys[b], w.wm[b], w.we[b], w.fate, w.packed, w.ctl + b, w.parts);
+                a, i, hi, lo, w.keys, H, w.ord[b], w.endk[b], w.wm[b], w.we[b], w.fate, w.chunks,
+                w.ctl + b, w.parts, w.free_slots, w.ctl + 3);
         else
             perm_grow_kernel<false><<<grid, kPermThreads, 0, s>>>(
-                a, i, hi, lo, w.keys[b], w.wm[b], w.we[b], w.fate, w.packed, w.ctl + b, w.parts);
-        perm_tiles_kernel<<<tiles, kPermThreads, 0, s>>>(w.packed, w.ctl + b, w.excl, w.tiles);
-        perm_top_kernel<<<1, kTopThreads, 0, s>>>(i, MP, log_m0, w.tiles, w.ctl + b,
-                                                  w.ctl + (b ^ 1), w.ctl + 2, w.parts, grid,
-                                                  population, o->logz, o->mean_r2);
+                a, i, hi, lo, w.keys, H, w.ord[b], w.endk[b], w.wm[b], w.we[b], w.fate, w.chunks,
+                w.ctl + b, w.parts, w.free_slots, w.ctl + 3);
+        perm_top_kernel<<<1, kTopThreads, 0, s>>>(i, MP, log_m0, w.chunks, w.ctl + b,
+                                                  w.ctl + (b ^ 1), w.ctl + 2, w.ctl + 3,
+                                                  w.ctl + 4, w.parts, grid, population, o->logz,
+                                                  o->mean_r2);
         perm_scatter_kernel<<<grid, kPermThreads, 0, s>>>(
-            i, MP, w.keys[b], w.keys[b ^ 1], w.wm[b], w.we[b], w.wm[b ^ 1], w.we[b ^ 1], w.fate,
-            w.excl, w.tiles, w.ctl + b, w.ctl + 2);
+            i, H, w.keys, w.ord[b], w.ord[b ^ 1], w.endk[b], w.endk[b ^ 1], w.wm[b], w.we[b],
+            w.wm[b ^ 1], w.we[b ^ 1], w.fate, w.chunks, w.ctl + b, w.ctl + 2, w.free_slots,
+            w.ctl + 4);
     }
     const int fb = (p->N - 1) & 1;      // the buffer the last step wrote
     perm_final_kernel<<<grid, kPermThreads, 0, s>>>(
-        p->N, MP, w.keys[fb], w.wm[fb], w.we[fb], w.ctl + fb,
+        p->N, MP, H, w.keys, w.ord[fb], w.wm[fb], w.we[fb], w.ctl + fb,
         reinterpret_cast<long long *>(o->final_n), o->w_m, o->w_e,
         (p->flags & ROSEN_STORE_COORDS) ? o->coords : nullptr);
     return check_launch("rosen_perm_run");

@@ -260,8 +260,11 @@ def test_perm_workspace_and_outputs(rosen):
     assert L.rosen_perm_workspace_size(16, 0) == 0
     assert L.rosen_perm_workspace_size(16, (1 << 24) + 1) == 0
     n = L.rosen_perm_workspace_size(64, 10 ** 6)
-    # two populations of keys (8 N bytes per chain) plus weights and scans
-    assert 8 * 64 * 10 ** 6 < n < (8 * 64 + 64) * 10 ** 6
+    # one storage slot of keys (4 N bytes per chain) plus slot numbers,
+    # weights, the free-slot stack and scans
+    assert 4 * 64 * 10 ** 6 < n < (4 * 64 + 64) * 10 ** 6
+    # an odd N rounds each half slot up to whole 16-byte words
+    assert L.rosen_perm_workspace_size(65, 1024) >= 1024 * (4 * 2 * 36)
     assert _perm(rosen, nbytes=L.rosen_perm_workspace_size(16, 400) - 1) == rosen.ROSEN_ENOMEM
     assert _perm(rosen, ws=4096 + 16) == rosen.ROSEN_EINVAL          # 256-byte alignment
     missing = rosen.rosen_perm_out(population=4096, logz=None, final_n=12288)
