@@ -100,6 +100,8 @@ size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Words per half slot: the keys of one parity, rounded up to 16-byte words.
 __host__ __device__ inline int perm_half_words(int N) { return (((N + 1) / 2) + 3) & ~3; }
+// Words per slot: the two halves.
+__host__ __device__ inline int64_t perm_slot_words(int H) { return 2 * (int64_t)H; }
 
 // Carve the workspace (or, with base == nullptr, measure it).
 size_t perm_carve(void *base, int N, int64_t max_pop, PermWs *w)
@@ -114,7 +116,7 @@ size_t perm_carve(void *base, int N, int64_t max_pop, PermWs *w)
     const size_t P = (size_t)max_pop;
     const size_t chunks = (P + kPermThreads - 1) / kPermThreads;
     PermWs t;
-    t.keys = static_cast<uint32_t *>(take(4 * 2 * (size_t)perm_half_words(N) * P));
+    t.keys = static_cast<uint32_t *>(take(4 * (size_t)perm_slot_words(perm_half_words(N)) * P));
     for (int b = 0; b < 2; ++b) t.ord[b] = static_cast<int32_t *>(take(4 * P));
     for (int b = 0; b < 2; ++b) t.endk[b] = static_cast<uint32_t *>(take(4 * P));
     for (int b = 0; b < 2; ++b) t.wm[b] = static_cast<double *>(take(8 * P));
@@ -161,7 +163,7 @@ __global__ void perm_init_kernel(int64_t M0, int64_t max_pop, int H, uint32_t *k
         if (j < M0) {
             ord[j] = (int32_t)j;
             endk[j] = kOriginKey;
-            keys[j * 2 * H] = kOriginKey;
+            keys[j * perm_slot_words(H)] = kOriginKey;
             wm[j] = 1.0;
             we[j] = 0;
         } else {
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
         int32_t slot = 0;
         if (valid) {
             slot = ord[j];
-            uint32_t *ks = keys + (int64_t)slot * (2 * H);
+            uint32_t *ks = keys + slot * perm_slot_words(H);
             const uint32_t key = endk[j];
             const uint32_t kb = kNearBias - key;
             // Monomers 0 .. i-2 (ISAW), or those of the parity of i, the only
@@ -387,34 +389,43 @@ __global__ void __launch_bounds__(kTopThreads) perm_top_kernel(
     const PermPartial *parts, int nparts, long long *population, double *logz,
     double *mean_r2)
 {
-    __shared__ unsigned long long wsum[kTopThreads / 32];
+    __shared__ unsigned long long wsum[kTopThreads / 32 + 1];
     __shared__ double rs[kTopThreads / 32], rr[kTopThreads / 32], rg[kTopThreads / 32];
     __shared__ int32_t re[kTopThreads / 32];
     const int64_t P = *pcount;
     const int64_t nchunks = (P + kPermThreads - 1) / kPermThreads;
-    const int64_t per = (nchunks + kTopThreads - 1) / kTopThreads;
-    const int64_t t0 = (int64_t)threadIdx.x * per;
-    unsigned long long run = 0;
-    for (int64_t t = t0; t < t0 + per && t < nchunks; ++t) run += chunks[t];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long incl = run;
+    // Exclusive scan in rounds of kTopThreads chunks (coalesced; the next
+    // round's counts are loaded before this round is scanned).
+    unsigned long long total = 0;
+    unsigned long long v = (int64_t)threadIdx.x < nchunks ? chunks[threadIdx.x] : 0ull;
+    for (int64_t r0 = 0; r0 < nchunks; r0 += kTopThreads) {
+        const int64_t t = r0 + threadIdx.x, tn = t + kTopThreads;
+        const unsigned long long vn = tn < nchunks ? chunks[tn] : 0ull;
+        unsigned long long incl = v;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += u;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    unsigned long long woff = 0, total = 0;
-    for (int q = 0; q < kTopThreads / 32; ++q) {
-        if (q < warp) woff += wsum[q];
-        total += wsum[q];
-    }
-    unsigned long long off = woff + incl - run;
-    for (int64_t t = t0; t < t0 + per && t < nchunks; ++t) {
-        const unsigned long long v = chunks[t];
-        chunks[t] = off;
-        off += v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned long long ws = wsum[lane];
+            unsigned long long wi = ws;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long u = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += u;
+            }
+            wsum[lane] = wi - ws;            // exclusive offset of warp `lane`
+            if (lane == 31) wsum[32] = wi;   // the round's total
+        }
+        __syncthreads();
+        if (t < nchunks) chunks[t] = total + wsum[warp] + incl - v;
+        total += wsum[32];
+        __syncthreads();                     // wsum is rewritten by the next round
+        v = vn;
     }
     // Estimates: the largest exponent over the partials, then the sums.
     int32_t E = INT_MIN;
@@ -509,34 +520,46 @@ __global__ void __launch_bounds__(kPermThreads) perm_scatter_kernel(
             rb += wr[q];
         }
         __syncthreads();
-        if (f == 0) continue;
-        const unsigned long long c = chunks[j0 / kPermThreads];
-        const long long kept_before =
-            (long long)(c & 0xFFFFFFFFull) + kb + __popc(kept_m & below_me);
-        const long long rank = (long long)(c >> 32) + rb + __popc(req_m & below_me);
-        const long long dst = kept_before + (rank < G ? rank : G);
-        const int copies = (f == 2 && rank < G) ? 2 : 1;
-        const int32_t w_e = we[j] + (copies == 2 ? -1 : (f == -1 ? 1 : 0));
-        const int32_t slot = ord[j];
-        const uint32_t ek = endk[j];
-        const double w_m = wm[j];
-        ord_n[dst] = slot;
-        endk_n[dst] = ek;
-        wm_n[dst] = w_m;
-        we_n[dst] = w_e;
-        if (copies == 2) {
-            const int32_t s2 = free_slots[top - 1 - rank];
-            ord_n[dst + 1] = s2;
-            endk_n[dst + 1] = ek;
-            wm_n[dst + 1] = w_m;
-            we_n[dst + 1] = w_e;
-            // Keys 0..i: i/2 + 1 even and (i + 1)/2 odd monomers, whole
-            // 16-byte words (the words past them are never read unmasked).
-            const uint4 *src = reinterpret_cast<const uint4 *>(keys + (int64_t)slot * (2 * H));
-            uint4 *dstk = reinterpret_cast<uint4 *>(keys + (int64_t)s2 * (2 * H));
-            const int g0 = (i / 2 + 4) >> 2, g1 = ((i + 1) / 2 + 3) >> 2, h4 = H >> 2;
-            for (int t = 0; t < g0; ++t) dstk[t] = src[t];
-            for (int t = 0; t < g1; ++t) dstk[h4 + t] = src[h4 + t];
+        int32_t slot = 0, s2 = -1;
+        if (f != 0) {
+            const unsigned long long c = chunks[j0 / kPermThreads];
+            const long long kept_before =
+                (long long)(c & 0xFFFFFFFFull) + kb + __popc(kept_m & below_me);
+            const long long rank = (long long)(c >> 32) + rb + __popc(req_m & below_me);
+            const long long dst = kept_before + (rank < G ? rank : G);
+            const int copies = (f == 2 && rank < G) ? 2 : 1;
+            const int32_t w_e = we[j] + (copies == 2 ? -1 : (f == -1 ? 1 : 0));
+            slot = ord[j];
+            const uint32_t ek = endk[j];
+            const double w_m = wm[j];
+            ord_n[dst] = slot;
+            endk_n[dst] = ek;
+            wm_n[dst] = w_m;
+            we_n[dst] = w_e;
+            if (copies == 2) {
+                s2 = free_slots[top - 1 - rank];
+                ord_n[dst + 1] = s2;
+                endk_n[dst + 1] = ek;
+                wm_n[dst + 1] = w_m;
+                we_n[dst + 1] = w_e;
+            }
+        }
+        // The copies' keys 0..i (i/2 + 1 even and (i + 1)/2 odd monomers, in
+        // whole 16-byte words; the words past them are never read unmasked):
+        // the warp copies one copy at a time, a word per lane.
+        unsigned cm = __ballot_sync(0xffffffffu, s2 >= 0);
+        const int g0 = (i / 2 + 4) >> 2, g1 = ((i + 1) / 2 + 3) >> 2, h4 = H >> 2;
+        while (cm) {
+            const int from = __ffs(cm) - 1;
+            cm &= cm - 1u;
+            const int64_t a = __shfl_sync(0xffffffffu, slot, from);
+            const int64_t b = __shfl_sync(0xffffffffu, s2, from);
+            const uint4 *src = reinterpret_cast<const uint4 *>(keys + a * perm_slot_words(H));
+            uint4 *dstk = reinterpret_cast<uint4 *>(keys + b * perm_slot_words(H));
+            for (int t = lane; t < g0 + g1; t += 32) {
+                const int q = t < g0 ? t : h4 + (t - g0);
+                dstk[q] = src[q];
+            }
         }
     }
 }
@@ -554,7 +577,7 @@ __global__ void perm_final_kernel(int N, int64_t max_pop, int H, const uint32_t 
         if (w_m) w_m[c] = wm[c];
         if (w_e) w_e[c] = we[c];
         if (coords) {
-            const uint32_t *ks = keys + (int64_t)ord[c] * (2 * H);
+            const uint32_t *ks = keys + ord[c] * perm_slot_words(H);
             for (int q = 0; q < N; ++q) {
                 const uint32_t k = ks[(q & 1) * H + (q >> 1)];
                 coords[((int64_t)q * 3 + 0) * max_pop + c] = (int32_t)(k & 1023u) - 512;
