@@ -205,14 +205,24 @@ __device__ __forceinline__ void sincos_turn24(uint32_t V, float &sn, float &cs)
 
 // Trial direction from two words (the reading of "rngonsphere"):
 // z = 1 - 2 u24(a), phi = 2 pi u24(b), s = sqrt((1-z)(1+z)).  (1-z), (1+z) are
-// exact in FP32; sqrtf is correctly rounded.
-__device__ __forceinline__ float3 dir32(uint32_t a, uint32_t b)
+// exact in FP32; sqrtf is correctly rounded.  dir32x2 returns twice the
+// direction, as the pair test uses it, with the factor folded in:
+// 2z = 2 - 4 u24(a), 2s = sqrt((2 - 2z)(2 + 2z)).  Every factor of 2 (and 4
+// under the root) is exact and commutes with the rounding of a product or
+// a correctly rounded root, so dir32x2 is 2 dir32, bit for bit.
+__device__ __forceinline__ float3 dir32x2(uint32_t a, uint32_t b)
 {
-    const float z = 1.f - 2.f * u24f(a);
-    const float s = sqrtf((1.f - z) * (1.f + z));
+    const float z2 = 2.f - 4.f * u24f(a);
+    const float s2 = sqrtf((2.f - z2) * (2.f + z2));
     float sn, cs;
     sincos_turn24(b >> 8, sn, cs);
-    return make_float3(s * cs, s * sn, z);
+    return make_float3(s2 * cs, s2 * sn, z2);
+}
+
+__device__ __forceinline__ float3 dir32(uint32_t a, uint32_t b)
+{
+    const float3 u = dir32x2(a, b);
+    return make_float3(0.5f * u.x, 0.5f * u.y, 0.5f * u.z);
 }
 
 __device__ __forceinline__ void dir64(uint32_t a, uint32_t b, double &x, double &y, double &z)
@@ -820,10 +830,10 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                 trial_words(x, t, wa, wb);
                 twa[s] = wa;
                 twb[s] = wb;
-                const float3 u = dir32(wa, wb);
-                ux[s] = 2.f * u.x;   // 2u: d^2 = c + (2u).g
-                uy[s] = 2.f * u.y;
-                uz[s] = 2.f * u.z;
+                const float3 u = dir32x2(wa, wb);   // 2u: d^2 = c + (2u).g
+                ux[s] = u.x;
+                uy[s] = u.y;
+                uz[s] = u.z;
             }
             selw = g.bcast(selw, 0);
 
