@@ -505,8 +505,11 @@ typedef struct rosen_serve_config {
     int32_t shortest_first;    /* order in which admitted requests get GPU time
                                   slices: 0 = arrival order; 1 = least
                                   estimated remaining GPU time first, divided
-                                  by 1 + the seconds the request has waited
-                                  (so large requests are not starved)          */
+                                  by 1 + the seconds the request has waited;
+                                  a request admitted for longer than 1 s + 2x
+                                  its own GPU time gets every other slice
+                                  until done, every slice while requests wait
+                                  for admission (so none starves)              */
     uint64_t pool_max_bytes;   /* cap of the server's device memory pool (0: no
                                   cap); a request whose memory the pool cannot
                                   supply fails with ROSEN_ENOMEM and gives its

@@ -16,9 +16,12 @@
 //    last blocks of the previous one finish;
 //  - chooses the request of each next slice by policy: arrival order, or
 //    (shortest_first) the least estimated remaining GPU time, discounted by
-//    the time the request has waited; under either policy a request that has
-//    been admitted for more than kStarveNs goes first, oldest first, so that
-//    no request starves;
+//    the time the request has waited.  Under shortest_first a request that
+//    has been admitted for longer than kStarveNs plus kStarveOwn times its
+//    own estimated GPU time is overdue: the oldest overdue request gets every
+//    other slice, so no request starves and short requests still pass it;
+//    while requests wait for admission (the server is saturated, and short
+//    requests wait in the queue anyway) it gets every slice;
 //  - keeps about kLookaheadNs of slices enqueued so that the GPU does not
 //    idle between slices (the next slice's blocks start as the last ones of
 //    the running slice finish);
@@ -67,7 +70,8 @@ constexpr int64_t kLookaheadNs = 8'000'000;    // estimated work kept enqueued
 constexpr int kMaxInflight = 16;               // slices enqueued at once
 constexpr int64_t kPassLimitNs = 1'000'000'000;   // longest a request may be passed over
 constexpr double kAgingNs = 1e9;               // shortest_first: waiting discount scale
-constexpr int64_t kStarveNs = 1'000'000'000;   // admitted longer: served in arrival order
+constexpr int64_t kStarveNs = 1'000'000'000;   // shortest_first: overdue after this wait
+constexpr double kStarveOwn = 2.0;             //   plus this many times its own GPU time
 
 int64_t now_ns()
 {
@@ -147,6 +151,7 @@ struct rosen_server {
     std::vector<std::pair<void *, size_t>> to_free;   // released conformations
     cudaStream_t free_stream = nullptr;
     uint64_t next_ticket = 1;
+    bool overdue_turn = false;         // shortest_first: the next shared slice's turn
     bool stop = false;
     std::thread th;
     // counters
@@ -558,35 +563,40 @@ void launch_slice(rosen_server *s, Request *q)
     if (q->next_chain >= C) finish(q);
 }
 
-// The request whose slice goes next: the oldest (arrival order), or the one
-// with the least estimated remaining GPU time divided by 1 + its waiting
-// time in seconds (shortest_first); requests admitted more than kStarveNs
-// ago come first, oldest first.  At most two slices of one request (one per
+// The request whose slice goes next: the oldest (arrival order), or
+// (shortest_first) the one with the least estimated remaining GPU time
+// divided by 1 + its waiting time in seconds, alternating with the oldest
+// overdue request while there is one (which goes first outright while
+// requests wait for admission).  At most two slices of one request (one per
 // stream) are enqueued at once.
 Request *pick(rosen_server *s, int64_t now)
 {
-    Request *best = nullptr;
+    Request *overdue = nullptr, *best = nullptr;
     double best_key = 0.0;
-    bool best_old = false;
     for (Request *q : s->active) {
         if (q->finishing || q->inflight >= 2 || q->next_chain >= q->req.C) continue;
-        const bool old = now - q->t_admit > kStarveNs;
-        if (best_old && !old) continue;
-        if (old && !best_old) best = nullptr;
-        best_old = best_old || old;
-        double key;
-        if (s->cfg.shortest_first && !old) {
-            const double rem = (double)(q->req.C - q->next_chain) * q->ns_per_chain;
-            key = rem / (1.0 + (double)(now - q->t_submit) / kAgingNs);
-        } else {
-            key = (double)q->t_submit;
+        if (!s->cfg.shortest_first) {
+            if (!best || q->t_submit < best->t_submit) best = q;
+            continue;
         }
+        const double own = (double)q->req.C * q->ns_per_chain;
+        if ((double)(now - q->t_admit) > (double)kStarveNs + kStarveOwn * own) {
+            if (!overdue || q->t_submit < overdue->t_submit) overdue = q;
+            continue;
+        }
+        const double rem = (double)(q->req.C - q->next_chain) * q->ns_per_chain;
+        const double key = rem / (1.0 + (double)(now - q->t_submit) / kAgingNs);
         if (!best || key < best_key) {
             best = q;
             best_key = key;
         }
     }
-    return best;
+    if (overdue && best) {
+        if (!s->queue.empty()) return overdue;
+        s->overdue_turn = !s->overdue_turn;
+        return s->overdue_turn ? overdue : best;
+    }
+    return overdue ? overdue : best;
 }
 
 // Completed slices (oldest first): refine the GPU-time estimates.  A slice's
@@ -615,9 +625,15 @@ bool reap_slices(rosen_server *s)
             if (own > 0.f && sl.chains > 0) {
                 const double per = (double)own * 1e6 / (double)sl.chains;
                 q->ns_per_chain = 0.5 * q->ns_per_chain + 0.5 * per;
-                const uint64_t key = rate_key(q->req);
-                auto it = s->rate.find(key);
-                s->rate[key] = it == s->rate.end() ? per : 0.8 * it->second + 0.2 * per;
+                // Only a slice of at least the chains the GPU grows at once
+                // measures the class's rate: a smaller one takes about the
+                // time of one chain whatever its size (and any wait for the
+                // SMs, divided by few chains, would inflate the rate).
+                if (sl.chains >= q->resident) {
+                    const uint64_t key = rate_key(q->req);
+                    auto it = s->rate.find(key);
+                    s->rate[key] = it == s->rate.end() ? per : 0.8 * it->second + 0.2 * per;
+                }
             }
             if (s->last_end) s->timing_events.push_back(s->last_end);
             s->last_end = sl.end;
@@ -804,6 +820,14 @@ extern "C" int rosen_serve_create(const rosen_serve_config *cfg, rosen_server **
     if (e == cudaSuccess) {
         uint64_t keep = cfg->mem_budget_bytes;   // keep freed blocks for reuse up to the budget
         e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e == cudaSuccess) {
+        // A block freed by a request whose stream still has work queued is not
+        // handed to another request with a wait on that stream: the new
+        // request would otherwise start only when the old one's queued slices
+        // have run.  (Blocks whose frees have completed are still reused.)
+        int no = 0;
+        e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolReuseAllowInternalDependencies, &no);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->free_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
