@@ -65,6 +65,8 @@ def compare(g, o, N, max_pop):
     (4, 11, 800, 800, 0.2, 4.684, math.inf, 0.0),    # no thresholds: plain Rosenbluth
     (5, 200, 20000, 60000, 0.0, 4.684, 2.0, 0.5),    # long chains, many scan tiles
     (6, 2, 37, 100, 0.0, 4.684, 1.3, 0.6),           # a single step
+    (8, 33, 2000, 6000, 0.35, 5.0, 1.3, 0.6),        # odd N: half slots of 20 words
+    (9, 512, 300, 1200, 0.0, 4.684, 1.5, 0.5),       # the longest chains: 2 KiB slots
 ])
 def test_matches_the_oracle(rosen, seed, N, M0, max_pop, beta_eps, mu, c_hi, c_lo):
     g = run_gpu(rosen, seed, N, M0, max_pop, beta_eps, mu, c_hi, c_lo)
