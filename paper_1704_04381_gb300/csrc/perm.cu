@@ -238,13 +238,20 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
     double s = 0.0, sr = 0.0, grown = 0.0;
     // Whole blocks step through the population together, one chunk of
     // kPermThreads chains at a time.
+    // The next chunk's slot numbers are loaded one chunk ahead and the half
+    // slot its scan reads is prefetched to L2 while this chunk grows.
+    const int64_t j_first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int32_t slot_next = j_first < P ? ord[j_first] : 0;
+    const int half = i & 1;     // the half slot an athermal step scans
     for (int64_t j0 = (int64_t)blockIdx.x * blockDim.x; j0 < P; j0 += stride) {
         const int64_t j = j0 + threadIdx.x;
         const bool valid = j < P;
         int8_t f = 0;
-        int32_t slot = 0;
+        int32_t slot = slot_next;
+        if (j + stride < P) {
+            slot_next = ord[j + stride];
+        }
         if (valid) {
-            slot = ord[j];
             uint32_t *ks = keys + slot * perm_slot_words(H);
             const uint32_t key = endk[j];
             const uint32_t kb = kNearBias - key;
@@ -312,6 +319,15 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
                 grown += 1.0;
             }
             fate[j] = f;
+        }
+        if (j + stride < P) {
+            const uint32_t *nx = keys + slot_next * perm_slot_words(H);
+            if (kIsaw) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(nx));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + H));
+            } else {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + half * H));
+            }
         }
         // The slots of the chains that leave, back to the free stack (one
         // atomic per warp; the stack's order does not matter).
