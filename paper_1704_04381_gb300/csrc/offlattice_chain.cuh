@@ -117,19 +117,33 @@ __device__ __forceinline__ uint32_t cell_slot(uint64_t key, int logH)
     return x | (y << bx) | (z << (bx + by));
 }
 
-// First bead of the cell whose tagged key is `want` (-1: no bead there).
-__device__ __forceinline__ int cell_head(const uint4 *cells, int logH, uint64_t want,
-                                         uint64_t tag)
+// First bead of the cell whose tagged key is `want` (-1: no bead there),
+// going on from entry h, already loaded as e.
+__device__ __forceinline__ int cell_find(const uint4 *cells, int logH, uint64_t want,
+                                         uint64_t tag, uint32_t h, uint4 e)
 {
     const uint32_t hmask = (1u << logH) - 1u;
-    uint32_t h = cell_slot(want & kCellKeyMask, logH);
     for (;;) {
-        const uint4 e = cells[h];
         const uint64_t k = (uint64_t)e.x | ((uint64_t)e.y << 32);
         if ((k & ~kCellKeyMask) != tag) return -1;
         if (k == want) return (int)e.z;
         h = (h + 1u) & hmask;
+        e = cells[h];
     }
+}
+
+// First beads of two cells (the second only if `two`), their first probes
+// loaded together.
+__device__ __forceinline__ void cell_heads2(const uint4 *cells, int logH, uint64_t want0,
+                                            uint64_t want1, bool two, uint64_t tag, int &b0,
+                                            int &b1)
+{
+    const uint32_t h0 = cell_slot(want0 & kCellKeyMask, logH);
+    const uint32_t h1 = cell_slot(want1 & kCellKeyMask, logH);
+    const uint4 e0 = cells[h0];
+    const uint4 e1 = two ? cells[h1] : make_uint4(0u, 0u, 0u, 0u);
+    b0 = cell_find(cells, logH, want0, tag, h0, e0);
+    b1 = two ? cell_find(cells, logH, want1, tag, h1, e1) : -1;
 }
 
 // Put bead j at the head of the list of its cell (key `want`); returns the
@@ -589,6 +603,7 @@ __device__ __forceinline__ void redecide(const OffArgs &a, const ChainSmem &w, c
 // The heads of the 27 cells are kept between steps (cell[], heads[2] per
 // lane: cells gl and gl + G): while the end stays in one cell the only change
 // to those lists is the bead filed at this step, which heads its cell's list.
+// When the end changes cell, a lane's two cells are probed together.
 template <int G, bool LJ>
 __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong &w,
                                               const Group<G> &g, int i, uint64_t tag, float ehx,
@@ -619,14 +634,11 @@ __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong 
     const int cx = cell_coord(ehx, w.inv_cell), cy = cell_coord(ehy, w.inv_cell),
               cz = cell_coord(ehz, w.inv_cell);
     if (cx != cell[0] || cy != cell[1] || cz != cell[2]) {
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int q = g.gl + r * G;
-            const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = q / 9 - 1;
-            heads[r] = q < 27 ? cell_head(w.cells, w.logH,
-                                          cell_key(cx + dx, cy + dy, cz + dz) | tag, tag)
-                              : -1;
-        }
+        const int q0 = g.gl, q1 = g.gl + G;
+        cell_heads2(w.cells, w.logH,
+                    cell_key(cx + q0 % 3 - 1, cy + (q0 / 3) % 3 - 1, cz + q0 / 9 - 1) | tag,
+                    cell_key(cx + q1 % 3 - 1, cy + (q1 / 3) % 3 - 1, cz + q1 / 9 - 1) | tag,
+                    q1 < 27, tag, heads[0], heads[1]);
         cell[0] = cx;
         cell[1] = cy;
         cell[2] = cz;
