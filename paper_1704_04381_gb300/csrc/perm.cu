@@ -237,9 +237,9 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
     int32_t emax = INT_MIN;     // running largest exponent of this lane's grown chains
     double s = 0.0, sr = 0.0, grown = 0.0;
     // Whole blocks step through the population together, one chunk of
-    // kPermThreads chains at a time.
-    // The next chunk's slot numbers are loaded one chunk ahead and the half
-    // slot its scan reads is prefetched to L2 while this chunk grows.
+    // kPermThreads chains at a time; the next chunk's slot numbers are loaded
+    // a chunk ahead, and the half slots its scans read are prefetched to L2
+    // while this chunk grows.
     const int64_t j_first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int32_t slot_next = j_first < P ? ord[j_first] : 0;
     const int half = i & 1;     // the half slot an athermal step scans
@@ -248,9 +248,7 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
         const bool valid = j < P;
         int8_t f = 0;
         int32_t slot = slot_next;
-        if (j + stride < P) {
-            slot_next = ord[j + stride];
-        }
+        if (j + stride < P) slot_next = ord[j + stride];
         if (valid) {
             uint32_t *ks = keys + slot * perm_slot_words(H);
             const uint32_t key = endk[j];
