@@ -138,17 +138,52 @@ __device__ __forceinline__ void norm_weight(double x, double &m, int32_t &e)
     m = __longlong_as_double((b & 0x800FFFFFFFFFFFFFll) | (1023ll << 52));
 }
 
+// Weight against threshold.  Mantissas in [1, 2) are positive normal
+// doubles, which order like their bit patterns: the comparisons stay off the
+// FP64 pipe (a small fraction of the FP32 rate on this GPU).
 __device__ __forceinline__ bool above(double wm, int32_t we, const Threshold &t)
 {
     if (t.mode == 1) return false;
     if (t.mode == 2) return true;
-    return we > t.e || (we == t.e && wm > t.m);
+    return we > t.e || (we == t.e && __double_as_longlong(wm) > __double_as_longlong(t.m));
 }
 
 __device__ __forceinline__ bool below(double wm, int32_t we, const Threshold &t)
 {
     if (t.mode != 0) return false;
-    return we < t.e || (we == t.e && wm < t.m);
+    return we < t.e || (we == t.e && __double_as_longlong(wm) < __double_as_longlong(t.m));
+}
+
+// wm m for wm in [1, 2) and a small integer m (1..6: an athermal step),
+// rounded to the nearest double (ties to even) exactly as one FP64 multiply
+// rounds it, and renormalised to (mantissa in [1, 2), exponent): in integer
+// arithmetic, off the FP64 pipe.  The 53-bit significand times m is exact in
+// 64 bits (< 2^56); its top 53 bits are kept, rounded on the k bits below.
+__device__ __forceinline__ void mul_small(double wm, uint32_t m, double &m_out, int32_t &e_out)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(wm);
+    const unsigned long long X = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) * (unsigned long long)m;
+    int k = 11 - __clzll((long long)X);           // X in [2^(52+k), 2^(53+k))
+    unsigned long long q = X >> k;
+    if (k > 0) {
+        const unsigned long long r = X & ((1ull << k) - 1ull), half = 1ull << (k - 1);
+        if (r > half || (r == half && (q & 1ull))) ++q;
+        if (q >> 53) {                            // rounded up to 2^53
+            q >>= 1;
+            ++k;
+        }
+    }
+    m_out = __longlong_as_double((long long)((q & 0xFFFFFFFFFFFFFull) | (1023ull << 52)));
+    e_out = k;
+}
+
+// m 2^d for m in [1, 2) and d <= 0 by its exponent field; 0 below the
+// normal range (a relative weight under 2^-1022, far below the estimates'
+// rounding).
+__device__ __forceinline__ double scale_down(double m, int d)
+{
+    if (d < -1022) return 0.0;
+    return __longlong_as_double(__double_as_longlong(m) + ((long long)d << 52));
 }
 
 // Chain j of the first population in slot j, at the origin; the other
@@ -235,7 +270,8 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t emax = INT_MIN;     // running largest exponent of this lane's grown chains
-    double s = 0.0, sr = 0.0, grown = 0.0;
+    double s = 0.0, sr = 0.0;
+    int grown_n = 0;
     // Whole blocks step through the population together, one chunk of
     // kPermThreads chains at a time; the next chunk's slot numbers are loaded
     // a chunk ahead, and the half slots its scans read are prefetched to L2
@@ -269,18 +305,16 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
                     philox(make_uint4((uint32_t)j, a.ens, (uint32_t)i, 0u), a.key).x;
                 LogW lw_unused;
                 const int sel = choose<kIsaw>(freem, m, acc, x, seltab, wt32, wt64, lw_unused);
-                // The step's weight factor in FP64: m, or the sum of the free
+                // The step's weight factor: m (athermal: the product in
+                // integer arithmetic, mul_small), or the FP64 sum of the free
                 // neighbours' Boltzmann factors in slot order.
-                double S;
+                double S = 0.0;
                 if (kIsaw) {
-                    S = 0.0;
 #pragma unroll
                     for (int d = 0; d < 6; ++d) {
                         const uint32_t cd = (acc >> (8 + 3 * d)) & 7u;
                         S = __dadd_rn(S, ((freem >> d) & 1u) ? wt64[cd] : 0.0);
                     }
-                } else {
-                    S = (double)m;
                 }
                 const uint32_t axis_step = 1u << (10 * (sel >> 1));
                 const uint32_t nk = (sel & 1) ? key - axis_step : key + axis_step;
@@ -288,7 +322,10 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
                 endk[j] = nk;
                 double m_;
                 int32_t e_;
-                norm_weight(__dmul_rn(wm[j], S), m_, e_);
+                if (kIsaw)
+                    norm_weight(__dmul_rn(wm[j], S), m_, e_);
+                else
+                    mul_small(wm[j], (uint32_t)m, m_, e_);
                 const int32_t e_new = we[j] + e_;
                 wm[j] = m_;
                 we[j] = e_new;
@@ -306,15 +343,15 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
                           ez = (int)(nk >> 20) - 512;
                 const double R2 = (double)(ex * ex + ey * ey + ez * ez);
                 if (e_new > emax) {
-                    const double sc = emax == INT_MIN ? 0.0 : ldexp(1.0, emax - e_new);
+                    const double sc = emax == INT_MIN ? 0.0 : scale_down(1.0, emax - e_new);
                     s *= sc;
                     sr *= sc;
                     emax = e_new;
                 }
-                const double w = ldexp(m_, e_new - emax);
+                const double w = scale_down(m_, e_new - emax);
                 s += w;
-                sr += w * R2;
-                grown += 1.0;
+                sr = fma(w, R2, sr);
+                ++grown_n;
             }
             fate[j] = f;
         }
@@ -368,6 +405,7 @@ __global__ void __launch_bounds__(kPermThreads) perm_grow_kernel(
     const double sc = (emax == INT_MIN) ? 0.0 : ldexp(1.0, emax - E);
     s *= sc;
     sr *= sc;
+    double grown = (double)grown_n;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_xor_sync(0xffffffffu, s, o);
