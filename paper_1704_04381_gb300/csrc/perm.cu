@@ -447,13 +447,32 @@ __global__ void __launch_bounds__(kTopThreads) perm_top_kernel(
     const int64_t P = *pcount;
     const int64_t nchunks = (P + kPermThreads - 1) / kPermThreads;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // Exclusive scan in rounds of kTopThreads chunks (coalesced; the next
-    // round's counts are loaded before this round is scanned).
+    // Exclusive scan in rounds of kTopThreads x 4 chunks, four consecutive
+    // chunks per thread (two 16-byte loads; the next round's are issued
+    // before this round is scanned).
+    constexpr int kPer = 4;
+    constexpr int64_t kRound = (int64_t)kTopThreads * kPer;
     unsigned long long total = 0;
-    unsigned long long v = (int64_t)threadIdx.x < nchunks ? chunks[threadIdx.x] : 0ull;
-    for (int64_t r0 = 0; r0 < nchunks; r0 += kTopThreads) {
-        const int64_t t = r0 + threadIdx.x, tn = t + kTopThreads;
-        const unsigned long long vn = tn < nchunks ? chunks[tn] : 0ull;
+    unsigned long long v4[kPer], n4[kPer];
+    auto load4 = [&](int64_t r0, unsigned long long (&d)[kPer]) {
+        const int64_t t = r0 + (int64_t)threadIdx.x * kPer;
+        if (t + kPer <= nchunks) {
+            const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(chunks + t);
+            const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(chunks + t + 2);
+            d[0] = a.x;
+            d[1] = a.y;
+            d[2] = b.x;
+            d[3] = b.y;
+        } else {
+#pragma unroll
+            for (int c = 0; c < kPer; ++c) d[c] = t + c < nchunks ? chunks[t + c] : 0ull;
+        }
+    };
+    load4(0, v4);
+    for (int64_t r0 = 0; r0 < nchunks; r0 += kRound) {
+        const int64_t t = r0 + (int64_t)threadIdx.x * kPer;
+        if (r0 + kRound < nchunks) load4(r0 + kRound, n4);
+        const unsigned long long v = v4[0] + v4[1] + v4[2] + v4[3];
         unsigned long long incl = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -474,10 +493,16 @@ __global__ void __launch_bounds__(kTopThreads) perm_top_kernel(
             if (lane == 31) wsum[32] = wi;   // the round's total
         }
         __syncthreads();
-        if (t < nchunks) chunks[t] = total + wsum[warp] + incl - v;
+        unsigned long long off = total + wsum[warp] + incl - v;
+#pragma unroll
+        for (int c = 0; c < kPer; ++c) {
+            if (t + c < nchunks) chunks[t + c] = off;
+            off += v4[c];
+        }
         total += wsum[32];
         __syncthreads();                     // wsum is rewritten by the next round
-        v = vn;
+#pragma unroll
+        for (int c = 0; c < kPer; ++c) v4[c] = n4[c];
     }
     // Estimates: the largest exponent over the partials, then the sums.
     int32_t E = INT_MIN;
@@ -511,13 +536,18 @@ __global__ void __launch_bounds__(kTopThreads) perm_top_kernel(
         rg[warp] = g;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        s = sr = g = 0.0;
-        for (int q = 0; q < kTopThreads / 32; ++q) {
-            s += rs[q];
-            sr += rr[q];
-            g += rg[q];
+    if (warp == 0) {
+        s = rs[lane];
+        sr = rr[lane];
+        g = rg[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_xor_sync(0xffffffffu, s, o);
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            g += __shfl_xor_sync(0xffffffffu, g, o);
         }
+    }
+    if (threadIdx.x == 0) {
         const long long base = (long long)(total & 0xFFFFFFFFull);
         const long long extra = (long long)(total >> 32);
         const long long G = max_pop - base > 0 ? max_pop - base : 0;
