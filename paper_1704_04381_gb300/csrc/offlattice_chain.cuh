@@ -267,6 +267,18 @@ __device__ __forceinline__ void ff_add(float &hi, float &lo, float v)
     lo = t - (hi - s);
 }
 
+// ff_add of v = w / 2: the halving is exact, so each sum with v is one
+// fused multiply-add with 0.5 and rounds exactly as the sum does.
+__device__ __forceinline__ void ff_add_half(float &hi, float &lo, float w)
+{
+    const float s = fmaf(0.5f, w, hi);
+    const float bp = s - hi;
+    const float e = (hi - (s - bp)) + fmaf(0.5f, w, -bp);
+    const float t = lo + e;
+    hi = s + t;
+    lo = t - (hi - s);
+}
+
 // ---- float-float arithmetic (Knuth's TwoSum, Dekker's product with FMA) ----
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
@@ -836,8 +848,10 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                     x = draw<kFly>(
                         a, make_uint4(chain, a.ens, (uint32_t)i | aw, 1u + (uint32_t)(t >> 1)));
                 if (s == 0)
-                    selw = (x.x & 0xFFu) | ((x.y & 0xFFu) << 8) | ((x.z & 0xFFu) << 16) |
-                           ((x.w & 0xFFu) << 24);
+                    // The low bytes of the four words, x.x's lowest:
+                    // (x.x & 0xFF) | (x.y & 0xFF) << 8 | (x.z & 0xFF) << 16 | ...
+                    selw = __byte_perm(__byte_perm(x.x, x.y, 0x0040u),
+                                       __byte_perm(x.z, x.w, 0x0040u), 0x5410u);
                 uint32_t wa, wb;
                 trial_words(x, t, wa, wb);
                 twa[s] = wa;
@@ -1022,12 +1036,10 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                             vy = uy[s];
                             vz = uz[s];
                         }
-                    vx = 0.5f * g.bcast(vx, src);
-                    vy = 0.5f * g.bcast(vy, src);
-                    vz = 0.5f * g.bcast(vz, src);
-                    ff_add(ehx, elx, vx);
-                    ff_add(ehy, ely, vy);
-                    ff_add(ehz, elz, vz);
+                    // (ux holds 2u: the commit adds half of it.)
+                    ff_add_half(ehx, elx, g.bcast(vx, src));
+                    ff_add_half(ehy, ely, g.bcast(vy, src));
+                    ff_add_half(ehz, elz, g.bcast(vz, src));
                 }
                 if (g.gl == 0) {
                     // (.w: a long chain's cell link, set when the bead is filed)
