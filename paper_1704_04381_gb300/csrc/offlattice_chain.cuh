@@ -223,11 +223,14 @@ __device__ __forceinline__ void sincos_turn24(uint32_t V, float &sn, float &cs)
 // direction, as the pair test uses it, with the factor folded in:
 // 2z = 2 - 4 u24(a), 2s = sqrt((2 - 2z)(2 + 2z)).  Every factor of 2 (and 4
 // under the root) is exact and commutes with the rounding of a product or
-// a correctly rounded root, so dir32x2 is 2 dir32, bit for bit.
+// a correctly rounded root, so dir32x2 is 2 dir32, bit for bit.  In FP32:
+// 2z = 2 - (a >> 8) 2^-22 is one fused multiply-add of exact terms, and
+// since 2 - 2z and 2 + 2z are exact, their product is the single rounding
+// of 4 - (2z)^2, which is what fmaf(-2z, 2z, 4) rounds too.
 __device__ __forceinline__ float3 dir32x2(uint32_t a, uint32_t b)
 {
-    const float z2 = 2.f - 4.f * u24f(a);
-    const float s2 = sqrtf((2.f - z2) * (2.f + z2));
+    const float z2 = fmaf(-0x1p-22f, (float)(a >> 8), 2.f);
+    const float s2 = sqrtf(fmaf(-z2, z2, 4.f));
     float sn, cs;
     sincos_turn24(b >> 8, sn, cs);
     return make_float3(s2 * cs, s2 * sn, z2);
