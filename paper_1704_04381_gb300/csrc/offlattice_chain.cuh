@@ -371,6 +371,7 @@ __device__ __forceinline__ void dir_ff(uint32_t a, uint32_t b, float &xh, float 
 template <int G>
 struct Group {
     unsigned mask;   // the group's lanes in the warp
+    unsigned below;  // the group's lanes below this one (warp lane bits)
     int gl;          // lane within the group
     int base;        // first lane of the group in the warp
 
@@ -380,12 +381,16 @@ struct Group {
         gl = lane & (G - 1);
         base = lane - gl;
         mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << base);
+        below = ((1u << lane) - 1u) & mask;
     }
     __device__ unsigned ballot(bool p) const
     {
         const unsigned b = __ballot_sync(mask, p);
         return (G == 32) ? b : (b >> base) & ((1u << G) - 1u);
     }
+    // The group's votes at their warp lane positions (for counts and ranks
+    // with `below`, without shifting them down).
+    __device__ unsigned vote(bool p) const { return __ballot_sync(mask, p) & mask; }
     template <class V>
     __device__ V bcast(V v, int src) const
     {
@@ -814,9 +819,9 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                     L = make_float4(gx, gy, gz, 1.f + g2);
                     near = g2 < a.rf2;
                 }
-                const unsigned m = g.ballot(near);
+                const unsigned m = g.vote(near);
                 if (near) {
-                    const int slot = nn + __popc(m & ((1u << g.gl) - 1u));
+                    const int slot = nn + __popc(m & g.below);
                     w.nl[slot] = L;
                     w.nj[slot] = j;
                     if (LJ) {
@@ -913,7 +918,7 @@ __device__ __forceinline__ void off_chain(const OffArgs &a, int64_t c, const W &
                     flag |= valid[s] && fabsf(mind[s] - a.sig2) < band;
                     cnt += fr[s];
                 }
-                if (g.ballot(flag)) {
+                if (g.vote(flag)) {
                     ok = false;
                 } else {
                     const int incl = g.scan(cnt);
