@@ -56,7 +56,7 @@ BRUTE_OFF_PAIR, BRUTE_OFF_TRIAL = 8, 90
 # passes -- from one ncu capture of that launch: first pass 23,213,312 +
 # 78,660,864, second pass 18,835,968 + 17,702,912.  Reported as the
 # roofline's traffic for that configuration only.
-HS_TRAFFIC_BYTES = 23089664 + 78427904 + 18817024 + 17696768
+HS_TRAFFIC_BYTES = 22961664 + 78489856 + 18875648 + 18076160
 
 
 def brute_lattice_ops(N):

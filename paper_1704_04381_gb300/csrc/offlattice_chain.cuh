@@ -672,7 +672,7 @@ __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong 
             j = q < 27 ? heads[1] : -1;
         }
         const bool has = j >= 0;
-        if (!g.ballot(has)) break;
+        if (!g.vote(has)) break;
         float4 L = make_float4(0.f, 0.f, 0.f, 0.f);
         bool near = false;
         float4 h = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
@@ -691,9 +691,9 @@ __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong 
                 near = g2 < a.rf2;
             }
         }
-        const unsigned m = g.ballot(near);
+        const unsigned m = g.vote(near);
         if (near) {
-            const int slot = nn + __popc(m & ((1u << g.gl) - 1u));
+            const int slot = nn + __popc(m & g.below);
             w.nls[slot] = L;
             w.njs[slot] = j;
             if (LJ) {
@@ -719,9 +719,9 @@ __device__ __forceinline__ int long_near_list(const OffArgs &a, const ChainLong 
             L = make_float4(gx, gy, gz, 1.f + g2);
             near = g2 < a.rf2;
         }
-        const unsigned m = g.ballot(near);
+        const unsigned m = g.vote(near);
         if (near) {
-            const int slot = nn + __popc(m & ((1u << g.gl) - 1u));
+            const int slot = nn + __popc(m & g.below);
             w.nls[slot] = L;
             w.njs[slot] = j;
             if (LJ) {
